@@ -1,0 +1,174 @@
+/*
+ * x2c.h -- C ABI of the GB300 exact-decoupling (X2C) one-electron Hamiltonian library.
+ *
+ * Method: Peng, Middendorf, Weigend, Reiher, J. Chem. Phys. 138, 184105 (2013).
+ * Given the primitive-basis matrices S, T, V and W (Sec. II, Eqs. 4-6) the library
+ * returns the decoupled two-component (or scalar) Hamiltonian h of Eq. 8, either for the
+ * whole system (X2C, Sec. II.A) or in the local DLU scheme (Sec. III.A, Eqs. 42-43), where
+ * atomic U^L_AA, U^S_AA are computed once per atom kind and every pair block
+ * h_AB = U^L_A+ V_AB U^L_B + U^L_A+ T_AB U^S_B + U^S_A+ T_AB U^L_B + U^S_A+ W'_AB U^S_B
+ * (W' = W/4c^2 - T) is assembled from them.
+ *
+ * Conventions shared by every call
+ *  - Matrices are FP64, row-major, n x n, with leading dimension n, in DEVICE memory unless
+ *    a function says otherwise.  They are owned by the caller; the library never frees them.
+ *  - Two-component matrices use the time-reversal (quaternion) form of Eq. 5:
+ *        M = I2 (x) M0 + i (sigma_x (x) Mx + sigma_y (x) My + sigma_z (x) Mz),
+ *    spin-blocked (alpha block first); M0, Mx, My, Mz are real n x n.  For W these are
+ *    W0, Wx, Wy, Wz of Eq. 6 (W0 symmetric, Wx/Wy/Wz antisymmetric).  The output h is
+ *    returned the same way: h0 (symmetric) and h1, h2, h3 (antisymmetric); the dense
+ *    2n x 2n complex matrix is [[h0 + i h3, h2 + i h1], [-h2 + i h1, h0 - i h3]].
+ *  - Calls are asynchronous on the caller's CUDA stream (passed as void*, NULL = the legacy
+ *    default stream).  A non-OK return means nothing was enqueued or the enqueue failed.
+ *    Numerical failures detected on the device (Cholesky pivot <= 0, non-convergence,
+ *    failed positive/negative-energy split, non-finite values) are latched in the context
+ *    and returned by x2c_ctx_status(), which synchronises the stream.
+ *  - A context is bound to one device and is not thread-safe; use one per host thread.
+ *    It owns a device workspace that grows on demand (the first call of a larger size
+ *    allocates) and is freed by x2c_ctx_destroy().
+ *  - No function aborts, traps or exits; errors are returned as x2c_status.
+ */
+#ifndef X2C_H
+#define X2C_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  X2C_OK = 0,
+  X2C_ERR_ARG = 1,         /* invalid argument: NULL pointer, size out of range, bad option */
+  X2C_ERR_NOMEM = 2,       /* device or pinned-host allocation failed */
+  X2C_ERR_CUDA = 3,        /* a CUDA runtime call failed (see x2c_last_error_message) */
+  X2C_ERR_NOT_POSDEF = 4,  /* S or T not positive definite (Cholesky pivot <= 0) */
+  X2C_ERR_NOCONV = 5,      /* sign-function or matrix-square-root iteration did not converge */
+  X2C_ERR_DECOUPLING = 6,  /* spectrum does not split at -c^2 into equal halves (Sec. II) */
+  X2C_ERR_NONFINITE = 7,   /* NaN or Inf met in a result */
+  X2C_ERR_ADMISSION = 8,   /* serving: request can never fit the memory budget */
+  X2C_ERR_TIMEOUT = 9,     /* serving: wait timed out (the request keeps running) */
+  X2C_ERR_CANCELLED = 10,  /* serving: request was cancelled */
+  X2C_ERR_NOT_FOUND = 11   /* serving: unknown ticket */
+} x2c_status;
+
+typedef enum {
+  X2C_PREC_FP64 = 0,       /* every product in FP64 */
+  X2C_PREC_SPLIT_BF16 = 1  /* DLU pair assembly as split-precision (Ozaki) BF16 products
+                              with FP32 accumulation on the tensor cores; every eigen-type
+                              step (sign function, square roots, Cholesky) stays FP64 */
+} x2c_precision;
+
+typedef enum {
+  X2C_DLU_FREE_ATOM = 0,      /* U_AA from each kind's free-atom inputs (x2c_layout.kinds) */
+  X2C_DLU_MOLECULAR_BLOCK = 1 /* U_AA from the diagonal blocks S_AA, T_AA, V_AA, W_AA of the
+                                 molecular matrices (Eq. 43 read literally); one solve per atom */
+} x2c_dlu_potential;
+
+typedef struct {
+  double c;                  /* speed of light (a.u.); <= 0 selects 137.035999 */
+  int32_t two_component;     /* 0 = scalar (spin-free), 1 = two-component with Wx, Wy, Wz */
+  int32_t precision;         /* x2c_precision */
+  int32_t dlu_potential;     /* x2c_dlu_potential */
+  int32_t so_same_atom_only; /* 1: Wx, Wy, Wz vanish outside same-atom blocks, so DLU reads
+                                only those blocks and skips the rest (two-component only) */
+  int32_t n_slices;          /* split precision: BF16 slices per operand, 0 = default (5) */
+  int32_t reserved[3];       /* must be zero */
+} x2c_options;
+
+typedef struct {
+  int32_t n;                       /* number of scalar basis functions */
+  const double *S, *T, *V, *W0;    /* n x n symmetric */
+  const double *Wx, *Wy, *Wz;      /* n x n antisymmetric; NULL when spin-free */
+} x2c_mats;
+
+typedef struct {
+  double *h[4];    /* h0 (n x n), then h1, h2, h3 for two-component (NULL if spin-free) */
+} x2c_hout;
+
+typedef struct {
+  double *UL[4];   /* U^L components (quaternion form, as h); UL[0] only if spin-free */
+  double *US[4];   /* U^S components */
+} x2c_uout;
+
+typedef struct {
+  int32_t n_atoms;
+  const int32_t *atom_offset;  /* HOST array, n_atoms + 1 entries: first function of each
+                                  atom, atom_offset[n_atoms] = n; atom-major basis order */
+  const int32_t *atom_kind;    /* HOST array, n_atoms entries: index into kinds */
+  int32_t n_kinds;
+  const x2c_mats *kinds;       /* HOST array of n_kinds free-atom input sets (device
+                                  matrices, sizes must match the atoms of that kind);
+                                  ignored in X2C_DLU_MOLECULAR_BLOCK mode */
+} x2c_layout;
+
+typedef struct x2c_ctx x2c_ctx;
+
+/* Create a context on CUDA device `device`.  Returns X2C_ERR_ARG for a bad device. */
+x2c_status x2c_ctx_create(int device, x2c_ctx **out);
+
+/* Destroy a context: waits for its work and frees its workspace.  NULL is allowed. */
+x2c_status x2c_ctx_destroy(x2c_ctx *ctx);
+
+/* Synchronise `stream`, return (and clear) the first device-side error latched since the
+ * last call, else X2C_OK. */
+x2c_status x2c_ctx_status(x2c_ctx *ctx, void *stream);
+
+/* Static description of a status code. */
+const char *x2c_status_string(x2c_status s);
+
+/* Text of the last CUDA error seen by this context (empty if none). */
+const char *x2c_last_error_message(x2c_ctx *ctx);
+
+/* Full X2C (Sec. II.A): h of the whole system, and optionally U^L, U^S (Eq. 22) for
+ * picture-change transformations (U may be NULL).  mol: device matrices.  Limits: n >= 1;
+ * the library keeps O(n^2) workspace (about 60 n^2 doubles spin-free, 200 n^2 two-component). */
+x2c_status x2c_build_full(x2c_ctx *ctx, const x2c_options *opt, const x2c_mats *mol,
+                          const x2c_hout *h, const x2c_uout *U, void *stream);
+
+/* DLU (Sec. III.A, Eqs. 42-43 with Eq. 8): h of the molecule from atomic transforms.
+ * mol: the molecular matrices; only the blocks the method needs are read (V, T, W0 on
+ * every pair block A <= B, the same-atom blocks of S, T, V, W for molecular-block mode, and
+ * Wx, Wy, Wz on same-atom blocks only when so_same_atom_only = 1).  Atoms may have any
+ * size >= 1; kinds must have the size of their atoms. */
+x2c_status x2c_build_dlu(x2c_ctx *ctx, const x2c_options *opt, const x2c_layout *layout,
+                         const x2c_mats *mol, const x2c_hout *h, void *stream);
+
+/* Batched DLU: n_mol independent molecules in one pass (one per-kind solve for the whole
+ * batch and one grouped pair-assembly launch over all molecules' pair blocks).
+ * layouts, mols, h: HOST arrays of n_mol entries. */
+x2c_status x2c_build_dlu_batched(x2c_ctx *ctx, const x2c_options *opt, int32_t n_mol,
+                                 const x2c_layout *layouts, const x2c_mats *mols,
+                                 const x2c_hout *h, void *stream);
+
+/* Atomic (or any) decoupling transforms U^L, U^S of n_problems independent input sets in
+ * one batched solve (the matrix function of Eq. 43).  inputs, U: HOST arrays. */
+x2c_status x2c_atomic_transforms(x2c_ctx *ctx, const x2c_options *opt, int32_t n_problems,
+                                 const x2c_mats *inputs, const x2c_uout *U, void *stream);
+
+/* DLU from HOST buffers (pageable or pinned): copies the inputs the method reads to the
+ * device, builds, and copies h back into the caller's host buffers, all on `stream`;
+ * returns after the stream has finished.  Arguments as x2c_build_dlu, but every matrix
+ * pointer (mol, kinds, h) is a host pointer. */
+x2c_status x2c_build_dlu_host(x2c_ctx *ctx, const x2c_options *opt, const x2c_layout *layout,
+                              const x2c_mats *mol, const x2c_hout *h, void *stream);
+
+/* Dense spin-blocked 2n x 2n complex matrix (interleaved re, im; row-major) from the
+ * quaternion parts h0..h3 (device).  out: device, 8 n^2 doubles. */
+x2c_status x2c_quaternion_to_dense(const double *const h[4], int32_t n, double *out,
+                                   void *stream);
+
+/* Counters of the last build on this context (for instrumentation and benchmarks). */
+typedef struct {
+  int64_t pair_blocks;       /* pair blocks assembled (A <= B) */
+  int64_t atomic_solves;     /* decoupling problems solved (kinds or atoms) */
+  int64_t kernel_launches;   /* kernels launched by the last call */
+  double credited_flops;     /* algorithmic FP64-equivalent flops of the last call */
+} x2c_counters;
+x2c_status x2c_ctx_counters(x2c_ctx *ctx, x2c_counters *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* X2C_H */

@@ -1,0 +1,268 @@
+"""GB300-native X2C / DLU relativistic one-electron Hamiltonian (sm_103a CUDA behind a C ABI).
+
+Python side: `x2c_*` functions with the names of include/x2c.h that marshal torch CUDA
+tensors into the library calls.  Every step of the computation runs in the CUDA library.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import abi
+from .abi import DLU_FREE_ATOM, DLU_MOLECULAR_BLOCK, PREC_FP64, PREC_SPLIT_BF16, X2CError  # noqa: F401
+
+C_LIGHT = 137.035999
+_MAT_KEYS = ("S", "T", "V", "W0", "Wx", "Wy", "Wz")
+
+
+def _torch():
+    import torch
+    return torch
+
+
+class Context:
+    """A library context on one CUDA device (x2c_ctx_create / x2c_ctx_destroy)."""
+
+    def __init__(self, device: int = 0):
+        self.lib = abi.load()
+        h = ctypes.c_void_p()
+        abi.check(self.lib.x2c_ctx_create(int(device), ctypes.byref(h)), "x2c_ctx_create")
+        self.handle = h
+        self.device = device
+
+    def close(self):
+        if self.handle:
+            self.lib.x2c_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def status(self, stream=None):
+        """x2c_ctx_status: synchronise the stream and raise on a latched device error."""
+        abi.check(self.lib.x2c_ctx_status(self.handle, _stream(stream)), "device status", self.handle)
+
+    def counters(self):
+        c = abi.Counters()
+        abi.check(self.lib.x2c_ctx_counters(self.handle, ctypes.byref(c)), "x2c_ctx_counters")
+        return dict(pair_blocks=c.pair_blocks, atomic_solves=c.atomic_solves,
+                    kernel_launches=c.kernel_launches, credited_flops=c.credited_flops)
+
+
+def _stream(stream):
+    if stream is None:
+        torch = _torch()
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def options(two_component=False, c=None, precision=PREC_FP64, dlu_potential=DLU_FREE_ATOM,
+            so_same_atom_only=True, n_slices=0) -> abi.Options:
+    o = abi.Options()
+    o.c = float(c) if c else C_LIGHT
+    o.two_component = int(bool(two_component))
+    o.precision = int(precision)
+    o.dlu_potential = int(dlu_potential)
+    o.so_same_atom_only = int(bool(so_same_atom_only))
+    o.n_slices = int(n_slices)
+    return o
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _check_tensor(t, n, device_expected=True):
+    torch = _torch()
+    if t is None:
+        return
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_contiguous():
+        raise ValueError("matrices must be contiguous float64 torch tensors")
+    if t.shape != (n, n):
+        raise ValueError(f"expected shape {(n, n)}, got {tuple(t.shape)}")
+    if device_expected and not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+
+
+def mats_struct(m: dict, two_component: bool) -> abi.Mats:
+    n = m["S"].shape[0]
+    s = abi.Mats()
+    s.n = n
+    for k in _MAT_KEYS:
+        t = m.get(k) if (two_component or k in ("S", "T", "V", "W0")) else None
+        _check_tensor(t, n)
+        setattr(s, k, _ptr(t).value if t is not None else None)
+    return s
+
+
+def _alloc_parts(n, nc, device, like=None):
+    torch = _torch()
+    return [torch.empty((n, n), dtype=torch.float64, device=device) for _ in range(nc)]
+
+
+def _hout(parts):
+    h = abi.HOut()
+    for q, t in enumerate(parts):
+        h.h[q] = t.data_ptr()
+    return h
+
+
+def x2c_build_full(ctx: Context, m: dict, two_component=False, c=None, want_U=False, stream=None):
+    """Full X2C: returns dict(h=[h0..], UL=[..], US=[..]) of CUDA tensors (quaternion parts)."""
+    nc = 4 if two_component else 1
+    ms = mats_struct(m, two_component)
+    dev = m["S"].device
+    h = _alloc_parts(ms.n, nc, dev)
+    U = None
+    out = dict(h=h)
+    if want_U:
+        UL, US = _alloc_parts(ms.n, nc, dev), _alloc_parts(ms.n, nc, dev)
+        U = abi.UOut()
+        for q in range(nc):
+            U.UL[q] = UL[q].data_ptr()
+            U.US[q] = US[q].data_ptr()
+        out.update(UL=UL, US=US)
+    o = options(two_component, c)
+    ho = _hout(h)
+    abi.check(ctx.lib.x2c_build_full(ctx.handle, ctypes.byref(o), ctypes.byref(ms), ctypes.byref(ho),
+                                     ctypes.byref(U) if U is not None else None, _stream(stream)),
+              "x2c_build_full", ctx.handle)
+    return out
+
+
+class LayoutHolder:
+    """Keeps the host arrays of an x2c_layout alive."""
+
+    def __init__(self, offsets, atom_kind=None, kinds=None, two_component=False):
+        self.off = np.ascontiguousarray(offsets, dtype=np.int32)
+        self.kind = None if atom_kind is None else np.ascontiguousarray(atom_kind, dtype=np.int32)
+        self.kinds = kinds or []
+        self.kind_structs = (abi.Mats * max(1, len(self.kinds)))()
+        for i, k in enumerate(self.kinds):
+            self.kind_structs[i] = mats_struct(k, two_component) if isinstance(k, dict) else k
+        self.s = abi.Layout()
+        self.s.n_atoms = len(self.off) - 1
+        self.s.atom_offset = self.off.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        self.s.atom_kind = (self.kind.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+                            if self.kind is not None else None)
+        self.s.n_kinds = len(self.kinds)
+        self.s.kinds = ctypes.cast(self.kind_structs, ctypes.POINTER(abi.Mats)) if self.kinds else None
+
+
+def x2c_build_dlu(ctx: Context, m: dict, offsets, atom_kind=None, kinds=None, two_component=False,
+                  c=None, precision=PREC_FP64, dlu_potential=DLU_FREE_ATOM, so_same_atom_only=True,
+                  n_slices=0, out=None, stream=None):
+    """DLU build.  m: molecular matrices (CUDA tensors); kinds: list of free-atom input dicts
+    (FREE_ATOM mode) indexed by atom_kind.  Returns the list of h parts."""
+    nc = 4 if two_component else 1
+    ms = mats_struct(m, two_component)
+    h = out if out is not None else _alloc_parts(ms.n, nc, m["S"].device)
+    lay = LayoutHolder(offsets, atom_kind, kinds, two_component)
+    o = options(two_component, c, precision, dlu_potential, so_same_atom_only, n_slices)
+    ho = _hout(h)
+    abi.check(ctx.lib.x2c_build_dlu(ctx.handle, ctypes.byref(o), ctypes.byref(lay.s), ctypes.byref(ms),
+                                    ctypes.byref(ho), _stream(stream)), "x2c_build_dlu", ctx.handle)
+    return h
+
+
+def x2c_build_dlu_batched(ctx: Context, mols: list, layouts: list, two_component=False, c=None,
+                          precision=PREC_FP64, dlu_potential=DLU_FREE_ATOM, so_same_atom_only=True,
+                          n_slices=0, outs=None, stream=None):
+    """Batched DLU over several molecules.  mols: list of matrix dicts; layouts: list of
+    (offsets, atom_kind, kinds) tuples.  Returns a list of h-part lists."""
+    nc = 4 if two_component else 1
+    n_mol = len(mols)
+    ms = (abi.Mats * n_mol)()
+    ls = (abi.Layout * n_mol)()
+    hs = (abi.HOut * n_mol)()
+    holders, outs_ = [], []
+    for i, (m, lay) in enumerate(zip(mols, layouts)):
+        ms[i] = mats_struct(m, two_component)
+        holder = LayoutHolder(*lay, two_component=two_component)
+        holders.append(holder)
+        ls[i] = holder.s
+        h = outs[i] if outs is not None else _alloc_parts(ms[i].n, nc, m["S"].device)
+        outs_.append(h)
+        hs[i] = _hout(h)
+    o = options(two_component, c, precision, dlu_potential, so_same_atom_only, n_slices)
+    abi.check(ctx.lib.x2c_build_dlu_batched(ctx.handle, ctypes.byref(o), n_mol, ls, ms, hs, _stream(stream)),
+              "x2c_build_dlu_batched", ctx.handle)
+    return outs_
+
+
+def x2c_atomic_transforms(ctx: Context, inputs: list, two_component=False, c=None, stream=None):
+    """Decoupling transforms of independent input sets: list of (UL parts, US parts)."""
+    nc = 4 if two_component else 1
+    k = len(inputs)
+    ms = (abi.Mats * k)()
+    us = (abi.UOut * k)()
+    res = []
+    for i, m in enumerate(inputs):
+        ms[i] = mats_struct(m, two_component)
+        UL, US = _alloc_parts(ms[i].n, nc, m["S"].device), _alloc_parts(ms[i].n, nc, m["S"].device)
+        for q in range(nc):
+            us[i].UL[q] = UL[q].data_ptr()
+            us[i].US[q] = US[q].data_ptr()
+        res.append((UL, US))
+    o = options(two_component, c)
+    abi.check(ctx.lib.x2c_atomic_transforms(ctx.handle, ctypes.byref(o), k, ms, us, _stream(stream)),
+              "x2c_atomic_transforms", ctx.handle)
+    return res
+
+
+def x2c_build_dlu_host(ctx: Context, m: dict, offsets, atom_kind=None, kinds=None, two_component=False,
+                       c=None, precision=PREC_FP64, dlu_potential=DLU_FREE_ATOM, so_same_atom_only=True,
+                       n_slices=0, out=None, stream=None):
+    """DLU build from HOST arrays (numpy float64 or CPU torch tensors, pinned or not);
+    h parts are written into `out` (host arrays) or new numpy arrays."""
+    nc = 4 if two_component else 1
+    n = m["S"].shape[0]
+
+    def hp(a):
+        if a is None:
+            return None
+        if isinstance(a, np.ndarray):
+            if a.dtype != np.float64 or not a.flags.c_contiguous:
+                raise ValueError("host matrices must be C-contiguous float64")
+            return a.ctypes.data
+        return a.data_ptr()
+
+    def hmats(d, nn):
+        s = abi.Mats()
+        s.n = nn
+        for k in _MAT_KEYS:
+            t = d.get(k) if (two_component or k in ("S", "T", "V", "W0")) else None
+            setattr(s, k, hp(t))
+        return s
+
+    ms = hmats(m, n)
+    kind_structs = [hmats(k, k["S"].shape[0]) for k in (kinds or [])]
+    lay = LayoutHolder(offsets, atom_kind, kind_structs, two_component)
+    if out is None:
+        out = [np.empty((n, n)) for _ in range(nc)]
+    ho = abi.HOut()
+    for q in range(nc):
+        ho.h[q] = hp(out[q])
+    o = options(two_component, c, precision, dlu_potential, so_same_atom_only, n_slices)
+    abi.check(ctx.lib.x2c_build_dlu_host(ctx.handle, ctypes.byref(o), ctypes.byref(lay.s), ctypes.byref(ms),
+                                         ctypes.byref(ho), _stream(stream)), "x2c_build_dlu_host", ctx.handle)
+    return out
+
+
+def x2c_quaternion_to_dense(h_parts: list, stream=None):
+    """Dense spin-blocked complex 2n x 2n matrix (complex128 CUDA tensor) from h parts."""
+    torch = _torch()
+    n = h_parts[0].shape[0]
+    out = torch.empty((2 * n, 2 * n), dtype=torch.complex128, device=h_parts[0].device)
+    arr = (ctypes.c_void_p * 4)(*[(h_parts[q].data_ptr() if q < len(h_parts) else None) for q in range(4)])
+    abi.check(abi.load().x2c_quaternion_to_dense(arr, n, ctypes.c_void_p(out.data_ptr()), _stream(stream)),
+              "x2c_quaternion_to_dense")
+    return out

@@ -1,0 +1,122 @@
+"""Thin ctypes binding of include/x2c.h (argument marshalling only).
+
+Every computation happens in libx2c_gb300.so; torch tensors only provide device memory
+and streams.  The functions keep the C names (x2c_build_full, x2c_build_dlu, ...).
+Loading fails loudly when the library is missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+X2C_OK = 0
+STATUS_NAMES = {0: "X2C_OK", 1: "X2C_ERR_ARG", 2: "X2C_ERR_NOMEM", 3: "X2C_ERR_CUDA",
+                4: "X2C_ERR_NOT_POSDEF", 5: "X2C_ERR_NOCONV", 6: "X2C_ERR_DECOUPLING",
+                7: "X2C_ERR_NONFINITE", 8: "X2C_ERR_ADMISSION", 9: "X2C_ERR_TIMEOUT",
+                10: "X2C_ERR_CANCELLED", 11: "X2C_ERR_NOT_FOUND"}
+PREC_FP64, PREC_SPLIT_BF16 = 0, 1
+DLU_FREE_ATOM, DLU_MOLECULAR_BLOCK = 0, 1
+
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("c", ctypes.c_double), ("two_component", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("dlu_potential", ctypes.c_int32),
+                ("so_same_atom_only", ctypes.c_int32), ("n_slices", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
+
+
+class Mats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("S", ctypes.c_void_p), ("T", ctypes.c_void_p),
+                ("V", ctypes.c_void_p), ("W0", ctypes.c_void_p), ("Wx", ctypes.c_void_p),
+                ("Wy", ctypes.c_void_p), ("Wz", ctypes.c_void_p)]
+
+
+class HOut(ctypes.Structure):
+    _fields_ = [("h", ctypes.c_void_p * 4)]
+
+
+class UOut(ctypes.Structure):
+    _fields_ = [("UL", ctypes.c_void_p * 4), ("US", ctypes.c_void_p * 4)]
+
+
+class Layout(ctypes.Structure):
+    _fields_ = [("n_atoms", ctypes.c_int32), ("atom_offset", ctypes.POINTER(ctypes.c_int32)),
+                ("atom_kind", ctypes.POINTER(ctypes.c_int32)), ("n_kinds", ctypes.c_int32),
+                ("kinds", ctypes.POINTER(Mats))]
+
+
+class Counters(ctypes.Structure):
+    _fields_ = [("pair_blocks", ctypes.c_int64), ("atomic_solves", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64), ("credited_flops", ctypes.c_double)]
+
+
+_LIB = None
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "x2c_ctx_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
+    "x2c_ctx_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "x2c_ctx_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "x2c_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "x2c_last_error_message": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "x2c_build_full": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Options), ctypes.POINTER(Mats),
+                                      ctypes.POINTER(HOut), ctypes.POINTER(UOut), ctypes.c_void_p]),
+    "x2c_build_dlu": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Options), ctypes.POINTER(Layout),
+                                     ctypes.POINTER(Mats), ctypes.POINTER(HOut), ctypes.c_void_p]),
+    "x2c_build_dlu_batched": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Options), ctypes.c_int32,
+                                             ctypes.POINTER(Layout), ctypes.POINTER(Mats),
+                                             ctypes.POINTER(HOut), ctypes.c_void_p]),
+    "x2c_atomic_transforms": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Options), ctypes.c_int32,
+                                             ctypes.POINTER(Mats), ctypes.POINTER(UOut), ctypes.c_void_p]),
+    "x2c_build_dlu_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Options), ctypes.POINTER(Layout),
+                                          ctypes.POINTER(Mats), ctypes.POINTER(HOut), ctypes.c_void_p]),
+    "x2c_quaternion_to_dense": (ctypes.c_int, [ctypes.c_void_p * 4, ctypes.c_int32, ctypes.c_void_p,
+                                               ctypes.c_void_p]),
+    "x2c_ctx_counters": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Counters)]),
+}
+
+
+def exported_symbols():
+    """Every function name declared in include/x2c.h that the binding exposes."""
+    return sorted(_SIGS)
+
+
+def lib_path() -> str:
+    return _build.LIB_PATH
+
+
+def load(build_if_missing: bool = True):
+    """Load libx2c_gb300.so (building it first if asked); raise if it is unavailable."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.LIB_PATH
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"CUDA library not built: {path}")
+        _build.build_library()
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+class X2CError(RuntimeError):
+    def __init__(self, code, where, detail=""):
+        self.code = code
+        super().__init__(f"{where}: {STATUS_NAMES.get(code, code)} {detail}".strip())
+
+
+def check(code, where, ctx=None):
+    if code != X2C_OK:
+        detail = ""
+        if ctx is not None and code == 3:
+            detail = load().x2c_last_error_message(ctx).decode()
+        raise X2CError(code, where, detail)

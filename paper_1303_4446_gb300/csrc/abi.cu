@@ -1,0 +1,444 @@
+// extern "C" entry points of the X2C library (include/x2c.h).
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <tuple>
+
+#include "common.cuh"
+
+namespace x2c {
+
+x2c_status ensure_workspace(x2c_ctx *ctx, size_t bytes, Arena *out) {
+  if (bytes > ctx->ws_bytes) {
+    X2C_TRY_CUDA(ctx, cudaDeviceSynchronize());
+    if (ctx->ws) cudaFree(ctx->ws);
+    ctx->ws = nullptr;
+    ctx->ws_bytes = 0;
+    const size_t want = bytes + bytes / 8;
+    cudaError_t e = cudaMalloc(&ctx->ws, want);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      ctx->last_error = std::string("workspace allocation: ") + cudaGetErrorString(e);
+      return X2C_ERR_NOMEM;
+    }
+    ctx->ws_bytes = want;
+  }
+  out->base = ctx->ws;
+  out->cap = ctx->ws_bytes;
+  out->off = 0;
+  return X2C_OK;
+}
+
+namespace {
+
+bool mats_ok(const x2c_mats *m, int nc) {
+  if (!m || m->n < 1 || !m->S || !m->T || !m->V || !m->W0) return false;
+  if (nc == 4 && (!m->Wx || !m->Wy || !m->Wz)) return false;
+  return true;
+}
+
+x2c_status check_options(const x2c_options *o) {
+  if (!o) return X2C_ERR_ARG;
+  if (o->two_component != 0 && o->two_component != 1) return X2C_ERR_ARG;
+  if (o->precision != X2C_PREC_FP64 && o->precision != X2C_PREC_SPLIT_BF16) return X2C_ERR_ARG;
+  if (o->dlu_potential != X2C_DLU_FREE_ATOM && o->dlu_potential != X2C_DLU_MOLECULAR_BLOCK) return X2C_ERR_ARG;
+  if (o->n_slices < 0 || o->n_slices > 8) return X2C_ERR_ARG;
+  for (int r : o->reserved)
+    if (r != 0) return X2C_ERR_ARG;
+  return X2C_OK;
+}
+
+double credited_pair_flops(int nA, int nB, int nc, bool diag, bool so) {
+  const double a = nA, b = nB;
+  if (nc == 1) return 2.0 * (4.0 * a * b * b + 2.0 * a * a * b);
+  double f = 2.0 * (16.0 * a * b * b + 32.0 * a * a * b);
+  if (diag || so) f += 24.0 * a * b * b;
+  return f;
+}
+
+// Conventional counts of the paper's operation list (Tables II and III) for one
+// decoupling problem of size n: eigen 9 m^3, inversion 2 m^3, product 2 m^3, complex x4.
+double credited_solve_flops(int n, int nc) {
+  const double N3 = (double)n * n * n;
+  if (nc == 1) return (2 * 9 + 9 * 8 + 2 * 2 + 15 * 2) * N3;
+  return (9 + 4 * 9 * 8 + 4 * 9 * 64 + 2 + 4 * 2 * 8 + 10 * 2 + 11 * 4 * 2 * 8) * N3;
+}
+
+struct Problem {
+  InputDesc in;
+  int n;
+};
+
+// One logical build: a set of decoupling problems (grouped by size), a U table indexed by
+// problem, molecules and their pair list.
+struct BuildPlan {
+  std::vector<Problem> problems;
+  std::vector<MolDesc> mols;
+  std::vector<PairDesc> pairs;
+  int nc = 1;
+  int max_n = 0;
+  double credited = 0;
+};
+
+x2c_status run_plan(x2c_ctx *ctx, const x2c_options *opt, BuildPlan &plan, cudaStream_t st,
+                    std::vector<double *> *UL_out = nullptr, std::vector<double *> *US_out = nullptr) {
+  const double c = speed_of_light(opt);
+  const int nc = plan.nc;
+  // group problems by size
+  std::map<int, std::vector<int>> groups;
+  for (size_t i = 0; i < plan.problems.size(); ++i) groups[plan.problems[i].n].push_back((int)i);
+  size_t u_doubles = 0, solve_ws = 0, desc_bytes = 0;
+  for (auto &g : groups) {
+    const size_t n2 = (size_t)g.first * g.first;
+    u_doubles += 2 * g.second.size() * nc * n2;
+    solve_ws = std::max(solve_ws, solve_workspace_bytes((int)g.second.size(), g.first, nc));
+    desc_bytes += ((g.second.size() * sizeof(InputDesc) + 255) / 256) * 256;
+  }
+  const size_t np = plan.problems.size();
+  const size_t table_bytes = 2 * (((np * sizeof(double *) + 255) / 256) * 256);
+  const size_t mol_bytes = ((plan.mols.size() * sizeof(MolDesc) + 255) / 256) * 256;
+  const size_t asm_ws = assemble_workspace_bytes(plan.pairs, nc, plan.max_n, opt->precision);
+  const size_t total = arena_doubles(u_doubles) + desc_bytes + table_bytes + mol_bytes +
+                       std::max(solve_ws, asm_ws) + 8192;
+  Arena ar;
+  X2C_TRY(ensure_workspace(ctx, total, &ar));
+  double *Ustore = ar.take(u_doubles);
+  double **dUL = reinterpret_cast<double **>(ar.take_bytes(np * sizeof(double *)));
+  double **dUS = reinterpret_cast<double **>(ar.take_bytes(np * sizeof(double *)));
+  MolDesc *dmols = reinterpret_cast<MolDesc *>(ar.take_bytes(std::max<size_t>(1, plan.mols.size()) * sizeof(MolDesc)));
+  if (!Ustore || !dUL || !dUS || !dmols) return X2C_ERR_NOMEM;
+  std::vector<double *> hUL(np), hUS(np);
+  // solve each size group
+  size_t uoff = 0;
+  std::vector<InputDesc *> ddescs;
+  for (auto &g : groups) {
+    const int n = g.first, nb = (int)g.second.size();
+    const size_t n2 = (size_t)n * n;
+    double *UL = Ustore + uoff;
+    double *US = UL + (size_t)nb * nc * n2;
+    uoff += 2 * (size_t)nb * nc * n2;
+    std::vector<InputDesc> hd(nb);
+    for (int i = 0; i < nb; ++i) {
+      hd[i] = plan.problems[g.second[i]].in;
+      hUL[g.second[i]] = UL + (size_t)i * nc * n2;
+      hUS[g.second[i]] = US + (size_t)i * nc * n2;
+    }
+    InputDesc *dd = reinterpret_cast<InputDesc *>(ar.take_bytes(nb * sizeof(InputDesc)));
+    if (!dd) return X2C_ERR_NOMEM;
+    X2C_TRY_CUDA(ctx, cudaMemcpyAsync(dd, hd.data(), nb * sizeof(InputDesc), cudaMemcpyHostToDevice, st));
+    ddescs.push_back(dd);
+    plan.credited += nb * credited_solve_flops(n, nc);
+  }
+  // solves share the scratch region that follows (assembly reuses it afterwards)
+  {
+    size_t gi = 0, uo = 0;
+    for (auto &g : groups) {
+      const int n = g.first, nb = (int)g.second.size();
+      const size_t n2 = (size_t)n * n;
+      double *UL = Ustore + uo;
+      double *US = UL + (size_t)nb * nc * n2;
+      uo += 2 * (size_t)nb * nc * n2;
+      Arena scratch = ar;
+      X2C_TRY(solve_transforms(ctx, st, c, nb, n, nc, ddescs[gi++], UL, US, scratch));
+    }
+  }
+  ctx->counters.atomic_solves = (int64_t)np;
+  if (UL_out) *UL_out = hUL;
+  if (US_out) *US_out = hUS;
+  if (plan.pairs.empty()) return X2C_OK;
+  X2C_TRY_CUDA(ctx, cudaMemcpyAsync(dUL, hUL.data(), np * sizeof(double *), cudaMemcpyHostToDevice, st));
+  X2C_TRY_CUDA(ctx, cudaMemcpyAsync(dUS, hUS.data(), np * sizeof(double *), cudaMemcpyHostToDevice, st));
+  X2C_TRY_CUDA(ctx, cudaMemcpyAsync(dmols, plan.mols.data(), plan.mols.size() * sizeof(MolDesc),
+                                    cudaMemcpyHostToDevice, st));
+  UTable ut{dUL, dUS};
+  const int so_all = (nc == 4 && !opt->so_same_atom_only) ? 1 : 0;
+  for (const auto &P : plan.pairs) plan.credited += credited_pair_flops(P.nA, P.nB, nc, P.diag, so_all);
+  ctx->counters.pair_blocks = (int64_t)plan.pairs.size();
+  if (opt->precision == X2C_PREC_SPLIT_BF16) {
+    const int slices = opt->n_slices ? opt->n_slices : 5;
+    return assemble_pairs_split(ctx, st, c, nc, so_all, plan.pairs, dmols, ut, plan.max_n, slices, ar);
+  }
+  return assemble_pairs_fp64(ctx, st, c, nc, so_all, plan.pairs, dmols, ut, plan.max_n, ar);
+}
+
+MolDesc mol_desc(const x2c_mats *m, const x2c_hout *h, int nc) {
+  MolDesc d{};
+  d.V = m->V;
+  d.T = m->T;
+  d.W0 = m->W0;
+  if (nc == 4) {
+    d.W[0] = m->Wx;
+    d.W[1] = m->Wy;
+    d.W[2] = m->Wz;
+  }
+  for (int q = 0; q < nc; ++q) d.h[q] = h->h[q];
+  d.ld = m->n;
+  return d;
+}
+
+InputDesc input_desc(const x2c_mats *m, int nc, int64_t off, int64_t ld) {
+  InputDesc d{};
+  const int64_t o = off * ld + off;
+  d.S = m->S + o;
+  d.T = m->T + o;
+  d.V = m->V + o;
+  d.W[0] = m->W0 + o;
+  if (nc == 4) {
+    d.W[1] = m->Wx + o;
+    d.W[2] = m->Wy + o;
+    d.W[3] = m->Wz + o;
+  }
+  d.ld = ld;
+  return d;
+}
+
+// Add one molecule's problems (molecular-block mode) or kind references and its pairs.
+x2c_status add_molecule(BuildPlan &plan, const x2c_options *opt, const x2c_layout *lay,
+                        const x2c_mats *mol, const x2c_hout *h, int mol_index,
+                        std::map<std::tuple<const double *, const double *, const double *, const double *,
+                                            const double *>, int> &kind_index) {
+  const int nc = plan.nc;
+  if (!lay || lay->n_atoms < 1 || !lay->atom_offset || !mats_ok(mol, nc) || !h) return X2C_ERR_ARG;
+  for (int q = 0; q < nc; ++q)
+    if (!h->h[q]) return X2C_ERR_ARG;
+  const int L = lay->n_atoms;
+  if (lay->atom_offset[0] != 0 || lay->atom_offset[L] != mol->n) return X2C_ERR_ARG;
+  for (int a = 0; a < L; ++a)
+    if (lay->atom_offset[a + 1] <= lay->atom_offset[a]) return X2C_ERR_ARG;
+  std::vector<int> uidx(L);
+  if (opt->dlu_potential == X2C_DLU_MOLECULAR_BLOCK) {
+    for (int a = 0; a < L; ++a) {
+      const int n = lay->atom_offset[a + 1] - lay->atom_offset[a];
+      if (n > kMaxSolveN) return X2C_ERR_ARG;
+      uidx[a] = (int)plan.problems.size();
+      plan.problems.push_back({input_desc(mol, nc, lay->atom_offset[a], mol->n), n});
+    }
+  } else {
+    if (!lay->atom_kind || lay->n_kinds < 1 || !lay->kinds) return X2C_ERR_ARG;
+    for (int a = 0; a < L; ++a) {
+      const int k = lay->atom_kind[a];
+      if (k < 0 || k >= lay->n_kinds) return X2C_ERR_ARG;
+      const x2c_mats *km = &lay->kinds[k];
+      const int n = lay->atom_offset[a + 1] - lay->atom_offset[a];
+      if (!mats_ok(km, nc) || km->n != n || n > kMaxSolveN) return X2C_ERR_ARG;
+      auto key = std::make_tuple(km->S, km->T, km->V, km->W0, nc == 4 ? km->Wx : nullptr);
+      auto it = kind_index.find(key);
+      if (it == kind_index.end()) {
+        const int id = (int)plan.problems.size();
+        plan.problems.push_back({input_desc(km, nc, 0, n), n});
+        it = kind_index.emplace(key, id).first;
+      }
+      uidx[a] = it->second;
+    }
+  }
+  plan.mols.push_back(mol_desc(mol, h, nc));
+  for (int A = 0; A < L; ++A) {
+    const int nA = lay->atom_offset[A + 1] - lay->atom_offset[A];
+    plan.max_n = std::max(plan.max_n, nA);
+    for (int B = A; B < L; ++B) {
+      PairDesc P{};
+      P.offA = lay->atom_offset[A];
+      P.offB = lay->atom_offset[B];
+      P.nA = nA;
+      P.nB = lay->atom_offset[B + 1] - lay->atom_offset[B];
+      P.uA = uidx[A];
+      P.uB = uidx[B];
+      P.mol = mol_index;
+      P.diag = (A == B);
+      plan.pairs.push_back(P);
+    }
+  }
+  return X2C_OK;
+}
+
+__global__ void quat_to_dense_kernel(const double *h0, const double *h1, const double *h2,
+                                     const double *h3, int n, double *out) {
+  const int64_t N = n;
+  const int64_t total = N * N;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx / N, j = idx % N;
+    const double a = h0[idx], x = h1 ? h1[idx] : 0.0, y = h2 ? h2[idx] : 0.0, z = h3 ? h3[idx] : 0.0;
+    const int64_t ld = 2 * N;  // complex elements per row
+    double *o = out;
+    // [[h0 + i h3, h2 + i h1], [-h2 + i h1, h0 - i h3]]
+    o[2 * (i * ld + j)] = a;              o[2 * (i * ld + j) + 1] = z;
+    o[2 * (i * ld + N + j)] = y;          o[2 * (i * ld + N + j) + 1] = x;
+    o[2 * ((N + i) * ld + j)] = -y;       o[2 * ((N + i) * ld + j) + 1] = x;
+    o[2 * ((N + i) * ld + N + j)] = a;    o[2 * ((N + i) * ld + N + j) + 1] = -z;
+  }
+}
+
+x2c_status begin_call(x2c_ctx *ctx) {
+  if (!ctx) return X2C_ERR_ARG;
+  ctx->launches = 0;
+  X2C_TRY_CUDA(ctx, cudaSetDevice(ctx->device));
+  return X2C_OK;
+}
+
+void end_call(x2c_ctx *ctx, const BuildPlan &plan) {
+  ctx->counters.kernel_launches = ctx->launches;
+  ctx->counters.credited_flops = plan.credited;
+}
+
+}  // namespace
+}  // namespace x2c
+
+using namespace x2c;
+
+extern "C" {
+
+const char *x2c_status_string(x2c_status s) {
+  switch (s) {
+    case X2C_OK: return "ok";
+    case X2C_ERR_ARG: return "invalid argument";
+    case X2C_ERR_NOMEM: return "out of memory";
+    case X2C_ERR_CUDA: return "CUDA error";
+    case X2C_ERR_NOT_POSDEF: return "S or T is not positive definite";
+    case X2C_ERR_NOCONV: return "iteration did not converge";
+    case X2C_ERR_DECOUPLING: return "positive/negative energy spectrum does not split at -c^2";
+    case X2C_ERR_NONFINITE: return "non-finite value";
+    case X2C_ERR_ADMISSION: return "request exceeds the memory budget";
+    case X2C_ERR_TIMEOUT: return "timed out";
+    case X2C_ERR_CANCELLED: return "cancelled";
+    case X2C_ERR_NOT_FOUND: return "unknown ticket";
+  }
+  return "unknown status";
+}
+
+x2c_status x2c_ctx_create(int device, x2c_ctx **out) {
+  if (!out) return X2C_ERR_ARG;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+    cudaGetLastError();
+    return X2C_ERR_ARG;
+  }
+  x2c_ctx *ctx = new x2c_ctx();
+  ctx->device = device;
+  if (cudaSetDevice(device) != cudaSuccess || cudaMalloc(&ctx->d_status, sizeof(int)) != cudaSuccess ||
+      cudaMemset(ctx->d_status, 0, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    delete ctx;
+    return X2C_ERR_CUDA;
+  }
+  *out = ctx;
+  return X2C_OK;
+}
+
+x2c_status x2c_ctx_destroy(x2c_ctx *ctx) {
+  if (!ctx) return X2C_OK;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  if (ctx->ws) cudaFree(ctx->ws);
+  if (ctx->stage) cudaFree(ctx->stage);
+  if (ctx->d_status) cudaFree(ctx->d_status);
+  delete ctx;
+  return X2C_OK;
+}
+
+const char *x2c_last_error_message(x2c_ctx *ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+x2c_status x2c_ctx_status(x2c_ctx *ctx, void *stream) {
+  if (!ctx) return X2C_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  X2C_TRY_CUDA(ctx, cudaSetDevice(ctx->device));
+  X2C_TRY_CUDA(ctx, cudaStreamSynchronize(st));
+  int code = 0;
+  X2C_TRY_CUDA(ctx, cudaMemcpy(&code, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (code) X2C_TRY_CUDA(ctx, cudaMemset(ctx->d_status, 0, sizeof(int)));
+  return static_cast<x2c_status>(code);
+}
+
+x2c_status x2c_ctx_counters(x2c_ctx *ctx, x2c_counters *out) {
+  if (!ctx || !out) return X2C_ERR_ARG;
+  *out = ctx->counters;
+  return X2C_OK;
+}
+
+x2c_status x2c_build_full(x2c_ctx *ctx, const x2c_options *opt, const x2c_mats *mol,
+                          const x2c_hout *h, const x2c_uout *U, void *stream) {
+  X2C_TRY(begin_call(ctx));
+  X2C_TRY(check_options(opt));
+  const int nc = opt->two_component ? 4 : 1;
+  if (!mats_ok(mol, nc) || !h) return X2C_ERR_ARG;
+  if (mol->n > kMaxSolveN) return X2C_ERR_ARG;
+  x2c_options o = *opt;
+  o.dlu_potential = X2C_DLU_MOLECULAR_BLOCK;
+  o.precision = X2C_PREC_FP64;
+  o.so_same_atom_only = 1;  // one atom: the only pair is the diagonal one
+  int32_t offs[2] = {0, mol->n};
+  x2c_layout lay{1, offs, nullptr, 0, nullptr};
+  BuildPlan plan;
+  plan.nc = nc;
+  std::map<std::tuple<const double *, const double *, const double *, const double *, const double *>, int> kinds;
+  X2C_TRY(add_molecule(plan, &o, &lay, mol, h, 0, kinds));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  std::vector<double *> ULp, USp;
+  X2C_TRY(run_plan(ctx, &o, plan, st, &ULp, &USp));
+  if (U) {
+    const size_t n2 = (size_t)mol->n * mol->n;
+    for (int q = 0; q < nc; ++q) {
+      if (U->UL[q]) X2C_TRY_CUDA(ctx, cudaMemcpyAsync(U->UL[q], ULp[0] + q * n2, n2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      if (U->US[q]) X2C_TRY_CUDA(ctx, cudaMemcpyAsync(U->US[q], USp[0] + q * n2, n2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    }
+  }
+  end_call(ctx, plan);
+  return X2C_OK;
+}
+
+x2c_status x2c_build_dlu(x2c_ctx *ctx, const x2c_options *opt, const x2c_layout *layout,
+                         const x2c_mats *mol, const x2c_hout *h, void *stream) {
+  return x2c_build_dlu_batched(ctx, opt, 1, layout, mol, h, stream);
+}
+
+x2c_status x2c_build_dlu_batched(x2c_ctx *ctx, const x2c_options *opt, int32_t n_mol,
+                                 const x2c_layout *layouts, const x2c_mats *mols,
+                                 const x2c_hout *h, void *stream) {
+  X2C_TRY(begin_call(ctx));
+  X2C_TRY(check_options(opt));
+  if (n_mol < 1 || !layouts || !mols || !h) return X2C_ERR_ARG;
+  BuildPlan plan;
+  plan.nc = opt->two_component ? 4 : 1;
+  std::map<std::tuple<const double *, const double *, const double *, const double *, const double *>, int> kinds;
+  for (int i = 0; i < n_mol; ++i) X2C_TRY(add_molecule(plan, opt, &layouts[i], &mols[i], &h[i], i, kinds));
+  X2C_TRY(run_plan(ctx, opt, plan, static_cast<cudaStream_t>(stream)));
+  end_call(ctx, plan);
+  return X2C_OK;
+}
+
+x2c_status x2c_atomic_transforms(x2c_ctx *ctx, const x2c_options *opt, int32_t n_problems,
+                                 const x2c_mats *inputs, const x2c_uout *U, void *stream) {
+  X2C_TRY(begin_call(ctx));
+  X2C_TRY(check_options(opt));
+  if (n_problems < 1 || !inputs || !U) return X2C_ERR_ARG;
+  BuildPlan plan;
+  plan.nc = opt->two_component ? 4 : 1;
+  for (int i = 0; i < n_problems; ++i) {
+    if (!mats_ok(&inputs[i], plan.nc) || inputs[i].n > kMaxSolveN) return X2C_ERR_ARG;
+    plan.problems.push_back({input_desc(&inputs[i], plan.nc, 0, inputs[i].n), inputs[i].n});
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  std::vector<double *> ULp, USp;
+  X2C_TRY(run_plan(ctx, opt, plan, st, &ULp, &USp));
+  for (int i = 0; i < n_problems; ++i) {
+    const size_t n2 = (size_t)inputs[i].n * inputs[i].n;
+    for (int q = 0; q < plan.nc; ++q) {
+      if (!U[i].UL[q] || !U[i].US[q]) return X2C_ERR_ARG;
+      X2C_TRY_CUDA(ctx, cudaMemcpyAsync(U[i].UL[q], ULp[i] + q * n2, n2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      X2C_TRY_CUDA(ctx, cudaMemcpyAsync(U[i].US[q], USp[i] + q * n2, n2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    }
+  }
+  end_call(ctx, plan);
+  return X2C_OK;
+}
+
+x2c_status x2c_quaternion_to_dense(const double *const h[4], int32_t n, double *out, void *stream) {
+  if (!h || !h[0] || n < 1 || !out) return X2C_ERR_ARG;
+  const int64_t total = (int64_t)n * n;
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+  quat_to_dense_kernel<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(h[0], h[1], h[2], h[3], n, out);
+  return cudaGetLastError() == cudaSuccess ? X2C_OK : X2C_ERR_CUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,153 @@
+// Internal definitions shared by the CUDA translation units of the X2C library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/x2c.h"
+
+// Device-side error codes latched in the context's status word (same values as x2c_status).
+#define X2C_DEV_NOT_POSDEF 4
+#define X2C_DEV_NOCONV 5
+#define X2C_DEV_DECOUPLING 6
+#define X2C_DEV_NONFINITE 7
+
+struct x2c_ctx {
+  int device = 0;
+  int *d_status = nullptr;      // first device-side error code (0 = none)
+  char *ws = nullptr;           // growable device workspace
+  size_t ws_bytes = 0;
+  char *stage = nullptr;        // growable device staging area of the host-buffer calls
+  size_t stage_bytes = 0;
+  std::string last_error;
+  x2c_counters counters{};
+  int64_t launches = 0;         // kernels launched by the current call
+};
+
+namespace x2c {
+
+constexpr double kDefaultC = 137.035999;
+
+inline double speed_of_light(const x2c_options *o) { return (o && o->c > 0) ? o->c : kDefaultC; }
+
+// Record a CUDA error in the context and return X2C_ERR_CUDA.
+inline x2c_status cuda_fail(x2c_ctx *ctx, cudaError_t e, const char *what) {
+  if (ctx) {
+    ctx->last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  }
+  return X2C_ERR_CUDA;
+}
+
+#define X2C_TRY_CUDA(ctx, call)                                  \
+  do {                                                           \
+    cudaError_t e__ = (call);                                    \
+    if (e__ != cudaSuccess) return x2c::cuda_fail(ctx, e__, #call); \
+  } while (0)
+
+#define X2C_TRY(expr)                 \
+  do {                                \
+    x2c_status s__ = (expr);          \
+    if (s__ != X2C_OK) return s__;    \
+  } while (0)
+
+// Check the launch that was just enqueued and count it.
+inline x2c_status launched(x2c_ctx *ctx, const char *name) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, name);
+  ctx->launches++;
+  return X2C_OK;
+}
+
+__device__ __forceinline__ void flag_error(int *st, int code) { atomicCAS(st, 0, code); }
+
+// ---------------------------------------------------------------------------------------
+// Quaternion (time-reversal) algebra of Eq. 5.  A two-component matrix
+//   M = I2 (x) M0 + i sum_k sigma_k (x) Mk
+// is stored as its four real parts M0..M3 (component-major).  With the Pauli product
+// sigma_k sigma_j = delta_kj + i eps_kjl sigma_l, the product C = A B has
+//   C0 = A0 B0 - sum_k Ak Bk
+//   Cl = A0 Bl + Al B0 - sum_kj eps_kjl Ak Bj
+// i.e. stack(C) = Lq(A) stack(B) with the 4 x 4 block matrix Lq(A) whose block (p, q) is
+// sign(p, q) * A_{p xor q}; the negative blocks are (0,1) (0,2) (0,3) (1,3) (2,1) (3,2).
+// The adjoint A+ has parts (A0^T, -A1^T, -A2^T, -A3^T).
+__host__ __device__ __forceinline__ double quat_sign(int p, int q) {
+  constexpr unsigned kNeg = (1u << 1) | (1u << 2) | (1u << 3) | (1u << 7) | (1u << 9) | (1u << 14);
+  return ((kNeg >> (p * 4 + q)) & 1u) ? -1.0 : 1.0;
+}
+// Block (p, q) of Lq(A+): sign * A_{p xor q}^T with the adjoint's extra minus on parts 1-3.
+__host__ __device__ __forceinline__ double quat_sign_adj(int p, int q) {
+  return ((p ^ q) == 0) ? quat_sign(p, q) : -quat_sign(p, q);
+}
+
+// Workspace bump allocator for one library call (256-byte aligned slices).
+struct Arena {
+  char *base = nullptr;
+  size_t cap = 0, off = 0;
+  double *take(size_t n_doubles) {
+    size_t bytes = ((n_doubles * sizeof(double) + 255) / 256) * 256;
+    if (off + bytes > cap) return nullptr;
+    double *p = reinterpret_cast<double *>(base + off);
+    off += bytes;
+    return p;
+  }
+  void *take_bytes(size_t bytes) {
+    bytes = ((bytes + 255) / 256) * 256;
+    if (off + bytes > cap) return nullptr;
+    void *p = base + off;
+    off += bytes;
+    return p;
+  }
+};
+inline size_t arena_doubles(size_t n) { return ((n * sizeof(double) + 255) / 256) * 256; }
+
+// Grow the context workspace to at least `bytes` (synchronises the device when it grows).
+x2c_status ensure_workspace(x2c_ctx *ctx, size_t bytes, Arena *out);
+
+// Descriptor of one decoupling problem's inputs (device pointers, leading dimension ld).
+struct InputDesc {
+  const double *S, *T, *V;
+  const double *W[4];  // W0, Wx, Wy, Wz (Wx..Wz NULL when spin-free)
+  int64_t ld;
+};
+
+// Batched decoupling transforms (the matrix function of Eqs. 43 / 22): nb problems of
+// size n with nc = 1 (scalar) or 4 (two-component) parts.  d_in: device array of nb
+// descriptors.  UL, US: device, nb * nc * n * n doubles each (problem-major, then part).
+// Scratch comes from `ar` (passed by value: the caller's arena is not advanced).
+constexpr int kMaxSolveN = 168;
+x2c_status solve_transforms(x2c_ctx *ctx, cudaStream_t st, double c, int nb, int n, int nc,
+                            const InputDesc *d_in, double *UL, double *US, Arena ar);
+size_t solve_workspace_bytes(int nb, int n, int nc);
+
+// Pair-block assembly of h = U+ D U for block-diagonal U (Eq. 8 with Eq. 42).
+struct PairDesc {
+  int32_t offA, offB;   // first basis function of atoms A and B (within the molecule)
+  int32_t nA, nB;       // atom sizes
+  int32_t uA, uB;       // index of the atoms' transforms in the U table
+  int32_t mol;          // molecule index (batched builds)
+  int32_t diag;         // 1 when A == B
+  int64_t r_off;        // offset (doubles) of this pair's intermediate in the R buffer
+};
+struct MolDesc {
+  const double *V, *T, *W0;
+  const double *W[3];   // Wx, Wy, Wz (NULL when spin-free)
+  double *h[4];
+  int64_t ld;
+};
+struct UTable {
+  const double *const *UL;  // device array: per transform index, pointer to nc*n*n doubles
+  const double *const *US;
+};
+x2c_status assemble_pairs_fp64(x2c_ctx *ctx, cudaStream_t st, double c, int nc, int so_all_pairs,
+                               const std::vector<PairDesc> &pairs, const MolDesc *d_mols,
+                               UTable ut, int max_n, Arena &ar);
+x2c_status assemble_pairs_split(x2c_ctx *ctx, cudaStream_t st, double c, int nc, int so_all_pairs,
+                                const std::vector<PairDesc> &pairs, const MolDesc *d_mols,
+                                UTable ut, int max_n, int n_slices, Arena &ar);
+size_t assemble_workspace_bytes(const std::vector<PairDesc> &pairs, int nc, int max_n, int precision);
+
+}  // namespace x2c

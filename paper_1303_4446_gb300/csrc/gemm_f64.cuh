@@ -1,0 +1,174 @@
+// Batched FP64 GEMM on the FMA pipe, C(b) = f(A(b) B(b)), with operand access through
+// functors so that transposes, quaternion left-multiplication matrices and gathers from
+// molecular pair blocks are read in place instead of being materialised.
+//
+// On GB300 the FP64 FMA rate (1.19 TFLOP/s measured) is above the FP64 tensor-core
+// (mma.sync f64) rate (1.05 TFLOP/s measured), so the tile is register-blocked for DFMA:
+// each thread owns TM x TN accumulators with rows ty + i*NTY and columns tx + j*NTX
+// (interleaved, so shared-memory reads are broadcasts or conflict-free and the epilogue
+// stores are coalesced).
+#pragma once
+
+#include "common.cuh"
+
+namespace x2c {
+
+template <int BM_, int BN_, int KC_, int TM_, int TN_>
+struct TileCfg {
+  static constexpr int BM = BM_, BN = BN_, KC = KC_, TM = TM_, TN = TN_;
+  static constexpr int NTY = BM / TM, NTX = BN / TN, NT = NTX * NTY;
+  static_assert(BM % TM == 0 && BN % TN == 0, "tile");
+};
+
+// Shapes: M(b), N(b), K(b) per batch entry.
+struct UniformDims {
+  int m, n, k;
+  __device__ int M(int) const { return m; }
+  __device__ int N(int) const { return n; }
+  __device__ int K(int) const { return k; }
+};
+
+// A plain strided matrix operand: element (r, k) (or (k, n) for B) of batch b.
+//   trans = false: p[b*bs + r*ld + k];  trans = true: p[b*bs + k*ld + r]
+template <bool TRANS>
+struct Mat {
+  const double *p;
+  int64_t ld, bs;
+  double scale;
+  static constexpr bool k_contig = !TRANS;  // as A operand: is k the contiguous index?
+  static constexpr bool n_contig = !TRANS;  // as B operand (k, n): is n contiguous?
+  __device__ __forceinline__ double operator()(int b, int r, int k) const {
+    return scale * (TRANS ? p[b * bs + (int64_t)k * ld + r] : p[b * bs + (int64_t)r * ld + k]);
+  }
+};
+
+// Quaternion left-multiplication matrix Lq(A) (or Lq(A+) when ADJ) of a batch of
+// quaternion matrices with parts of size m x m stored part-major (part q of batch b at
+// p + b*bs + q*ps).  nc = 1 degenerates to A (or A^T).
+template <bool ADJ>
+struct QuatLeft {
+  const double *p;
+  int64_t ld, bs, ps;
+  int m, nc;
+  double scale;
+  static constexpr bool k_contig = !ADJ;
+  __device__ __forceinline__ double operator()(int b, int r, int k) const {
+    int pr = 0, i = r, pq = 0, kk = k;
+    if (nc == 4) {
+      pr = r / m; i = r - pr * m;
+      pq = k / m; kk = k - pq * m;
+    }
+    const int comp = pr ^ pq;
+    const double *base = p + b * bs + comp * ps;
+    if (!ADJ) return scale * quat_sign(pr, pq) * base[(int64_t)i * ld + kk];
+    return scale * quat_sign_adj(pr, pq) * base[(int64_t)kk * ld + i];
+  }
+};
+
+// Epilogue writing alpha*acc + beta*Cin into a strided output (Cin may alias nothing).
+struct StoreAxpby {
+  double *out;
+  const double *cin;
+  int64_t ld, bs;
+  double alpha, beta;
+  __device__ __forceinline__ void operator()(int b, int r, int c, double acc) const {
+    const int64_t o = b * bs + (int64_t)r * ld + c;
+    double v = alpha * acc;
+    if (cin) v += beta * cin[o];
+    out[o] = v;
+  }
+};
+
+// Epilogue: out = alpha*acc + diag_shift*delta(r mod m, c) (identity part of a stacked
+// quaternion lives only in rows of part 0, i.e. r < m).
+struct StoreShiftIdentity {
+  double *out;
+  int64_t ld, bs;
+  int m;
+  double alpha, shift;
+  __device__ __forceinline__ void operator()(int b, int r, int c, double acc) const {
+    double v = alpha * acc;
+    if (r == c && r < m) v += shift;
+    out[b * bs + (int64_t)r * ld + c] = v;
+  }
+};
+
+template <class Cfg, class AOp, class BOp, class COp, class Dims>
+__global__ void __launch_bounds__(Cfg::NT) gemm_f64_kernel(AOp A, BOp B, COp C, Dims D, int tiles_n) {
+  constexpr int BM = Cfg::BM, BN = Cfg::BN, KC = Cfg::KC, TM = Cfg::TM, TN = Cfg::TN;
+  constexpr int NTX = Cfg::NTX, NTY = Cfg::NTY, NT = Cfg::NT;
+  const int b = blockIdx.x;
+  const int M = D.M(b), N = D.N(b), K = D.K(b);
+  const int tm = blockIdx.y / tiles_n, tn = blockIdx.y - (blockIdx.y / tiles_n) * tiles_n;
+  const int m0 = tm * BM, n0 = tn * BN;
+  if (m0 >= M || n0 >= N) return;
+
+  __shared__ double As[KC][BM + 1];
+  __shared__ double Bs[KC][BN + 1];
+  const int tid = threadIdx.x;
+  const int tx = tid % NTX, ty = tid / NTX;
+  double acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
+
+  for (int k0 = 0; k0 < K; k0 += KC) {
+    for (int idx = tid; idx < BM * KC; idx += NT) {
+      int r, kk;
+      if (AOp::k_contig) { r = idx / KC; kk = idx - r * KC; }
+      else { kk = idx / BM; r = idx - kk * BM; }
+      const int gm = m0 + r, gk = k0 + kk;
+      As[kk][r] = (gm < M && gk < K) ? A(b, gm, gk) : 0.0;
+    }
+    for (int idx = tid; idx < BN * KC; idx += NT) {
+      int c, kk;
+      if (BOp::n_contig) { kk = idx / BN; c = idx - kk * BN; }
+      else { c = idx / KC; kk = idx - c * KC; }
+      const int gn = n0 + c, gk = k0 + kk;
+      Bs[kk][c] = (gn < N && gk < K) ? B(b, gk, gn) : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < KC; ++kk) {
+      double a[TM], bv[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + i * NTY];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) bv[j] = Bs[kk][tx + j * NTX];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], bv[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    const int gm = m0 + ty + i * NTY;
+    if (gm >= M) continue;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const int gn = n0 + tx + j * NTX;
+      if (gn < N) C(b, gm, gn, acc[i][j]);
+    }
+  }
+}
+
+// Launch helper: grid.x = batch entries, grid.y = tiles of the largest M x N.
+template <class Cfg, class AOp, class BOp, class COp, class Dims>
+inline x2c_status gemm_f64(x2c_ctx *ctx, cudaStream_t st, int batch, int max_m, int max_n,
+                           const AOp &A, const BOp &B, const COp &C, const Dims &D) {
+  if (batch <= 0 || max_m <= 0 || max_n <= 0) return X2C_OK;
+  const int tiles_m = (max_m + Cfg::BM - 1) / Cfg::BM;
+  const int tiles_n = (max_n + Cfg::BN - 1) / Cfg::BN;
+  dim3 grid(batch, tiles_m * tiles_n);
+  gemm_f64_kernel<Cfg><<<grid, Cfg::NT, 0, st>>>(A, B, C, D, tiles_n);
+  return launched(ctx, "gemm_f64_kernel");
+}
+
+// Default tile for the dense (square-ish) products of the decoupling solve.
+using TileSolve = TileCfg<64, 64, 16, 4, 4>;
+using TileSmall = TileCfg<32, 32, 16, 2, 2>;
+
+}  // namespace x2c

@@ -1,0 +1,383 @@
+// Batched X2C decoupling transforms U^L, U^S (Sec. II.A) by a GEMM-only route.
+//
+// The paper diagonalises T K = S K t (Eq. 11), builds the orthonormal 4c matrix H^p
+// (Eq. 14), diagonalises it (Eq. 18), forms X' = C_S' C_L'^-1 (Eq. 19), R' =
+// (1 + X'+ X')^-1/2 (Eq. 20) and U^L = K R' K^-1, U^S = 2c K p^-1 X' R' K^-1 (Eq. 22).
+// Here the same transforms come from matrix functions evaluated with GEMMs:
+//  1. Orthonormalisation by Cholesky factors instead of the eigenvectors of (T, S):
+//       S = L L^T, T = M M^T,  K_L = L^-T,  K_S = sqrt(2) c M^-T
+//     so H^p = [[L^-1 V L^-T, sqrt2 c L^-1 M], [.., (1/2) M^-1 W M^-T - 2c^2]].
+//     (Any K_L with K_L+ S K_L = 1 and K_S+ (T/2c^2) K_S = 1 gives the same U: the
+//     appendix argument, Eqs. A9-A17, only uses these two properties.)
+//  2. The projector P onto the positive-energy solutions (eps + c^2 > 0) from the sign
+//     function of Z = H^p + c^2, P = (1 + sign Z)/2, by a scaled Newton-Schulz iteration
+//       Z <- (3 a/2) Z - (a^3/2) Z^3,   a = sqrt(3 / (1 + l + l^2))
+//     with l the running lower bound of |eigenvalue| / ||Z|| (schedule fixed on the host).
+//  3. With C+ the positive-energy eigenvectors, P_LL = C_L C_L+ and P_SL = C_S C_L+, so
+//       X' = P_SL P_LL^-1   and   R' = (1 + X'+ X')^-1/2 = P_LL^1/2
+//     (because 1 + X'+ X' = C_L^-+ C_L^-1 = P_LL^-1).  P_LL^(1/2) and P_LL^(-1/2) come
+//     from the coupled Newton-Schulz iteration (eigenvalues of P_LL lie in (0, 1]).
+//  4. U^L = K_L R' K_L^-1 = L^-T P_LL^1/2 L^T,
+//     U^S = K_S X' R' K_L^-1 = sqrt2 c M^-T P_SL P_LL^-1/2 L^T.
+// Two-component matrices are handled in the quaternion form (four real parts), so every
+// product is a real GEMM with the quaternion left-multiplication matrix read in place.
+#include <cmath>
+
+#include "common.cuh"
+#include "gemm_f64.cuh"
+
+namespace x2c {
+namespace {
+
+constexpr double kSignLowerBound = 1e-6;   // assumed min |eig| / ||Z|| for the schedule
+constexpr int kSqrtIters = 8;              // coupled Newton-Schulz steps for P_LL^(+-1/2)
+constexpr double kSignTol = 1e-7;          // ||Z^2 - 1|| at the last sign step
+constexpr double kSqrtTol = 1e-7;          // ||T - 1|| at the last square-root step
+
+std::vector<double> sign_schedule(double l0) {
+  std::vector<double> a;
+  double l = l0;
+  auto f = [](double x) { return 1.5 * x - 0.5 * x * x * x; };
+  while (1.0 - l > 1e-15 && a.size() < 60) {
+    double al = std::sqrt(3.0 / (1.0 + l + l * l));
+    a.push_back(al);
+    l = std::fmin(f(al * l), f(al));
+  }
+  a.push_back(1.0);  // one plain step to settle the rounding level
+  return a;
+}
+
+// Cholesky factor and its inverse of S (which = 0) or T (which = 1) of every problem.
+// One CTA per matrix, factorisation in shared memory (n <= 168), inverse by column-wise
+// forward substitution.  fac/inv: (2 * nb) blocks of n * n, lower triangular.
+__global__ void chol_inv_kernel(const InputDesc *in, int n, double *fac, double *inv, int *status) {
+  extern __shared__ double A[];
+  const int prob = blockIdx.x >> 1, which = blockIdx.x & 1;
+  const InputDesc d = in[prob];
+  const double *src = which ? d.T : d.S;
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int i = idx / n, j = idx - i * n;
+    A[idx] = src[(int64_t)i * d.ld + j];
+  }
+  __syncthreads();
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    if (threadIdx.x == 0) {
+      double p = A[j * n + j];
+      if (!(p > 0.0)) {   // also catches NaN
+        bad = 1;
+        p = 1.0;
+      }
+      A[j * n + j] = sqrt(p);
+    }
+    __syncthreads();
+    const double piv = A[j * n + j];
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[i * n + j] /= piv;
+    __syncthreads();
+    const int w = n - j - 1;
+    for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
+      const int i = j + 1 + idx / w, k = j + 1 + idx % w;
+      if (k <= i) A[i * n + k] -= A[i * n + j] * A[k * n + j];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && bad) flag_error(status, X2C_DEV_NOT_POSDEF);
+  double *F = fac + (int64_t)blockIdx.x * n * n;
+  double *X = inv + (int64_t)blockIdx.x * n * n;
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int i = idx / n, k = idx - i * n;
+    F[idx] = (k <= i) ? A[idx] : 0.0;
+    X[idx] = 0.0;
+  }
+  __syncthreads();
+  // X = L^-1, column j by one thread: X_jj = 1/L_jj, X_ij = -(sum_k=j..i-1 L_ik X_kj) / L_ii
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    X[(int64_t)j * n + j] = 1.0 / A[j * n + j];
+    for (int i = j + 1; i < n; ++i) {
+      double s = 0.0;
+      for (int k = j; k < i; ++k) s = fma(A[i * n + k], X[(int64_t)k * n + j], s);
+      X[(int64_t)i * n + j] = -s / A[i * n + i];
+    }
+  }
+}
+
+// B operand reading an input matrix of problem bb / div (part bb % div for W).
+struct InputOp {
+  const InputDesc *d;
+  int which;  // 0 S, 1 T, 2 V, 3 W[part]
+  int div;
+  static constexpr bool n_contig = true;
+  __device__ __forceinline__ double operator()(int bb, int k, int nn) const {
+    const InputDesc &D = d[bb / div];
+    const double *p = which == 0 ? D.S : which == 1 ? D.T : which == 2 ? D.V : D.W[bb % div];
+    return p[(int64_t)k * D.ld + nn];
+  }
+};
+
+// Strided operand whose batch index is divided by `div` (shared by the parts of a problem).
+template <bool TRANS>
+struct MatDiv {
+  const double *p;
+  int64_t ld, bs;
+  int div;
+  double scale;
+  static constexpr bool k_contig = !TRANS;
+  static constexpr bool n_contig = !TRANS;
+  __device__ __forceinline__ double operator()(int b, int r, int k) const {
+    const double *q = p + (int64_t)(b / div) * bs;
+    return scale * (TRANS ? q[(int64_t)k * ld + r] : q[(int64_t)r * ld + k]);
+  }
+};
+
+// Z = H^p + c^2 (Eq. 14 in the Cholesky-orthonormal basis), parts of size 2n x 2n.
+__global__ void assemble_hp_kernel(int n, int nc, double c, const double *Vt, const double *LSm,
+                                   const double *Wt, double *Z) {
+  const int prob = blockIdx.x / nc, q = blockIdx.x % nc;
+  const int d = 2 * n;
+  const double c2 = c * c;
+  const double *vt = Vt + (int64_t)prob * n * n;
+  const double *ls = LSm + (int64_t)prob * n * n;
+  const double *wt = Wt + ((int64_t)prob * nc + q) * n * n;
+  double *z = Z + ((int64_t)prob * nc + q) * d * d;
+  for (int idx = threadIdx.x; idx < d * d; idx += blockDim.x) {
+    const int r = idx / d, col = idx - r * d;
+    double v = 0.0;
+    if (r < n && col < n) {
+      if (q == 0) v = vt[r * n + col] + (r == col ? c2 : 0.0);
+    } else if (r < n) {
+      if (q == 0) v = ls[r * n + (col - n)];
+    } else if (col < n) {
+      if (q == 0) v = ls[col * n + (r - n)];
+    } else {
+      v = wt[(r - n) * n + (col - n)] - ((q == 0 && r == col) ? c2 : 0.0);
+    }
+    z[idx] = v;
+  }
+}
+
+__device__ double block_max(double v, double *red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    v = (l < (int)(blockDim.x >> 5)) ? red[l] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (l == 0) red[0] = v;
+  }
+  __syncthreads();
+  v = red[0];
+  __syncthreads();
+  return v;
+}
+
+__device__ double block_sum(double v, double *red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    v = (l < (int)(blockDim.x >> 5)) ? red[l] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (l == 0) red[0] = v;
+  }
+  __syncthreads();
+  v = red[0];
+  __syncthreads();
+  return v;
+}
+
+// Scale every problem's Z by an upper bound of its spectral radius: the largest row sum of
+// quaternion moduli (a Gershgorin bound of the equivalent complex matrix).
+__global__ void normalise_kernel(int d, int nc, double *Z, int *status) {
+  __shared__ double red[32];
+  double *z = Z + (int64_t)blockIdx.x * nc * d * d;
+  double mx = 0.0;
+  for (int r = threadIdx.x; r < d; r += blockDim.x) {
+    double s = 0.0;
+    for (int col = 0; col < d; ++col) {
+      double q2 = 0.0;
+      for (int q = 0; q < nc; ++q) {
+        const double v = z[(int64_t)q * d * d + (int64_t)r * d + col];
+        q2 += v * v;
+      }
+      s += sqrt(q2);
+    }
+    mx = fmax(mx, s);
+  }
+  mx = block_max(mx, red);
+  if (!(mx > 0.0) || !isfinite(mx)) {
+    if (threadIdx.x == 0) flag_error(status, X2C_DEV_NONFINITE);
+    mx = 1.0;
+  }
+  const double inv = 1.0 / mx;
+  for (int64_t idx = threadIdx.x; idx < (int64_t)nc * d * d; idx += blockDim.x) z[idx] *= inv;
+}
+
+// Convergence checks: ||Y - 1||_max of the last squared iterate and, for the sign
+// function, |trace Z_0| < 1/2 (equal numbers of positive- and negative-energy states).
+__global__ void check_kernel(int d, int nc, const double *Y, const double *Z, double tol,
+                             int trace_check, int *status) {
+  __shared__ double red[32];
+  const double *y = Y + (int64_t)blockIdx.x * nc * d * d;
+  double mx = 0.0;
+  for (int64_t idx = threadIdx.x; idx < (int64_t)nc * d * d; idx += blockDim.x) {
+    const int64_t rr = idx / d, col = idx % d;
+    double v = y[idx] - ((rr == col) ? 1.0 : 0.0);  // part 0 rows are rr < d
+    if (!isfinite(v)) v = 1e300;
+    mx = fmax(mx, fabs(v));
+  }
+  mx = block_max(mx, red);
+  double tr = 0.0;
+  if (trace_check) {
+    const double *z = Z + (int64_t)blockIdx.x * nc * d * d;
+    for (int r = threadIdx.x; r < d; r += blockDim.x) tr += z[(int64_t)r * d + r];
+    tr = block_sum(tr, red);
+  }
+  if (threadIdx.x == 0) {
+    if (!(mx <= tol)) flag_error(status, mx >= 1e299 ? X2C_DEV_NONFINITE : X2C_DEV_NOCONV);
+    if (trace_check && !(fabs(tr) < 0.5)) flag_error(status, X2C_DEV_DECOUPLING);
+  }
+}
+
+// P = (1 + Z)/2 blocks: P_LL (Hermitian part of the LL block) and P_SL.
+__global__ void projector_kernel(int n, int nc, const double *Z, double *PLL, double *PSL) {
+  const int prob = blockIdx.x / nc, q = blockIdx.x % nc;
+  const int d = 2 * n;
+  const double *z = Z + ((int64_t)prob * nc + q) * d * d;
+  double *pll = PLL + ((int64_t)prob * nc + q) * n * n;
+  double *psl = PSL + ((int64_t)prob * nc + q) * n * n;
+  const double sgn = (q == 0) ? 1.0 : -1.0;  // part 0 symmetric, parts 1-3 antisymmetric
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int i = idx / n, j = idx - i * n;
+    const double h = 0.5 * (z[i * d + j] + sgn * z[j * d + i]);
+    pll[idx] = 0.5 * h + ((q == 0 && i == j) ? 0.5 : 0.0);
+    psl[idx] = 0.5 * z[(n + i) * d + j];
+  }
+}
+
+// Quaternion identity (part 0 = 1, others 0) for every problem.
+__global__ void identity_kernel(int n, int nc, double *X) {
+  const int prob = blockIdx.x;
+  double *x = X + (int64_t)prob * nc * n * n;
+  for (int64_t idx = threadIdx.x; idx < (int64_t)nc * n * n; idx += blockDim.x) {
+    const int64_t r = idx / n, col = idx % n;
+    x[idx] = (r == col) ? 1.0 : 0.0;
+  }
+}
+
+// Quaternion product C = A B for nb problems (parts m x m): C_stack = Lq(A) B_stack.
+template <class COp>
+x2c_status quat_gemm(x2c_ctx *ctx, cudaStream_t st, int nb, int m, int nc, const double *A,
+                     const double *B, double scale, const COp &C) {
+  QuatLeft<false> a{A, m, (int64_t)nc * m * m, (int64_t)m * m, m, nc, scale};
+  Mat<false> b{B, m, (int64_t)nc * m * m, 1.0};
+  UniformDims dims{nc * m, m, nc * m};
+  return gemm_f64<TileSolve>(ctx, st, nb, nc * m, m, a, b, C, dims);
+}
+
+inline StoreAxpby store_plain(double *out, int m, int nc) {
+  return StoreAxpby{out, nullptr, m, (int64_t)nc * m * m, 1.0, 0.0};
+}
+
+}  // namespace
+
+size_t solve_workspace_bytes(int nb, int n, int nc) {
+  const size_t n2 = (size_t)n * n;
+  const size_t per = (6 + 23 * (size_t)nc) * n2;
+  return arena_doubles(per * nb) + 16 * 256;
+}
+
+x2c_status solve_transforms(x2c_ctx *ctx, cudaStream_t st, double c, int nb, int n, int nc,
+                            const InputDesc *d_in, double *UL, double *US, Arena ar) {
+  if (nb <= 0) return X2C_OK;
+  if (n < 1 || n > kMaxSolveN) return X2C_ERR_ARG;
+  const int64_t n2 = (int64_t)n * n;
+  const int d = 2 * n;
+  const int64_t d2 = (int64_t)d * d;
+  double *fac = ar.take(2 * nb * n2), *inv = ar.take(2 * nb * n2);
+  double *Vt = ar.take(nb * n2), *LSm = ar.take(nb * n2);
+  double *tmp = ar.take(nb * nc * n2), *Wt = ar.take(nb * nc * n2);
+  double *Z = ar.take(nb * nc * d2), *Zn = ar.take(nb * nc * d2), *Y = ar.take(nb * nc * d2);
+  double *PLL = ar.take(nb * nc * n2), *PSL = ar.take(nb * nc * n2);
+  double *Yk = ar.take(nb * nc * n2), *Zk = ar.take(nb * nc * n2), *Tm = ar.take(nb * nc * n2);
+  double *Yk2 = ar.take(nb * nc * n2), *Zk2 = ar.take(nb * nc * n2);
+  double *XR = ar.take(nb * nc * n2), *tmp2 = ar.take(nb * nc * n2);
+  if (!tmp2) return X2C_ERR_NOMEM;
+  int *status = ctx->d_status;
+
+  // 1. Cholesky factors and inverses of S and T.
+  const size_t smem = (size_t)n2 * sizeof(double);
+  X2C_TRY_CUDA(ctx, cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  chol_inv_kernel<<<2 * nb, 256, smem, st>>>(d_in, n, fac, inv, status);
+  X2C_TRY(launched(ctx, "chol_inv_kernel"));
+  // L_S at fac + 2b n2, L_T at fac + (2b+1) n2; inverses likewise in inv.
+  const double rt2c = std::sqrt(2.0) * c;
+  {
+    UniformDims dims{n, n, n};
+    // tmp = L^-1 V ;  Vt = tmp L^-T
+    X2C_TRY((gemm_f64<TileSolve>(ctx, st, nb, n, n, Mat<false>{inv, n, 2 * n2, 1.0},
+                                 InputOp{d_in, 2, 1}, StoreAxpby{tmp, nullptr, n, n2, 1.0, 0.0}, dims)));
+    X2C_TRY((gemm_f64<TileSolve>(ctx, st, nb, n, n, Mat<false>{tmp, n, n2, 1.0},
+                                 Mat<true>{inv, n, 2 * n2, 1.0}, StoreAxpby{Vt, nullptr, n, n2, 1.0, 0.0}, dims)));
+    // LSm = sqrt2 c L^-1 M
+    X2C_TRY((gemm_f64<TileSolve>(ctx, st, nb, n, n, Mat<false>{inv, n, 2 * n2, 1.0},
+                                 Mat<false>{fac + n2, n, 2 * n2, 1.0}, StoreAxpby{LSm, nullptr, n, n2, rt2c, 0.0}, dims)));
+    // tmp_q = M^-1 W_q ;  Wt_q = (1/2) tmp_q M^-T      (batch over problem x part)
+    X2C_TRY((gemm_f64<TileSolve>(ctx, st, nb * nc, n, n, MatDiv<false>{inv + n2, n, 2 * n2, nc, 1.0},
+                                 InputOp{d_in, 3, nc}, StoreAxpby{tmp, nullptr, n, n2, 1.0, 0.0}, dims)));
+    X2C_TRY((gemm_f64<TileSolve>(ctx, st, nb * nc, n, n, Mat<false>{tmp, n, n2, 1.0},
+                                 MatDiv<true>{inv + n2, n, 2 * n2, nc, 1.0}, StoreAxpby{Wt, nullptr, n, n2, 0.5, 0.0}, dims)));
+  }
+  // 2. Z = H^p + c^2, scaled into [-1, 1].
+  assemble_hp_kernel<<<nb * nc, 256, 0, st>>>(n, nc, c, Vt, LSm, Wt, Z);
+  X2C_TRY(launched(ctx, "assemble_hp_kernel"));
+  normalise_kernel<<<nb, 256, 0, st>>>(d, nc, Z, status);
+  X2C_TRY(launched(ctx, "normalise_kernel"));
+  // 3. Sign function by the scaled Newton-Schulz schedule.
+  const std::vector<double> sched = sign_schedule(kSignLowerBound);
+  for (double a : sched) {
+    X2C_TRY(quat_gemm(ctx, st, nb, d, nc, Z, Z, 1.0, store_plain(Y, d, nc)));
+    // Zn = (3a/2) Z - (a^3/2) Z Y
+    StoreAxpby upd{Zn, Z, d, (int64_t)nc * d2, -0.5 * a * a * a, 1.5 * a};
+    X2C_TRY(quat_gemm(ctx, st, nb, d, nc, Z, Y, 1.0, upd));
+    std::swap(Z, Zn);
+  }
+  check_kernel<<<nb, 256, 0, st>>>(d, nc, Y, Z, kSignTol, 1, status);
+  X2C_TRY(launched(ctx, "check_kernel"));
+  projector_kernel<<<nb * nc, 256, 0, st>>>(n, nc, Z, PLL, PSL);
+  X2C_TRY(launched(ctx, "projector_kernel"));
+  // 4. Coupled Newton-Schulz: Yk -> P_LL^1/2, Zk -> P_LL^-1/2.
+  X2C_TRY_CUDA(ctx, cudaMemcpyAsync(Yk, PLL, sizeof(double) * nb * nc * n2, cudaMemcpyDeviceToDevice, st));
+  identity_kernel<<<nb, 256, 0, st>>>(n, nc, Zk);
+  X2C_TRY(launched(ctx, "identity_kernel"));
+  for (int it = 0; it < kSqrtIters; ++it) {
+    StoreShiftIdentity tm{Tm, n, (int64_t)nc * n2, n, -0.5, 1.5};
+    X2C_TRY(quat_gemm(ctx, st, nb, n, nc, Zk, Yk, 1.0, tm));
+    X2C_TRY(quat_gemm(ctx, st, nb, n, nc, Yk, Tm, 1.0, store_plain(Yk2, n, nc)));
+    X2C_TRY(quat_gemm(ctx, st, nb, n, nc, Tm, Zk, 1.0, store_plain(Zk2, n, nc)));
+    std::swap(Yk, Yk2);
+    std::swap(Zk, Zk2);
+  }
+  check_kernel<<<nb, 256, 0, st>>>(n, nc, Tm, nullptr, kSqrtTol, 0, status);
+  X2C_TRY(launched(ctx, "check_kernel"));
+  // 5. X'R' = P_SL P_LL^-1/2
+  X2C_TRY(quat_gemm(ctx, st, nb, n, nc, PSL, Zk, 1.0, store_plain(XR, n, nc)));
+  // 6. U^L_q = L^-T (R'_q L^T),  U^S_q = sqrt2 c M^-T (X'R'_q L^T)   (batch over problem x part)
+  {
+    UniformDims dims{n, n, n};
+    X2C_TRY((gemm_f64<TileSolve>(ctx, st, nb * nc, n, n, Mat<false>{Yk, n, n2, 1.0},
+                                 MatDiv<true>{fac, n, 2 * n2, nc, 1.0}, StoreAxpby{tmp, nullptr, n, n2, 1.0, 0.0}, dims)));
+    X2C_TRY((gemm_f64<TileSolve>(ctx, st, nb * nc, n, n, MatDiv<true>{inv, n, 2 * n2, nc, 1.0},
+                                 Mat<false>{tmp, n, n2, 1.0}, StoreAxpby{UL, nullptr, n, n2, 1.0, 0.0}, dims)));
+    X2C_TRY((gemm_f64<TileSolve>(ctx, st, nb * nc, n, n, Mat<false>{XR, n, n2, 1.0},
+                                 MatDiv<true>{fac, n, 2 * n2, nc, 1.0}, StoreAxpby{tmp2, nullptr, n, n2, 1.0, 0.0}, dims)));
+    X2C_TRY((gemm_f64<TileSolve>(ctx, st, nb * nc, n, n, MatDiv<true>{inv + n2, n, 2 * n2, nc, 1.0},
+                                 Mat<false>{tmp2, n, n2, 1.0}, StoreAxpby{US, nullptr, n, n2, rt2c, 0.0}, dims)));
+  }
+  return X2C_OK;
+}
+
+}  // namespace x2c

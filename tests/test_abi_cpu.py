@@ -1,0 +1,75 @@
+"""CPU checks of the C ABI: the library exports every declared function, the ctypes
+structs match the header's layout, and the quaternion sign tables of the kernels give
+the product of the two-component matrices of Eq. 5 (checked against complex arithmetic)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_1303_4446_gb300 import abi, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "x2c.h")
+
+
+def declared_functions():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(x2c_[a-z_0-9]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build_library()
+    return ctypes.CDLL(build.LIB_PATH)
+
+
+def test_library_exports_every_declared_function(lib):
+    names = declared_functions()
+    assert len(names) >= 12
+    for name in names:
+        assert hasattr(lib, name), name
+    assert sorted(abi.exported_symbols()) == names
+
+
+def test_ctypes_structs_match_header(tmp_path):
+    exe = tmp_path / "abi_layout"
+    subprocess.check_call(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"),
+                           os.path.join(ROOT, "tests", "native", "abi_layout.c"), "-o", str(exe)])
+    out = dict((l.split()[0], list(map(int, l.split()[1:]))) for l in
+               subprocess.check_output([str(exe)], text=True).splitlines())
+    O = abi.Options
+    assert out["options"] == [ctypes.sizeof(O), O.two_component.offset, O.precision.offset,
+                              O.so_same_atom_only.offset, O.n_slices.offset, O.reserved.offset]
+    assert out["mats"] == [ctypes.sizeof(abi.Mats), abi.Mats.S.offset, abi.Mats.Wz.offset]
+    assert out["hout"] == [ctypes.sizeof(abi.HOut)]
+    assert out["uout"] == [ctypes.sizeof(abi.UOut), abi.UOut.US.offset]
+    L = abi.Layout
+    assert out["layout"] == [ctypes.sizeof(L), L.atom_offset.offset, L.n_kinds.offset, L.kinds.offset]
+    assert out["counters"] == [ctypes.sizeof(abi.Counters), abi.Counters.credited_flops.offset]
+
+
+def _spinor(parts):
+    sig = (np.array([[0, 1], [1, 0]]), np.array([[0, -1j], [1j, 0]]), np.array([[1, 0], [0, -1]]))
+    return np.kron(np.eye(2), parts[0]) + 1j * sum(np.kron(s, p) for s, p in zip(sig, parts[1:]))
+
+
+def test_quaternion_tables_reproduce_spinor_products(tmp_path):
+    exe = tmp_path / "quat"
+    subprocess.check_call(["nvcc", "-std=c++17", "-o", str(exe),
+                           os.path.join(ROOT, "tests", "native", "quat_tables.cu")])
+    m = 3
+    rng = np.random.default_rng(7)
+    A = rng.standard_normal((4, m, m))
+    B = rng.standard_normal((4, m, m))
+    fmt = lambda X: "\n".join("%.17g" % v for v in X.ravel())
+    inp = f"{m}\n" + fmt(A) + "\n" + fmt(B) + "\n"
+    vals = np.array(subprocess.check_output([str(exe)], input=inp, text=True).split(), float)
+    prod, prod_adj = vals[:4 * m * m].reshape(4, m, m), vals[4 * m * m:].reshape(4, m, m)
+    ref = _spinor(A) @ _spinor(B)
+    ref_adj = _spinor(A).conj().T @ _spinor(B)
+    assert np.abs(_spinor(prod) - ref).max() < 1e-12
+    assert np.abs(_spinor(prod_adj) - ref_adj).max() < 1e-12
