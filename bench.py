@@ -1,0 +1,354 @@
+"""Benchmark: X2C Hamiltonian builds/s of the two-component DLU scheme on Ag309.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload ag309_2c] [--precision fp64|split]
+
+One step = one complete DLU build (per-kind atomic decoupling solve + assembly of all
+A <= B pair blocks) of the workload, inputs resident in HBM (they are larger than L2, so
+no flush is needed).  Prints one JSON line.  Under torchrun every rank builds its own copy
+of the workload (independent problems, weak scaling); rank 0 prints.
+
+--impl reference times the CPU oracle (the plain FP64 definition of the method) on a
+bounded sample of the same workload: the atomic solve plus a seeded sample of pair blocks,
+extrapolated to the full pair list.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1303_4446_gb300 import workload as w  # noqa: E402
+
+METRIC = "X2C h builds/s & FP64-equiv TFLOP/s (Ag309 2c DLU) vs plain FP64; p99 latency"
+# FP64 FMA peak: paper_1303_4446_gb300/csrc/peak_probe.cu measured 1.193 TFLOP/s at 1995 MHz,
+# i.e. 2 DFMA per clock per SM; at the 2070 MHz maximum SM clock that is
+# 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz = 1.2586 TFLOP/s.  (mma.sync f64 measured 1.046.)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+WORKLOADS = {
+    "ag309_2c": dict(L=309, basis="s48", two_c=True),
+    "ag55_2c": dict(L=55, basis="s48", two_c=True),
+    "ag55_sf": dict(L=55, basis="s48", two_c=False),
+    "ag4_sf": dict(L=4, basis="s30", two_c=False),
+}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def pair_list(L):
+    return [(a, b) for a in range(L) for b in range(a, L)]
+
+
+def kernel_flops(name, nA, nB, nc, diag):
+    """Algorithmic FP64 flops of one pair block in each assembly kernel."""
+    if name == "dlu_stage1":
+        return 8.0 * nc * nA * nB * nB
+    if name == "dlu_stage2":
+        return 4.0 * nc * nc * nA * nA * nB
+    if name == "dlu_spin_orbit":
+        return 24.0 * nA * nB * nB if diag else 0.0
+    return 0.0
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index=0):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.idx = device_index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        rows = []
+        try:
+            for line in open(self.f.name):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except Exception:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i] and "Not" not in r[5 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def make_inputs(cfg, seed=w.DEFAULT_SEED):
+    mol = w.silver_cluster(cfg["L"], cfg["basis"])
+    m = w.molecule_inputs(mol, cfg["two_c"], seed)
+    kind = w.atomic_inputs(47.0, cfg["basis"], cfg["two_c"], seed)
+    return mol, m, kind
+
+
+def cpu_oracle_rate(mol, m, kind, two_c, budget_s, seed=1):
+    """Oracle builds/s from the atomic solve plus a timed seeded sample of pair blocks,
+    extrapolated to all pair blocks.  Returns (builds/s, n_sampled_pairs, seconds)."""
+    import oracle
+
+    t0 = time.perf_counter()
+    r = oracle.x2c_full(kind)
+    t_atom = time.perf_counter() - t0
+    UL, US = r["UL"], r["US"]
+    pairs = pair_list(mol.natoms)
+    rng = np.random.default_rng(seed)
+    order = rng.permutation(len(pairs))
+    keys = ("V", "T", "W0") + (("Wx", "Wy", "Wz") if two_c else ())
+    t_pairs, n = 0.0, 0
+    for idx in order:
+        A, B = pairs[idx]
+        ra = slice(mol.offsets[A], mol.offsets[A + 1])
+        rb = slice(mol.offsets[B], mol.offsets[B + 1])
+        blocks = {k: m[k][ra, rb] for k in keys}
+        t0 = time.perf_counter()
+        oracle.dlu_pair_block(blocks, UL, US, UL, US)
+        t_pairs += time.perf_counter() - t0
+        n += 1
+        if t_pairs + t_atom > budget_s and n >= 8:
+            break
+    per_build = t_atom + t_pairs / n * len(pairs)
+    return 1.0 / per_build, n, t_atom + t_pairs
+
+
+def run_reference(args, cfg):
+    """CPU oracle arm: each step times the atomic solve and a bounded pair-block sample."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    mol = w.silver_cluster(cfg["L"], cfg["basis"])
+    kind = w.atomic_inputs(47.0, cfg["basis"], cfg["two_c"])
+    pairs = pair_list(mol.natoms)
+    rng = np.random.default_rng(7)
+    # pair blocks for the samples are generated on demand (input generation, not timed)
+    so = w.so_blocks(47.0, cfg["basis"]) if cfg["two_c"] else None
+
+    def block(A, B):
+        ra = slice(int(mol.offsets[A]), int(mol.offsets[A + 1]))
+        rb = slice(int(mol.offsets[B]), int(mol.offsets[B + 1]))
+        b = w.integrals_block(mol, ra, rb, want=("T", "V", "W0"))
+        if cfg["two_c"]:
+            for k, name in enumerate(("Wx", "Wy", "Wz")):
+                b[name] = so[k].copy() if A == B else np.zeros_like(b["T"])
+        return b
+
+    import oracle
+    per_step = 64
+    rates = []
+    for step in range(args.warmup + args.steps):
+        sample = [pairs[i] for i in rng.choice(len(pairs), per_step, replace=False)]
+        blocks = [block(A, B) for A, B in sample]
+        t0 = time.perf_counter()
+        r = oracle.x2c_full(kind)
+        t_atom = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        for b in blocks:
+            oracle.dlu_pair_block(b, r["UL"], r["US"], r["UL"], r["US"])
+        t_p = time.perf_counter() - t0
+        if step >= args.warmup:
+            rates.append(1.0 / (t_atom + t_p / per_step * len(pairs)))
+    v = float(np.mean(rates))
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "builds/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"Ag{cfg['L']} {'two-component' if cfg['two_c'] else 'spin-free'} DLU, "
+                                   f"{cfg['basis']} primitives per atom, N={mol.nbf}",
+                       "pairs": len(pairs)},
+            "cpu_baseline": {"value": v, "unit": "builds/s", "cores": cores, "kind": "oracle",
+                             "sample": f"per step: atomic solve + {per_step} seeded pair blocks, "
+                                       f"extrapolated to {len(pairs)} pair blocks"},
+            "e2e": {"value": v, "unit": "builds/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="ag309_2c", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "split"])
+    ap.add_argument("--slices", type=int, default=0)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    cfg = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, cfg)
+
+    import torch
+    import paper_1303_4446_gb300 as x
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    t_gen = time.perf_counter()
+    mol, m, kind = make_inputs(cfg)
+    t_gen = time.perf_counter() - t_gen
+    two_c = cfg["two_c"]
+    nc = 4 if two_c else 1
+    dev = torch.device("cuda", local)
+    g = {k: torch.from_numpy(v).to(dev) for k, v in m.items()}
+    gk = {k: torch.from_numpy(v).to(dev) for k, v in kind.items()}
+    N = mol.nbf
+    out = [torch.empty((N, N), dtype=torch.float64, device=dev) for _ in range(nc)]
+    ctx = x.Context(local)
+    prec = x.PREC_SPLIT_BF16 if args.precision == "split" else x.PREC_FP64
+    stream = torch.cuda.current_stream(dev)
+    kinds = [0] * mol.natoms
+
+    def build():
+        x.x2c_build_dlu(ctx, g, mol.offsets, kinds, [gk], two_component=two_c, precision=prec,
+                        n_slices=args.slices, out=out, stream=stream)
+
+    for _ in range(args.warmup):
+        build()
+    ctx.status(stream)
+    counters = ctx.counters()
+    ctx.set_timing(True)
+    torch.cuda.synchronize()
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            build()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ctx.status(stream)
+    ms = ev0.elapsed_time(ev1) / args.steps
+    ktimes = ctx.kernel_times()
+    ctx.set_timing(False)
+    ms_t = torch.tensor([ms], device=dev)
+    if dist is not None:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    clocks = clk.summary()
+    credited = counters["credited_flops"]
+    # roofline of the dominant kernel (largest total time in the timed region)
+    dom = max(ktimes.items(), key=lambda kv: kv[1][0])
+    dom_name, (dom_ms, dom_launches) = dom
+    pairs = pair_list(mol.natoms)
+    sizes = np.diff(mol.offsets)
+    dom_flops = sum(kernel_flops(dom_name, sizes[a], sizes[b], nc, a == b) for a, b in pairs) * args.steps
+    peaks = measured_peaks()
+    if dom_name.startswith("dlu_") and args.precision == "fp64":
+        roof = {"bound": "alu", "achieved": dom_flops / (dom_ms * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "kernel": dom_name,
+                "peak_source": "152 SMs x 2 DFMA/clk (measured by peak_probe.cu) x 2.07 GHz max clock"}
+    else:
+        roof = {"bound": "tensor", "achieved": dom_flops / (dom_ms * 1e-3) / 1e12,
+                "peak": peaks.get("bf16_tflops_sustained", 1730.2), "unit": "TFLOP/s", "kernel": dom_name,
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained, of measured"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["launches"] = int(dom_launches)
+    roof["avg_launch_ms"] = dom_ms / max(1, dom_launches)
+
+    line = {"metric": METRIC, "value": world * 1e3 / ms_max, "unit": "builds/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "bf16x-split",
+            "data": "synthetic",
+            "config": {"workload": f"Ag{cfg['L']} {'two-component' if two_c else 'spin-free'} DLU "
+                                   f"(free-atom U per kind), {cfg['basis']} primitives per atom, N={N}",
+                       "pairs": len(pairs), "precision": args.precision, "inputs": "larger than L2 (no flush)",
+                       "parallelism": f"independent replicas x{world}"},
+            "fp64_equiv_tflops": world * credited / (ms_max * 1e-3) / 1e12,
+            "credited_flops_per_build": credited,
+            "gpu_launches": int(counters["kernel_launches"]) * args.steps,
+            "roofline": roof, "clocks": clocks,
+            "kernel_ms_per_step": {k: v[0] / args.steps for k, v in sorted(ktimes.items(), key=lambda kv: -kv[1][0])},
+            "input_generation_s": t_gen}
+
+    if not args.no_e2e:
+        # end to end through the host-buffer entry point: H2D of the inputs the method reads,
+        # build, D2H of h, every step, from pinned host memory
+        pin = {k: torch.from_numpy(v).pin_memory() for k, v in m.items()}
+        pink = {k: torch.from_numpy(v).pin_memory() for k, v in kind.items()}
+        hout = [torch.empty((N, N), dtype=torch.float64).pin_memory() for _ in range(nc)]
+        e2e_args = dict(two_component=two_c, precision=prec, n_slices=args.slices, out=hout, stream=stream)
+        x.x2c_build_dlu_host(ctx, pin, mol.offsets, kinds, [pink], **e2e_args)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            x.x2c_build_dlu_host(ctx, pin, mol.offsets, kinds, [pink], **e2e_args)
+        t_e2e = (time.perf_counter() - t0) / args.e2e_steps
+        t_t = torch.tensor([t_e2e], device=dev)
+        if dist is not None:
+            dist.all_reduce(t_t, op=dist.ReduceOp.MAX)
+        sz = np.diff(mol.offsets)
+        h2d = 8 * (3 * N * N + (3 * int((sz * sz).sum()) if two_c else 0) + (3 + (4 if two_c else 1)) * len(kind["S"]) ** 2)
+        line["e2e"] = {"value": world / float(t_t.item()), "unit": "builds/s", "h2d_bytes_per_step": int(h2d),
+                       "d2h_bytes_per_step": int(8 * nc * N * N), "steps": args.e2e_steps}
+        del pin, hout
+
+    if rank == 0 and not args.no_cpu_baseline:
+        v, n, secs = cpu_oracle_rate(mol, m, kind, two_c, args.cpu_budget)
+        line["cpu_baseline"] = {"value": v, "unit": "builds/s", "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": f"atomic solve + {n} seeded pair blocks ({secs:.1f} s), "
+                                          f"extrapolated to {len(pairs)} pair blocks"}
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -168,6 +168,16 @@ typedef struct {
 } x2c_counters;
 x2c_status x2c_ctx_counters(x2c_ctx *ctx, x2c_counters *out);
 
+/* Per-kernel timing for instrumentation.  With enable = 1 every kernel this context
+ * launches is bracketed by CUDA events recorded on the launching stream (this adds a little
+ * host overhead); enabling also clears the accumulated times.  x2c_ctx_kernel_times()
+ * waits for the recorded events and returns, per kernel name (NUL-terminated, 32 bytes per
+ * entry in `names`), the accumulated milliseconds and the number of launches; at most
+ * max_entries entries are written and *n_entries receives the number written. */
+x2c_status x2c_ctx_set_timing(x2c_ctx *ctx, int32_t enable);
+x2c_status x2c_ctx_kernel_times(x2c_ctx *ctx, int32_t max_entries, char *names, double *ms,
+                                int64_t *launches, int32_t *n_entries);
+
 #ifdef __cplusplus
 }
 #endif

@@ -46,6 +46,21 @@ class Context:
         """x2c_ctx_status: synchronise the stream and raise on a latched device error."""
         abi.check(self.lib.x2c_ctx_status(self.handle, _stream(stream)), "device status", self.handle)
 
+    def set_timing(self, enable: bool):
+        """x2c_ctx_set_timing: bracket every kernel launch with CUDA events (clears totals)."""
+        abi.check(self.lib.x2c_ctx_set_timing(self.handle, int(bool(enable))), "x2c_ctx_set_timing")
+
+    def kernel_times(self, max_entries: int = 64):
+        """x2c_ctx_kernel_times: {kernel name: (total ms, launches)} since timing was enabled."""
+        names = ctypes.create_string_buffer(32 * max_entries)
+        ms = (ctypes.c_double * max_entries)()
+        cnt = (ctypes.c_int64 * max_entries)()
+        n = ctypes.c_int32()
+        abi.check(self.lib.x2c_ctx_kernel_times(self.handle, max_entries, names, ms, cnt, ctypes.byref(n)),
+                  "x2c_ctx_kernel_times", self.handle)
+        raw = names.raw
+        return {raw[32 * i:32 * i + 32].split(b"\0")[0].decode(): (ms[i], cnt[i]) for i in range(n.value)}
+
     def counters(self):
         c = abi.Counters()
         abi.check(self.lib.x2c_ctx_counters(self.handle, ctypes.byref(c)), "x2c_ctx_counters")

@@ -77,6 +77,10 @@ _SIGS = {
     "x2c_quaternion_to_dense": (ctypes.c_int, [ctypes.c_void_p * 4, ctypes.c_int32, ctypes.c_void_p,
                                                ctypes.c_void_p]),
     "x2c_ctx_counters": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Counters)]),
+    "x2c_ctx_set_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "x2c_ctx_kernel_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_char_p,
+                                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
+                                            ctypes.POINTER(ctypes.c_int32)]),
 }
 
 

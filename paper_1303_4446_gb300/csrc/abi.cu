@@ -332,6 +332,7 @@ x2c_status x2c_ctx_destroy(x2c_ctx *ctx) {
   cudaDeviceSynchronize();
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->stage) cudaFree(ctx->stage);
+  for (auto e : ctx->ev_pool) cudaEventDestroy(e);
   if (ctx->d_status) cudaFree(ctx->d_status);
   delete ctx;
   return X2C_OK;
@@ -353,6 +354,47 @@ x2c_status x2c_ctx_status(x2c_ctx *ctx, void *stream) {
 x2c_status x2c_ctx_counters(x2c_ctx *ctx, x2c_counters *out) {
   if (!ctx || !out) return X2C_ERR_ARG;
   *out = ctx->counters;
+  return X2C_OK;
+}
+
+x2c_status x2c_ctx_set_timing(x2c_ctx *ctx, int32_t enable) {
+  if (!ctx) return X2C_ERR_ARG;
+  X2C_TRY_CUDA(ctx, cudaSetDevice(ctx->device));
+  if (!ctx->pending.empty()) X2C_TRY_CUDA(ctx, cudaDeviceSynchronize());
+  ctx->timing = enable != 0;
+  ctx->pending.clear();
+  ctx->ev_used = 0;
+  ctx->kernel_ms.clear();
+  return X2C_OK;
+}
+
+x2c_status x2c_ctx_kernel_times(x2c_ctx *ctx, int32_t max_entries, char *names, double *ms,
+                                int64_t *launches, int32_t *n_entries) {
+  if (!ctx || max_entries < 0 || !n_entries) return X2C_ERR_ARG;
+  X2C_TRY_CUDA(ctx, cudaSetDevice(ctx->device));
+  for (auto &p : ctx->pending) {
+    cudaEvent_t b = ctx->ev_pool[p.second], e = ctx->ev_pool[p.second + 1];
+    X2C_TRY_CUDA(ctx, cudaEventSynchronize(e));
+    float t = 0.f;
+    X2C_TRY_CUDA(ctx, cudaEventElapsedTime(&t, b, e));
+    auto &acc = ctx->kernel_ms[p.first];
+    acc.first += t;
+    acc.second += 1;
+  }
+  ctx->pending.clear();
+  ctx->ev_used = 0;
+  int32_t i = 0;
+  for (auto &kv : ctx->kernel_ms) {
+    if (i >= max_entries) break;
+    if (names) {
+      std::strncpy(names + 32 * i, kv.first.c_str(), 31);
+      names[32 * i + 31] = 0;
+    }
+    if (ms) ms[i] = kv.second.first;
+    if (launches) launches[i] = kv.second.second;
+    ++i;
+  }
+  *n_entries = i;
   return X2C_OK;
 }
 

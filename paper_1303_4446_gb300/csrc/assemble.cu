@@ -241,11 +241,11 @@ x2c_status assemble_pairs_fp64(x2c_ctx *ctx, cudaStream_t st, double c, int nc, 
     const int np = (int)(ch.second - ch.first);
     const PairDesc *dp = d_pairs + ch.first;
     X2C_TRY((gemm_f64<TileStage1>(ctx, st, np, 2 * max_n, nc * max_n, MidOp{dp, d_mols, inv4c2},
-                                  FOp{dp, ut, nc}, StoreR{dp, R, nc}, Stage1Dims{dp, nc})));
+                                  FOp{dp, ut, nc}, StoreR{dp, R, nc}, Stage1Dims{dp, nc}, "dlu_stage1")));
     if (nc == 4) {
       if (so_all_pairs) {
         X2C_TRY((gemm_f64<TileStage2q>(ctx, st, np, 4 * max_n, max_n, SoLeftOp{dp, d_mols, inv4c2},
-                                       UStackOp{dp, ut}, AccumulateRS{dp, R}, SoDims{dp})));
+                                       UStackOp{dp, ut}, AccumulateRS{dp, R}, SoDims{dp}, "dlu_spin_orbit")));
       } else {
         // same-atom blocks only: run the product over the diagonal pairs of the chunk, which
         // are gathered into a separate descriptor list at the end of the pair buffer
@@ -259,16 +259,16 @@ x2c_status assemble_pairs_fp64(x2c_ctx *ctx, cudaStream_t st, double c, int nc, 
                                             cudaMemcpyHostToDevice, st));
           X2C_TRY((gemm_f64<TileStage2q>(ctx, st, (int)diag.size(), 4 * max_n, max_n,
                                          SoLeftOp{dd, d_mols, inv4c2}, UStackOp{dd, ut},
-                                         AccumulateRS{dd, R}, SoDims{dd})));
+                                         AccumulateRS{dd, R}, SoDims{dd}, "dlu_spin_orbit")));
         }
       }
     }
     if (nc == 4) {
       X2C_TRY((gemm_f64<TileStage2q>(ctx, st, np, nc * max_n, max_n, GOp{dp, ut, nc}, RppOp{dp, R, nc},
-                                     StoreH{dp, d_mols}, Stage2Dims{dp, nc})));
+                                     StoreH{dp, d_mols}, Stage2Dims{dp, nc}, "dlu_stage2")));
     } else {
       X2C_TRY((gemm_f64<TileStage2s>(ctx, st, np, nc * max_n, max_n, GOp{dp, ut, nc}, RppOp{dp, R, nc},
-                                     StoreH{dp, d_mols}, Stage2Dims{dp, nc})));
+                                     StoreH{dp, d_mols}, Stage2Dims{dp, nc}, "dlu_stage2")));
     }
   }
   return X2C_OK;

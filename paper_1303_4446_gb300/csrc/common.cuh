@@ -5,7 +5,9 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <map>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/x2c.h"
@@ -26,6 +28,13 @@ struct x2c_ctx {
   std::string last_error;
   x2c_counters counters{};
   int64_t launches = 0;         // kernels launched by the current call
+  // optional per-kernel timing (x2c_ctx_set_timing): events around every launch
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<std::pair<std::string, size_t>> pending;  // kernel name, index of its begin event
+  std::map<std::string, std::pair<double, int64_t>> kernel_ms;  // accumulated ms, launches
+  std::string names_buf;
 };
 
 namespace x2c {
@@ -54,11 +63,35 @@ inline x2c_status cuda_fail(x2c_ctx *ctx, cudaError_t e, const char *what) {
     if (s__ != X2C_OK) return s__;    \
   } while (0)
 
+// Timing: tbegin() records a begin event before a launch, launched() the end event after
+// it (both on the launching stream); x2c_ctx_kernel_times() turns them into durations.
+inline cudaEvent_t next_event(x2c_ctx *ctx) {
+  if (ctx->ev_used == ctx->ev_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    ctx->ev_pool.push_back(e);
+  }
+  return ctx->ev_pool[ctx->ev_used++];
+}
+inline void tbegin(x2c_ctx *ctx, cudaStream_t st) {
+  if (!ctx->timing) return;
+  cudaEvent_t e = next_event(ctx);
+  if (e) cudaEventRecord(e, st);
+}
+
 // Check the launch that was just enqueued and count it.
-inline x2c_status launched(x2c_ctx *ctx, const char *name) {
+inline x2c_status launched(x2c_ctx *ctx, const char *name, cudaStream_t st = nullptr) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, e, name);
   ctx->launches++;
+  if (ctx->timing && ctx->ev_used > 0) {
+    const size_t begin = ctx->ev_used - 1;
+    cudaEvent_t ev = next_event(ctx);
+    if (ev) {
+      cudaEventRecord(ev, st);
+      ctx->pending.push_back({name, begin});
+    }
+  }
   return X2C_OK;
 }
 

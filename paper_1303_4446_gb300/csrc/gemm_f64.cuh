@@ -158,13 +158,15 @@ __global__ void __launch_bounds__(Cfg::NT) gemm_f64_kernel(AOp A, BOp B, COp C, 
 // Launch helper: grid.x = batch entries, grid.y = tiles of the largest M x N.
 template <class Cfg, class AOp, class BOp, class COp, class Dims>
 inline x2c_status gemm_f64(x2c_ctx *ctx, cudaStream_t st, int batch, int max_m, int max_n,
-                           const AOp &A, const BOp &B, const COp &C, const Dims &D) {
+                           const AOp &A, const BOp &B, const COp &C, const Dims &D,
+                           const char *name = "gemm_f64") {
   if (batch <= 0 || max_m <= 0 || max_n <= 0) return X2C_OK;
   const int tiles_m = (max_m + Cfg::BM - 1) / Cfg::BM;
   const int tiles_n = (max_n + Cfg::BN - 1) / Cfg::BN;
   dim3 grid(batch, tiles_m * tiles_n);
+  tbegin(ctx, st);
   gemm_f64_kernel<Cfg><<<grid, Cfg::NT, 0, st>>>(A, B, C, D, tiles_n);
-  return launched(ctx, "gemm_f64_kernel");
+  return launched(ctx, name, st);
 }
 
 // Default tile for the dense (square-ish) products of the decoupling solve.

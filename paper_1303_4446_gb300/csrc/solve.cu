@@ -275,7 +275,7 @@ x2c_status quat_gemm(x2c_ctx *ctx, cudaStream_t st, int nb, int m, int nc, const
   QuatLeft<false> a{A, m, (int64_t)nc * m * m, (int64_t)m * m, m, nc, scale};
   Mat<false> b{B, m, (int64_t)nc * m * m, 1.0};
   UniformDims dims{nc * m, m, nc * m};
-  return gemm_f64<TileSolve>(ctx, st, nb, nc * m, m, a, b, C, dims);
+  return gemm_f64<TileSolve>(ctx, st, nb, nc * m, m, a, b, C, dims, "solve_quat_gemm");
 }
 
 inline StoreAxpby store_plain(double *out, int m, int nc) {
@@ -311,8 +311,9 @@ x2c_status solve_transforms(x2c_ctx *ctx, cudaStream_t st, double c, int nb, int
   // 1. Cholesky factors and inverses of S and T.
   const size_t smem = (size_t)n2 * sizeof(double);
   X2C_TRY_CUDA(ctx, cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  tbegin(ctx, st);
   chol_inv_kernel<<<2 * nb, 256, smem, st>>>(d_in, n, fac, inv, status);
-  X2C_TRY(launched(ctx, "chol_inv_kernel"));
+  X2C_TRY(launched(ctx, "chol_inv_kernel", st));
   // L_S at fac + 2b n2, L_T at fac + (2b+1) n2; inverses likewise in inv.
   const double rt2c = std::sqrt(2.0) * c;
   {
@@ -332,10 +333,12 @@ x2c_status solve_transforms(x2c_ctx *ctx, cudaStream_t st, double c, int nb, int
                                  MatDiv<true>{inv + n2, n, 2 * n2, nc, 1.0}, StoreAxpby{Wt, nullptr, n, n2, 0.5, 0.0}, dims)));
   }
   // 2. Z = H^p + c^2, scaled into [-1, 1].
+  tbegin(ctx, st);
   assemble_hp_kernel<<<nb * nc, 256, 0, st>>>(n, nc, c, Vt, LSm, Wt, Z);
-  X2C_TRY(launched(ctx, "assemble_hp_kernel"));
+  X2C_TRY(launched(ctx, "assemble_hp_kernel", st));
+  tbegin(ctx, st);
   normalise_kernel<<<nb, 256, 0, st>>>(d, nc, Z, status);
-  X2C_TRY(launched(ctx, "normalise_kernel"));
+  X2C_TRY(launched(ctx, "normalise_kernel", st));
   // 3. Sign function by the scaled Newton-Schulz schedule.
   const std::vector<double> sched = sign_schedule(kSignLowerBound);
   for (double a : sched) {
@@ -345,14 +348,17 @@ x2c_status solve_transforms(x2c_ctx *ctx, cudaStream_t st, double c, int nb, int
     X2C_TRY(quat_gemm(ctx, st, nb, d, nc, Z, Y, 1.0, upd));
     std::swap(Z, Zn);
   }
+  tbegin(ctx, st);
   check_kernel<<<nb, 256, 0, st>>>(d, nc, Y, Z, kSignTol, 1, status);
-  X2C_TRY(launched(ctx, "check_kernel"));
+  X2C_TRY(launched(ctx, "check_kernel", st));
+  tbegin(ctx, st);
   projector_kernel<<<nb * nc, 256, 0, st>>>(n, nc, Z, PLL, PSL);
-  X2C_TRY(launched(ctx, "projector_kernel"));
+  X2C_TRY(launched(ctx, "projector_kernel", st));
   // 4. Coupled Newton-Schulz: Yk -> P_LL^1/2, Zk -> P_LL^-1/2.
   X2C_TRY_CUDA(ctx, cudaMemcpyAsync(Yk, PLL, sizeof(double) * nb * nc * n2, cudaMemcpyDeviceToDevice, st));
+  tbegin(ctx, st);
   identity_kernel<<<nb, 256, 0, st>>>(n, nc, Zk);
-  X2C_TRY(launched(ctx, "identity_kernel"));
+  X2C_TRY(launched(ctx, "identity_kernel", st));
   for (int it = 0; it < kSqrtIters; ++it) {
     StoreShiftIdentity tm{Tm, n, (int64_t)nc * n2, n, -0.5, 1.5};
     X2C_TRY(quat_gemm(ctx, st, nb, n, nc, Zk, Yk, 1.0, tm));
@@ -361,8 +367,9 @@ x2c_status solve_transforms(x2c_ctx *ctx, cudaStream_t st, double c, int nb, int
     std::swap(Yk, Yk2);
     std::swap(Zk, Zk2);
   }
+  tbegin(ctx, st);
   check_kernel<<<nb, 256, 0, st>>>(n, nc, Tm, nullptr, kSqrtTol, 0, status);
-  X2C_TRY(launched(ctx, "check_kernel"));
+  X2C_TRY(launched(ctx, "check_kernel", st));
   // 5. X'R' = P_SL P_LL^-1/2
   X2C_TRY(quat_gemm(ctx, st, nb, n, nc, PSL, Zk, 1.0, store_plain(XR, n, nc)));
   // 6. U^L_q = L^-T (R'_q L^T),  U^S_q = sqrt2 c M^-T (X'R'_q L^T)   (batch over problem x part)
