@@ -147,6 +147,34 @@ x2c_status x2c_build_dlu_batched(x2c_ctx *ctx, const x2c_options *opt, int32_t n
 x2c_status x2c_atomic_transforms(x2c_ctx *ctx, const x2c_options *opt, int32_t n_problems,
                                  const x2c_mats *inputs, const x2c_uout *U, void *stream);
 
+/* Size of the fixed device scratch array used by x2c_atomic_transforms_noalloc (32 MiB). */
+#define X2C_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+
+/* x2c_atomic_transforms without any device allocation, for callers that cannot call
+ * cudaMalloc: code whose device memory is owned by another allocator (a serving process or
+ * framework that reserved its memory budget up front), or that must not let an allocation
+ * synchronise the device.  The paper has no counterpart; this is an interface variant of
+ * the batched decoupling solve (same kernels, same results as x2c_atomic_transforms).
+ *
+ * No context is needed.  Scratch lives in one file-scope device array of
+ * X2C_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds until the process
+ * exits.  The caller passes inputs and outputs (device pointers, as x2c_atomic_transforms);
+ * all n_problems input sets must have the same n.  The call calls no cudaMalloc, cudaFree or
+ * allocating library routine.  It returns X2C_ERR_NOMEM, before enqueueing anything, when the
+ * problems need more scratch than the array holds: about 8 (2 nc + 6 + 23 nc) n^2 bytes per
+ * problem plus 5 KB (nc = 1 spin-free, 4 two-component): e.g. up to 16 two-component problems
+ * of n = 48, or 58 spin-free ones.
+ *
+ * The first call on a device looks up the array's device address (once per device, with
+ * that device current); make that first call before any stream capture.  The call is
+ * synchronous: it waits for `stream` and returns the device-side status of this call
+ * (X2C_ERR_NOT_POSDEF, X2C_ERR_NOCONV, ...).  Every call shares the one array, which keeps the
+ * last call's contents; calls that overlap on the GPU (other host threads, other streams)
+ * race on it and must be serialised by the caller. */
+x2c_status x2c_atomic_transforms_noalloc(const x2c_options *opt, int32_t n_problems,
+                                         const x2c_mats *inputs, const x2c_uout *U,
+                                         void *stream);
+
 /* DLU from HOST buffers (pageable or pinned): copies the inputs the method reads to the
  * device, builds, and copies h back into the caller's host buffers, all on `stream`;
  * returns after the stream has finished.  Arguments as x2c_build_dlu, but every matrix

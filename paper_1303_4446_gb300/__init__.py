@@ -233,6 +233,31 @@ def x2c_atomic_transforms(ctx: Context, inputs: list, two_component=False, c=Non
     return res
 
 
+def x2c_atomic_transforms_noalloc(inputs: list, two_component=False, c=None, out=None, stream=None):
+    """x2c_atomic_transforms_noalloc: the batched decoupling solve with no device allocation
+    inside the library (fixed scratch array, no context).  Output tensors are allocated here
+    by torch unless `out` (list of (UL parts, US parts)) is given.  Synchronous."""
+    nc = 4 if two_component else 1
+    k = len(inputs)
+    ms = (abi.Mats * k)()
+    us = (abi.UOut * k)()
+    res = []
+    for i, m in enumerate(inputs):
+        ms[i] = mats_struct(m, two_component)
+        if out is not None:
+            UL, US = out[i]
+        else:
+            UL, US = _alloc_parts(ms[i].n, nc, m["S"].device), _alloc_parts(ms[i].n, nc, m["S"].device)
+        for q in range(nc):
+            us[i].UL[q] = UL[q].data_ptr()
+            us[i].US[q] = US[q].data_ptr()
+        res.append((UL, US))
+    o = options(two_component, c)
+    abi.check(abi.load().x2c_atomic_transforms_noalloc(ctypes.byref(o), k, ms, us, _stream(stream)),
+              "x2c_atomic_transforms_noalloc")
+    return res
+
+
 def x2c_build_dlu_host(ctx: Context, m: dict, offsets, atom_kind=None, kinds=None, two_component=False,
                        c=None, precision=PREC_FP64, dlu_potential=DLU_FREE_ATOM, so_same_atom_only=True,
                        n_slices=0, out=None, stream=None):

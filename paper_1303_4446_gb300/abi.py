@@ -72,6 +72,8 @@ _SIGS = {
                                              ctypes.POINTER(HOut), ctypes.c_void_p]),
     "x2c_atomic_transforms": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Options), ctypes.c_int32,
                                              ctypes.POINTER(Mats), ctypes.POINTER(UOut), ctypes.c_void_p]),
+    "x2c_atomic_transforms_noalloc": (ctypes.c_int, [ctypes.POINTER(Options), ctypes.c_int32,
+                                                     ctypes.POINTER(Mats), ctypes.POINTER(UOut), ctypes.c_void_p]),
     "x2c_build_dlu_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Options), ctypes.POINTER(Layout),
                                           ctypes.POINTER(Mats), ctypes.POINTER(HOut), ctypes.c_void_p]),
     "x2c_quaternion_to_dense": (ctypes.c_int, [ctypes.c_void_p * 4, ctypes.c_int32, ctypes.c_void_p,
