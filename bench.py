@@ -56,12 +56,13 @@ def pair_list(L):
 
 
 def kernel_flops(name, nA, nB, nc, diag):
-    """Algorithmic FP64 flops of one pair block in each assembly kernel."""
-    if name == "dlu_stage1":
+    """Algorithmic FP64-equivalent flops of one pair block in each assembly kernel (the
+    split kernels compute the same products, as digit-slice products on the tensor cores)."""
+    if name in ("dlu_stage1", "split_stage1"):
         return 8.0 * nc * nA * nB * nB
-    if name == "dlu_stage2":
+    if name in ("dlu_stage2", "split_stage2"):
         return 4.0 * nc * nc * nA * nA * nB
-    if name == "dlu_spin_orbit":
+    if name in ("dlu_spin_orbit", "split_spin_orbit"):
         return 24.0 * nA * nB * nB if diag else 0.0
     return 0.0
 
@@ -209,7 +210,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="ag309_2c", choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "split"])
+    ap.add_argument("--precision", default="split", choices=["fp64", "split"])
+    ap.add_argument("--fp64-steps", type=int, default=2,
+                    help="split runs: also time this many plain FP64 builds and compare h")
     ap.add_argument("--slices", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
@@ -292,8 +295,12 @@ def main():
                 "unit": "TFLOP/s", "kernel": dom_name,
                 "peak_source": "152 SMs x 2 DFMA/clk (measured by peak_probe.cu) x 2.07 GHz max clock"}
     else:
-        roof = {"bound": "tensor", "achieved": dom_flops / (dom_ms * 1e-3) / 1e12,
+        # tensor-core work of the split kernels: S(S+1)/2 BF16 digit products per FP64 product
+        S = args.slices or 5
+        bf16_flops = dom_flops * S * (S + 1) / 2
+        roof = {"bound": "tensor", "achieved": bf16_flops / (dom_ms * 1e-3) / 1e12,
                 "peak": peaks.get("bf16_tflops_sustained", 1730.2), "unit": "TFLOP/s", "kernel": dom_name,
+                "fp64_equiv_achieved": dom_flops / (dom_ms * 1e-3) / 1e12,
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained, of measured"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = None
@@ -314,6 +321,35 @@ def main():
             "roofline": roof, "clocks": clocks,
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in sorted(ktimes.items(), key=lambda kv: -kv[1][0])},
             "input_generation_s": t_gen}
+
+    if args.precision == "split" and args.fp64_steps > 0:
+        # the plain FP64 path on the same inputs: its rate, and the split path's error in h
+        # on every element against it (FP64 path parity: tests/test_gpu_parity.py)
+        h_split = [t.clone() for t in out]
+        prec64 = x.PREC_FP64
+
+        def build64():
+            x.x2c_build_dlu(ctx, g, mol.offsets, kinds, [gk], two_component=two_c, precision=prec64,
+                            out=out, stream=stream)
+
+        build64()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.fp64_steps):
+            build64()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ctx.status(stream)
+        ms64 = e0.elapsed_time(e1) / args.fp64_steps
+        scale = max(t.abs().max().item() for t in out)
+        err = max((a - b).abs().max().item() for a, b in zip(h_split, out)) / scale
+        line["fp64_path"] = {"value": 1e3 / ms64, "unit": "builds/s", "ms_per_step": ms64,
+                             "fp64_equiv_tflops": credited / (ms64 * 1e-3) / 1e12, "steps": args.fp64_steps}
+        line["speedup_vs_fp64_path"] = ms64 / ms_max
+        line["split_max_abs_err_rel_to_max_h"] = err
+        line["split_slices"] = args.slices or 5
+        del h_split
 
     if not args.no_e2e:
         # end to end through the host-buffer entry point: H2D of the inputs the method reads,

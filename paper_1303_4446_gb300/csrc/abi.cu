@@ -156,7 +156,8 @@ x2c_status run_plan(x2c_ctx *ctx, const x2c_options *opt, BuildPlan &plan, cudaS
   ctx->counters.pair_blocks = (int64_t)plan.pairs.size();
   if (opt->precision == X2C_PREC_SPLIT_BF16) {
     const int slices = opt->n_slices ? opt->n_slices : 5;
-    return assemble_pairs_split(ctx, st, c, nc, so_all, plan.pairs, dmols, ut, plan.max_n, slices, ar);
+    std::vector<const double *> cUL(hUL.begin(), hUL.end()), cUS(hUS.begin(), hUS.end());
+    return assemble_pairs_split(ctx, st, c, nc, so_all, plan.pairs, dmols, ut, cUL, cUS, slices, ar);
   }
   return assemble_pairs_fp64(ctx, st, c, nc, so_all, plan.pairs, dmols, ut, plan.max_n, ar);
 }

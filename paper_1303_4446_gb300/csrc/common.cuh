@@ -178,9 +178,11 @@ struct UTable {
 x2c_status assemble_pairs_fp64(x2c_ctx *ctx, cudaStream_t st, double c, int nc, int so_all_pairs,
                                const std::vector<PairDesc> &pairs, const MolDesc *d_mols,
                                UTable ut, int max_n, Arena &ar);
+// hUL/hUS: host copies of the U table (device pointers), used to build per-kind operands.
 x2c_status assemble_pairs_split(x2c_ctx *ctx, cudaStream_t st, double c, int nc, int so_all_pairs,
-                                const std::vector<PairDesc> &pairs, const MolDesc *d_mols,
-                                UTable ut, int max_n, int n_slices, Arena &ar);
+                                const std::vector<PairDesc> &pairs, const MolDesc *d_mols, UTable ut,
+                                const std::vector<const double *> &hUL, const std::vector<const double *> &hUS,
+                                int n_slices, Arena &ar);
 size_t assemble_workspace_bytes(const std::vector<PairDesc> &pairs, int nc, int max_n, int precision);
 
 }  // namespace x2c

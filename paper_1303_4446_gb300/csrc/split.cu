@@ -1,12 +1,731 @@
-// Split-precision (Ozaki) BF16 pair assembly -- not provided yet.
+// Split-precision (Ozaki) DLU pair assembly on the tcgen05 BF16 tensor cores.
+//
+// Every FP64 operand row x_k (k < K) is scaled by a power of two 2^e (|x| < 2^e) and cut
+// into S signed 8-bit digits,  x 2^-e = sum_s a_s 2^-8(s+1),  |a_0| <= 256, a_s in
+// [-128, 127] (s >= 1), each exactly representable in BF16.  A product A B is the sum of the
+// digit products A_s B_t with s + t <= S - 1; all products of one diagonal g = s + t share
+// the scale 2^-8(g+2) and accumulate in their own FP32 TMEM accumulator.  With K <= 96 every
+// partial sum is an integer below 1.75 K 2^16 < 2^24, so the FP32 accumulation is exact and
+// the only error is the dropped diagonals g >= S (relative 2^-8S of the row x column scale).
+//
+// GB300 has 2 FP64 FMA per clock per SM, so no FP64 arithmetic is used inside the pipeline:
+// digits are cut from the IEEE bits with integer operations, the epilogue recombines the S
+// accumulators as an int64 (I = sum_g acc_g 2^8(S-1-g)) with integer exponent bookkeeping,
+// and the only conversion to double is the final write of h, done with integer operations.
+//
+// Pair assembly (Eq. 8 with Eq. 42), per class of pairs sharing (U_A, U_B) and sizes:
+//   stage 1   R_AB = Mid_AB F_B          rows (Y,i) of A, K = (X,k) of B, cols (j,q)
+//             Mid = [[V, T], [T, W/4c^2 - T]]_AB,  F[(X,k),(j,q)] = U^X_{B,q}[k][j]
+//             stored transposed as int64: Rt[pair][(j,q)][(Y,i)]
+//   stage 2   O[(j,p),(i',a)] = sum_(Y,i) R_AB[(Y,i),(j,p)] U^Y_{A,a}[i][i']   (K = 2 nA)
+//             h_l[i'][j] = sum_p sign+(l,p) O[(j,p),(i', l xor p)]   (quaternion adjoint
+//             product U_A+ R_AB, combined across the 4 TMEM lanes of one j with shuffles)
+// The same-atom spin-orbit part of W enters through an FP64 correction
+//   h_AB += U^S_A+ (i sum_k sigma_k Wk_AB / 4c^2) U^S_B
+// on the pairs whose Wk block is non-zero.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <map>
+
 #include "common.cuh"
+#include "gemm_f64.cuh"
+#include "umma.cuh"
 
 namespace x2c {
+namespace {
+
+constexpr int kTileM = 128;
+constexpr long long kWaitBudget = 4000000000ll;  // ~2 s of SM clock per wait
+constexpr int kNoExp = -4000;
+
+// ------------------------------------------------------------------ integer helpers
+__device__ __forceinline__ int frexp_exp(double x) {  // |x| < 2^e  (normal x); kNoExp for 0
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+  const int be = static_cast<int>((b >> 52) & 0x7FF);
+  return be == 0 ? kNoExp : be - 1022;
+}
+
+// round(x 2^shift) for |x 2^shift| < 2^62 from the IEEE bits (subnormals flush to 0).
+__device__ __forceinline__ long long fixed_point(double x, int shift) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+  const int be = static_cast<int>((b >> 52) & 0x7FF);
+  if (be == 0) return 0;
+  const long long m = static_cast<long long>((b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull);
+  const int e = be - 1075 + shift;
+  long long v;
+  if (e >= 0) v = m << e;
+  else if (e <= -62) v = 0;
+  else v = (m + (1ll << (-e - 1))) >> (-e);
+  return (b >> 63) ? -v : v;
+}
+
+// round(I 2^shift) for integers, with |I 2^shift| < 2^62.
+__device__ __forceinline__ long long shift_round(long long I, int shift) {
+  if (shift >= 0) return I << shift;
+  if (shift <= -62) return 0;
+  return (I + (1ll << (-shift - 1))) >> (-shift);
+}
+
+template <int S>
+__device__ __forceinline__ void digits(long long F, int (&d)[S]) {
+#pragma unroll
+  for (int s = S - 1; s >= 1; --s) {
+    const long long q = (F + 128) >> 8;
+    d[s] = static_cast<int>(F - (q << 8));
+    F = q;
+  }
+  d[0] = static_cast<int>(F);
+}
+
+// I 2^E as a double, using integer operations only (round half up on the magnitude).
+__device__ __forceinline__ double scaled_to_double(long long I, int E) {
+  if (I == 0) return 0.0;
+  const unsigned long long neg = I < 0;
+  unsigned long long v = neg ? static_cast<unsigned long long>(-I) : static_cast<unsigned long long>(I);
+  const int lz = __clzll(static_cast<long long>(v));
+  const unsigned long long m = v << lz;
+  unsigned long long mant = (m >> 11) + ((m >> 10) & 1ull);
+  int ex = 63 - lz + E;
+  if (mant >> 53) {
+    mant >>= 1;
+    ex += 1;
+  }
+  const int be = ex + 1023;
+  if (be <= 0) return neg ? -0.0 : 0.0;
+  if (be >= 2047) return __longlong_as_double(static_cast<long long>((neg << 63) | (0x7FFull << 52)));
+  const unsigned long long bits = (neg << 63) | (static_cast<unsigned long long>(be) << 52) | (mant & 0xFFFFFFFFFFFFFull);
+  return __longlong_as_double(static_cast<long long>(bits));
+}
+
+// Offset (elements) of digit slice s of element (r, k) in the core-matrix tiled layout:
+// tiles of TR rows, each tile holding S slices of TR x KP BF16 values arranged as
+// [TR/8][KP/8] core matrices of 8 x 8 (one 8-element row = 16 bytes).
+__device__ __forceinline__ size_t core_off(int r, int k, int TR, int KP, int S, int s) {
+  const int tile = r / TR, rr = r - tile * TR;
+  return ((static_cast<size_t>(tile) * S + s) * TR * KP) +
+         static_cast<size_t>((rr >> 3) * (KP >> 3) + (k >> 3)) * 64 + (rr & 7) * 8 + (k & 7);
+}
+
+// Exact integer value of an FP32 holding an integer of magnitude < 2^31 (integer ops only).
+__device__ __forceinline__ long long f32_exact_int(uint32_t b) {
+  const int be = static_cast<int>((b >> 23) & 0xFF);
+  if (be == 0) return 0;
+  const long long m = static_cast<long long>((b & 0x7FFFFFu) | 0x800000u);
+  const int sh = 150 - be;
+  const long long v = sh >= 0 ? (sh >= 32 ? 0 : (m >> sh)) : (m << (-sh));
+  return (b >> 31) ? -v : v;
+}
+
+// BF16 bits of a small integer |d| <= 256 (exact; integer ops only).
+__device__ __forceinline__ __nv_bfloat16 int_to_bf16(int d) {
+  if (d == 0) return __ushort_as_bfloat16(0);
+  const uint32_t sgn = d < 0 ? 0x8000u : 0u;
+  const uint32_t a = static_cast<uint32_t>(d < 0 ? -d : d);
+  const int msb = 31 - __clz(a);
+  const uint32_t mant = msb <= 7 ? ((a << (7 - msb)) & 0x7Fu) : ((a >> (msb - 7)) & 0x7Fu);
+  return __ushort_as_bfloat16(static_cast<unsigned short>(sgn | (static_cast<uint32_t>(msb + 127) << 7) | mant));
+}
+
+__device__ __forceinline__ int warp_max(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// ------------------------------------------------------------------ slicers
+// Class description: pairs share nA, nB and the transforms U_A, U_B.
+struct ClassInfo {
+  const PairDesc *pairs;  // this chunk's pairs (device)
+  const MolDesc *mols;
+  int nA, nB, nc;
+  double inv4c2;
+};
+
+// Stage-1 A rows: (pair, Y, i) with K = (X, k) over atom B.
+struct MidRows {
+  ClassInfo ci;
+  __device__ __forceinline__ double operator()(int r, int k) const {
+    const int per = 2 * ci.nA;
+    const int p = r / per, rr = r - p * per;
+    const PairDesc &P = ci.pairs[p];
+    const MolDesc &m = ci.mols[P.mol];
+    const int Y = rr >= ci.nA, X = k >= ci.nB;
+    const int i = rr - Y * ci.nA, kk = k - X * ci.nB;
+    const int64_t o = static_cast<int64_t>(P.offA + i) * m.ld + (P.offB + kk);
+    if (!Y && !X) return m.V[o];
+    if (Y != X) return m.T[o];
+    return m.W0[o] * ci.inv4c2 - m.T[o];
+  }
+};
+
+// B operand of stage 1: rows (j, q), K = (X, k): U^X_q[k][j] of atom kind B.
+struct FtRows {
+  const double *UL, *US;
+  int n, nc;
+  __device__ __forceinline__ double operator()(int r, int k) const {
+    const int j = r / nc, q = r - j * nc;
+    const int X = k >= n, kk = k - X * n;
+    const double *U = X ? US : UL;
+    return U[(static_cast<int64_t>(q) * n + kk) * n + j];
+  }
+};
+
+// B operand of stage 2: rows (i', a), K = (Y, i): U^Y_a[i][i'] of atom kind A.
+struct GtRows {
+  const double *UL, *US;
+  int n, nc;
+  __device__ __forceinline__ double operator()(int r, int k) const {
+    const int ip = r / nc, a = r - ip * nc;
+    const int Y = k >= n, i = k - Y * n;
+    const double *U = Y ? US : UL;
+    return U[(static_cast<int64_t>(a) * n + i) * n + ip];
+  }
+};
+
+// One warp per row: exponent, fixed point, digits, BF16 slices in the core layout.  The
+// value of column k is taken as x 2^kexp[k] (exact K-equilibration; kexp may be NULL).
+template <int S, class Src>
+__global__ void slice_fp64_kernel(Src src, int rows, int rows_pad, int K, int KP, int TR, const int *kexp,
+                                  __nv_bfloat16 *out, int *rexp) {
+  const int r = static_cast<int>((blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (r >= rows_pad) return;
+  double v[4];
+  int kx[4];
+  int e = kNoExp;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int k = lane + 32 * i;
+    v[i] = (r < rows && k < K) ? src(r, k) : 0.0;
+    kx[i] = (kexp && k < K) ? kexp[k] : 0;
+    const int ei = frexp_exp(v[i]);
+    if (ei != kNoExp) e = max(e, ei + kx[i]);
+  }
+  e = warp_max(e);
+  if (e == kNoExp) e = 0;
+  if (lane == 0) rexp[r] = e;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int k = lane + 32 * i;
+    if (k >= KP) break;
+    int d[S];
+    digits<S>(fixed_point(v[i], 8 * S - e + kx[i]), d);
+#pragma unroll
+    for (int s = 0; s < S; ++s) out[core_off(r, k, TR, KP, S, s)] = int_to_bf16(d[s]);
+  }
+}
+
+// Stage-2 A rows from the int64 stage-1 result: row (pair, c), K = (Y, i) of atom A, value
+// Rt[pair][c][k] 2^(e1[pair][k] + eF[c] - 8(S+1)).  Writes the row exponent e2.
+template <int S>
+__global__ void slice_r_kernel(const long long *Rt, const int *e1, const int *eF, const int *kexp, int n_pairs,
+                               int nA, int cols1, int rows_pad, int KP, __nv_bfloat16 *out, int *e2) {
+  const int r = static_cast<int>((blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (r >= rows_pad) return;
+  const int K = 2 * nA;
+  const int rows = n_pairs * cols1;
+  const int p = r / cols1, c = r - p * cols1;
+  long long I[4];
+  int ek[4], bl = kNoExp;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int k = lane + 32 * i;
+    I[i] = 0;
+    ek[i] = 0;
+    if (r < rows && k < K) {
+      I[i] = Rt[(static_cast<int64_t>(p) * cols1 + c) * K + k];
+      ek[i] = e1[p * K + k] + kexp[k];
+      if (I[i] != 0) {
+        const unsigned long long a = I[i] < 0 ? static_cast<unsigned long long>(-I[i]) : static_cast<unsigned long long>(I[i]);
+        bl = max(bl, 64 - __clzll(static_cast<long long>(a)) + ek[i]);
+      }
+    }
+  }
+  bl = warp_max(bl);
+  if (bl == kNoExp) bl = 0;
+  if (lane == 0) e2[r] = (r < rows) ? bl + eF[c] - 8 * (S + 1) : 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int k = lane + 32 * i;
+    if (k >= KP) break;
+    int d[S];
+    digits<S>(shift_round(I[i], ek[i] - bl + 8 * S), d);
+#pragma unroll
+    for (int s = 0; s < S; ++s) out[core_off(r, k, kTileM, KP, S, s)] = int_to_bf16(d[s]);
+  }
+}
+
+// Exponent of the largest magnitude in column k of a B operand (rows x K, through Src).
+template <class Src>
+__global__ void kexp_kernel(Src src, int rows, int K, int *kexp_pos, int *kexp_neg) {
+  const int k = static_cast<int>((blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (k >= K) return;
+  int e = kNoExp;
+  for (int r = lane; r < rows; r += 32) e = max(e, frexp_exp(src(r, k)));
+  e = warp_max(e);
+  if (e == kNoExp) e = 0;
+  if (lane == 0) {
+    kexp_pos[k] = e;    // applied to the A operand's column k
+    kexp_neg[k] = -e;   // applied to the B operand's row k
+  }
+}
+
+// ------------------------------------------------------------------ epilogues
+// Stage 1: Rt[pair][(j,q)][(Y,i)] = I.
+struct Stage1Store {
+  long long *Rt;
+  int rows, nA, cols1;
+  __device__ __forceinline__ void operator()(int r, int c0, const long long (&I)[16], int) const {
+    if (r >= rows) return;
+    const int per = 2 * nA;
+    const int p = r / per, rr = r - p * per;
+    long long *base = Rt + static_cast<int64_t>(p) * cols1 * per + rr;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int c = c0 + j;
+      if (c < cols1) base[static_cast<int64_t>(c) * per] = I[j];
+    }
+  }
+};
+
+// Stage 2: quaternion combination over the 4 lanes of one j, FP64 write of h and its mirror.
+struct Stage2Store {
+  const PairDesc *pairs;
+  const MolDesc *mols;
+  const int *e2, *eG;
+  int rows, nA, nB, nc, S;
+  __device__ __forceinline__ void operator()(int r, int c0, const long long (&I)[16], int lane) const {
+    const bool valid = r < rows;
+    const int per = nc * nB;
+    const int p = valid ? r / per : 0;
+    const int rr = valid ? r - p * per : 0;
+    const int j = rr / nc, pq = rr - j * nc;
+    const PairDesc P = pairs[p];
+    const MolDesc &m = mols[P.mol];
+    const int er = valid ? e2[r] : 0;
+    const int cols = nc * nA;
+    if (nc == 1) {
+      if (!valid) return;
+#pragma unroll
+      for (int t = 0; t < 16; ++t) {
+        const int ip = c0 + t;
+        if (ip >= cols) break;
+        const double v = scaled_to_double(I[t], er + eG[ip] - 8 * (S + 1));
+        m.h[0][static_cast<int64_t>(P.offA + ip) * m.ld + (P.offB + j)] = v;
+        if (!P.diag) m.h[0][static_cast<int64_t>(P.offB + j) * m.ld + (P.offA + ip)] = v;
+      }
+      return;
+    }
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {  // four i' per 16 columns
+      const int ip = (c0 >> 2) + g;
+      const bool colv = (c0 + 4 * g) < cols;
+      long long mine = 0;
+      int emine = 0;
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        const int a = l ^ pq;
+        long long term = valid && colv ? I[4 * g + a] : 0;
+        if (quat_sign_adj(l, pq) < 0) term = -term;
+        const int E = er + (colv ? eG[ip * 4 + a] : 0);
+        int Em = E;
+        Em = max(Em, __shfl_xor_sync(0xffffffffu, Em, 1));
+        Em = max(Em, __shfl_xor_sync(0xffffffffu, Em, 2));
+        const int sh = Em - E;
+        long long t = sh >= 62 ? 0 : (term >> sh);
+        t += __shfl_xor_sync(0xffffffffu, t, 1);
+        t += __shfl_xor_sync(0xffffffffu, t, 2);
+        if (l == pq) {
+          mine = t;
+          emine = Em;
+        }
+      }
+      if (valid && colv) {
+        const double v = scaled_to_double(mine, emine - 8 * (S + 1));
+        double *h = m.h[pq];
+        h[static_cast<int64_t>(P.offA + ip) * m.ld + (P.offB + j)] = v;
+        if (!P.diag) h[static_cast<int64_t>(P.offB + j) * m.ld + (P.offA + ip)] = (pq == 0) ? v : -v;
+      }
+    }
+    (void)lane;
+  }
+};
+
+// ------------------------------------------------------------------ tcgen05 GEMM
+// C = sum_{s+t<S} A_s B_t^T for BF16 digit slices; A: [m_tiles][S][128 x KP] core layout,
+// B: [n_tiles][S][NT x KP].  One CTA per SM-slot, 128 threads; thread 0 streams A slices
+// (double buffered bulk copies) and issues the MMAs, then all four warps drain TMEM.
+template <int S, int NT, int KP>
+struct GemmShape {
+  static constexpr int KG = KP / 8;
+  static constexpr uint32_t A_TILE = kTileM * KP * 2;
+  static constexpr uint32_t B_TILE = NT * KP * 2;
+  // at least 116 KB so that one CTA (which takes all 512 TMEM columns) occupies an SM alone
+  static constexpr uint32_t SMEM_RAW = S * B_TILE + 2 * A_TILE + 128;
+  static constexpr uint32_t SMEM = SMEM_RAW > 118784u ? SMEM_RAW : 118784u;
+  static constexpr uint32_t TMEM_COLS = 512;
+  static_assert(S * NT <= 512, "accumulators exceed TMEM");
+  static_assert(KP % 16 == 0 && KP <= 128, "K");
+  static_assert(NT % 16 == 0 && NT >= 16 && NT <= 256, "N");
+};
+
+template <int S, int NT, int KP, class Epi>
+__global__ void __launch_bounds__(128, 1)
+    ozaki_gemm_kernel(const __nv_bfloat16 *__restrict__ A, const __nv_bfloat16 *__restrict__ B, int m_tiles,
+                      Epi epi, int *status) {
+  using G = GemmShape<S, NT, KP>;
+  extern __shared__ __align__(128) uint8_t smem[];
+  uint8_t *sB = smem;
+  uint8_t *sA = smem + S * G::B_TILE;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(sA + 2 * G::A_TILE);  // 0: B, 1-2: A, 3-4: MMA done
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 6);
+  const int nt = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __shared__ int failed;
+  if (threadIdx.x == 0) {
+    failed = 0;
+    for (int i = 0; i < 5; ++i) umma::mbar_init(&bars[i], 1);
+    umma::fence_barrier_init();
+  }
+  if (warp == 0) {
+    umma::tmem_alloc(tmem_slot, G::TMEM_COLS);
+    umma::tmem_relinquish();
+  }
+  __syncthreads();
+  umma::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+  constexpr uint32_t idesc = umma::idesc_bf16_f32(kTileM, NT);
+  uint32_t phA[2] = {0, 0}, phM[2] = {0, 0};
+  bool ok = true;
+  if (threadIdx.x == 0) {
+    umma::mbar_expect_tx(&bars[0], S * G::B_TILE);
+    for (int t = 0; t < S; ++t)
+      umma::bulk_g2s(sB + t * G::B_TILE, B + (static_cast<size_t>(nt) * S + t) * (G::B_TILE / 2), G::B_TILE, &bars[0]);
+    ok = umma::mbar_wait(&bars[0], 0, kWaitBudget);
+  }
+  for (int mt = blockIdx.y; mt < m_tiles; mt += gridDim.y) {
+    if (threadIdx.x == 0 && !ok) failed = 1;
+    if (threadIdx.x == 0 && ok) {
+      const __nv_bfloat16 *Atile = A + static_cast<size_t>(mt) * S * (G::A_TILE / 2);
+      umma::mbar_expect_tx(&bars[1], G::A_TILE);
+      umma::bulk_g2s(sA, Atile, G::A_TILE, &bars[1]);
+      for (int s = 0; s < S && ok; ++s) {
+        const int buf = s & 1;
+        if (s + 1 < S) {
+          const int nb = (s + 1) & 1;
+          if (s + 1 >= 2) {  // buffer nb was read by the MMAs of slice s-1
+            ok = umma::mbar_wait(&bars[3 + nb], phM[nb], kWaitBudget);
+            phM[nb] ^= 1;
+            if (!ok) break;
+          }
+          umma::mbar_expect_tx(&bars[1 + nb], G::A_TILE);
+          umma::bulk_g2s(sA + nb * G::A_TILE, Atile + static_cast<size_t>(s + 1) * (G::A_TILE / 2), G::A_TILE,
+                         &bars[1 + nb]);
+        }
+        ok = umma::mbar_wait(&bars[1 + buf], phA[buf], kWaitBudget);
+        phA[buf] ^= 1;
+        if (!ok) break;
+        umma::fence_after_sync();
+        const uint32_t a0 = umma::smem_u32(sA + buf * G::A_TILE);
+        for (int t = 0; t + s < S; ++t) {
+          const uint32_t b0 = umma::smem_u32(sB + t * G::B_TILE);
+          const uint32_t d = tmem + static_cast<uint32_t>((s + t) * NT);
+#pragma unroll
+          for (int kk = 0; kk < KP / 16; ++kk) {
+            const uint64_t ad = umma::smem_desc(a0 + kk * 256, 128, G::KG * 128);
+            const uint64_t bd = umma::smem_desc(b0 + kk * 256, 128, G::KG * 128);
+            umma::mma_bf16(d, ad, bd, idesc, (s > 0 || kk > 0) ? 1u : 0u);
+          }
+        }
+        umma::mma_commit(&bars[3 + buf]);
+      }
+      // consume the commits of the last two slices: afterwards every MMA of this tile is done
+      for (int s = (S >= 2 ? S - 2 : 0); s < S && ok; ++s) {
+        const int buf = s & 1;
+        ok = umma::mbar_wait(&bars[3 + buf], phM[buf], kWaitBudget);
+        phM[buf] ^= 1;
+      }
+      if (!ok) failed = 1;
+    }
+    __syncthreads();
+    if (failed) break;
+    umma::fence_after_sync();
+    const int row = mt * kTileM + warp * 32 + lane;
+    const uint32_t lane_addr = tmem + (static_cast<uint32_t>(warp * 32) << 16);
+#pragma unroll 1
+    for (int c = 0; c < NT; c += 16) {
+      long long I[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) I[j] = 0;
+#pragma unroll
+      for (int g = 0; g < S; ++g) {
+        uint32_t v[16];
+        umma::tmem_ld16(lane_addr + static_cast<uint32_t>(g * NT + c), v);
+        umma::tmem_ld_wait();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) I[j] = I[j] * 256 + f32_exact_int(v[j]);
+      }
+      epi(row, nt * NT + c, I, lane);
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && (failed || !ok)) {
+    flag_error(status, X2C_DEV_NOCONV);
+    // drain: give outstanding copies and MMAs time to land before the CTA releases TMEM
+    umma::mbar_wait(&bars[1], phA[0], kWaitBudget);
+    umma::mbar_wait(&bars[2], phA[1], kWaitBudget);
+    umma::mbar_wait(&bars[3], phM[0], kWaitBudget);
+    umma::mbar_wait(&bars[4], phM[1], kWaitBudget);
+  }
+  __syncthreads();
+  if (warp == 0) umma::tmem_dealloc(tmem, G::TMEM_COLS);
+}
+
+// ------------------------------------------------------------------ spin-orbit correction (FP64)
+struct SoDimsC {
+  const PairDesc *p;
+  __device__ int M(int b) const { return 4 * p[b].nA; }
+  __device__ int N(int b) const { return p[b].nB; }
+  __device__ int K(int b) const { return 4 * p[b].nB; }
+};
+struct SoLeftC {
+  const PairDesc *p;
+  const MolDesc *mols;
+  double inv4c2;
+  static constexpr bool k_contig = true;
+  __device__ __forceinline__ double operator()(int b, int r, int k) const {
+    const PairDesc &P = p[b];
+    const int pr = r / P.nA, i = r - pr * P.nA;
+    const int pq = k / P.nB, kk = k - pq * P.nB;
+    const int comp = pr ^ pq;
+    if (comp == 0) return 0.0;
+    const MolDesc &m = mols[P.mol];
+    return quat_sign(pr, pq) * inv4c2 * m.W[comp - 1][static_cast<int64_t>(P.offA + i) * m.ld + (P.offB + kk)];
+  }
+};
+struct UsStackC {
+  const PairDesc *p;
+  UTable ut;
+  static constexpr bool n_contig = true;
+  __device__ __forceinline__ double operator()(int b, int k, int j) const {
+    const PairDesc &P = p[b];
+    return ut.US[P.uB][static_cast<int64_t>(k) * P.nB + j];
+  }
+};
+struct StoreT1 {
+  double *T1;
+  int64_t per;
+  int ld;
+  __device__ __forceinline__ void operator()(int b, int r, int c, double acc) const {
+    T1[b * per + static_cast<int64_t>(r) * ld + c] = acc;
+  }
+};
+struct SoDims2 {
+  const PairDesc *p;
+  __device__ int M(int b) const { return 4 * p[b].nA; }
+  __device__ int N(int b) const { return p[b].nB; }
+  __device__ int K(int b) const { return 4 * p[b].nA; }
+};
+// A operand: Lq(U^S_A+), element ((l,i'), (q,i)) = sign+(l,q) U^S_{A, l^q}[i][i'].
+struct UsAdjLeft {
+  const PairDesc *p;
+  UTable ut;
+  static constexpr bool k_contig = false;
+  __device__ __forceinline__ double operator()(int b, int r, int k) const {
+    const PairDesc &P = p[b];
+    const int n = P.nA;
+    const int l = r / n, ip = r - l * n;
+    const int q = k / n, i = k - q * n;
+    return quat_sign_adj(l, q) * ut.US[P.uA][(static_cast<int64_t>(l ^ q) * n + i) * n + ip];
+  }
+};
+struct T1Op {
+  const double *T1;
+  int64_t per;
+  int ld;
+  static constexpr bool n_contig = true;
+  __device__ __forceinline__ double operator()(int b, int k, int j) const {
+    return T1[b * per + static_cast<int64_t>(k) * ld + j];
+  }
+};
+struct AddH {
+  const PairDesc *p;
+  const MolDesc *mols;
+  __device__ __forceinline__ void operator()(int b, int r, int j, double acc) const {
+    const PairDesc &P = p[b];
+    const MolDesc &m = mols[P.mol];
+    const int l = r / P.nA, ip = r - l * P.nA;
+    double *h = m.h[l];
+    h[static_cast<int64_t>(P.offA + ip) * m.ld + (P.offB + j)] += acc;
+    if (!P.diag) h[static_cast<int64_t>(P.offB + j) * m.ld + (P.offA + ip)] += (l == 0) ? acc : -acc;
+  }
+};
+using TileSo = TileCfg<96, 48, 16, 6, 3>;
+
+// ------------------------------------------------------------------ host orchestration
+template <int S>
+struct Runner {
+  static constexpr int NT = (S <= 5) ? 96 : 64;
+
+  template <int KP, class Epi>
+  static x2c_status gemm(x2c_ctx *ctx, cudaStream_t st, const __nv_bfloat16 *A, const __nv_bfloat16 *B,
+                         int m_tiles, int n_tiles, const Epi &epi, const char *name) {
+    using Gs = GemmShape<S, NT, KP>;
+    auto kern = ozaki_gemm_kernel<S, NT, KP, Epi>;
+    X2C_TRY_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Gs::SMEM));
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int per_n = std::max(1, std::min(m_tiles, std::max(1, sms / n_tiles)));
+    dim3 grid(n_tiles, per_n);
+    tbegin(ctx, st);
+    kern<<<grid, 128, Gs::SMEM, st>>>(A, B, m_tiles, epi, ctx->d_status);
+    return launched(ctx, name, st);
+  }
+
+  template <class Epi>
+  static x2c_status gemm_kp(x2c_ctx *ctx, cudaStream_t st, int KP, const __nv_bfloat16 *A, const __nv_bfloat16 *B,
+                            int m_tiles, int n_tiles, const Epi &epi, const char *name) {
+    switch (KP) {
+      case 16: return gemm<16>(ctx, st, A, B, m_tiles, n_tiles, epi, name);
+      case 32: return gemm<32>(ctx, st, A, B, m_tiles, n_tiles, epi, name);
+      case 48: return gemm<48>(ctx, st, A, B, m_tiles, n_tiles, epi, name);
+      case 64: return gemm<64>(ctx, st, A, B, m_tiles, n_tiles, epi, name);
+      case 80: return gemm<80>(ctx, st, A, B, m_tiles, n_tiles, epi, name);
+      case 96: return gemm<96>(ctx, st, A, B, m_tiles, n_tiles, epi, name);
+      case 112: return gemm<112>(ctx, st, A, B, m_tiles, n_tiles, epi, name);
+      case 128: return gemm<128>(ctx, st, A, B, m_tiles, n_tiles, epi, name);
+    }
+    return X2C_ERR_ARG;
+  }
+
+  template <class Src>
+  static x2c_status slice(x2c_ctx *ctx, cudaStream_t st, const Src &src, int rows, int rows_pad, int K, int KP,
+                          int TR, const int *kexp, __nv_bfloat16 *out, int *rexp, const char *name) {
+    const int threads = 256;
+    const int64_t warps = rows_pad;
+    const int blocks = static_cast<int>((warps * 32 + threads - 1) / threads);
+    tbegin(ctx, st);
+    slice_fp64_kernel<S, Src><<<blocks, threads, 0, st>>>(src, rows, rows_pad, K, KP, TR, kexp, out, rexp);
+    return launched(ctx, name, st);
+  }
+
+  template <class Src>
+  static x2c_status kexp(x2c_ctx *ctx, cudaStream_t st, const Src &src, int rows, int K, int *kpos, int *kneg) {
+    tbegin(ctx, st);
+    kexp_kernel<Src><<<(K * 32 + 255) / 256, 256, 0, st>>>(src, rows, K, kpos, kneg);
+    return launched(ctx, "split_kexp", st);
+  }
+
+  static x2c_status run(x2c_ctx *ctx, cudaStream_t st, double c, int nc, int so_all,
+                        const std::vector<PairDesc> &pairs_in, const MolDesc *d_mols, UTable ut,
+                        const std::vector<const double *> &hUL, const std::vector<const double *> &hUS,
+                        Arena &ar) {
+    const double inv4c2 = 1.0 / (4.0 * c * c);
+    // classes: pairs sharing (uA, uB) (and so nA, nB)
+    std::map<std::pair<int, int>, std::vector<PairDesc>> classes;
+    for (const auto &P : pairs_in) classes[{P.uA, P.uB}].push_back(P);
+    if (classes.size() > 64) return X2C_ERR_ARG;  // split precision needs transforms shared per kind
+    for (auto &kv : classes) {
+      const auto &cls = kv.second;
+      const int nA = cls[0].nA, nB = cls[0].nB;
+      if (2 * nA > 128 || 2 * nB > 128) return X2C_ERR_ARG;
+      const int KP1 = (2 * nB + 15) / 16 * 16, KP2 = (2 * nA + 15) / 16 * 16;
+      const int cols1 = nc * nB, cols2 = nc * nA;
+      const int ntile1 = (cols1 + NT - 1) / NT, ntile2 = (cols2 + NT - 1) / NT;
+      // per-kind B operands: F (stage 1) of U_B, G' (stage 2) of U_A
+      Arena a0 = ar;
+      __nv_bfloat16 *Fs = reinterpret_cast<__nv_bfloat16 *>(a0.take_bytes((size_t)ntile1 * NT * KP1 * S * 2));
+      __nv_bfloat16 *Gs = reinterpret_cast<__nv_bfloat16 *>(a0.take_bytes((size_t)ntile2 * NT * KP2 * S * 2));
+      int *eF = reinterpret_cast<int *>(a0.take_bytes((size_t)ntile1 * NT * 4));
+      int *eG = reinterpret_cast<int *>(a0.take_bytes((size_t)ntile2 * NT * 4));
+      // K-equilibration exponents (+ on the A operand's columns, - on the B operand's rows)
+      int *k1p = reinterpret_cast<int *>(a0.take_bytes(128 * 4)), *k1n = reinterpret_cast<int *>(a0.take_bytes(128 * 4));
+      int *k2p = reinterpret_cast<int *>(a0.take_bytes(128 * 4)), *k2n = reinterpret_cast<int *>(a0.take_bytes(128 * 4));
+      if (!k2n) return X2C_ERR_NOMEM;
+      const FtRows ft{hUL[kv.first.second], hUS[kv.first.second], nB, nc};
+      const GtRows gt{hUL[kv.first.first], hUS[kv.first.first], nA, nc};
+      X2C_TRY(kexp(ctx, st, ft, cols1, 2 * nB, k1p, k1n));
+      X2C_TRY(kexp(ctx, st, gt, cols2, 2 * nA, k2p, k2n));
+      X2C_TRY(slice(ctx, st, ft, cols1, ntile1 * NT, 2 * nB, KP1, NT, k1n, Fs, eF, "split_slice_u"));
+      X2C_TRY(slice(ctx, st, gt, cols2, ntile2 * NT, 2 * nA, KP2, NT, k2n, Gs, eG, "split_slice_u"));
+      // chunk the pairs so the per-chunk buffers fit the arena
+      const size_t per_pair = (size_t)2 * nA * KP1 * S * 2 + (size_t)2 * nA * 4 + (size_t)cols1 * 2 * nA * 8 +
+                              (size_t)cols1 * KP2 * S * 2 + (size_t)cols1 * 4 +
+                              (size_t)4 * nA * nB * 8 + 2 * sizeof(PairDesc);  // + spin-orbit scratch
+      const size_t avail = a0.cap - a0.off;
+      const size_t fixed = 4 * (size_t)(kTileM * 128 * S * 2) + 64 * 1024;
+      if (avail < fixed + per_pair) return X2C_ERR_NOMEM;
+      size_t chunk = std::min<size_t>(cls.size(), (avail - fixed) / per_pair);
+      chunk = std::max<size_t>(1, chunk);
+      for (size_t c0 = 0; c0 < cls.size(); c0 += chunk) {
+        const int np = (int)std::min(chunk, cls.size() - c0);
+        Arena a1 = a0;
+        PairDesc *dp = reinterpret_cast<PairDesc *>(a1.take_bytes(np * sizeof(PairDesc)));
+        const int rows1 = np * 2 * nA, rows1p = (rows1 + kTileM - 1) / kTileM * kTileM;
+        const int rows2 = np * cols1, rows2p = (rows2 + kTileM - 1) / kTileM * kTileM;
+        __nv_bfloat16 *A1 = reinterpret_cast<__nv_bfloat16 *>(a1.take_bytes((size_t)rows1p * KP1 * S * 2));
+        int *e1 = reinterpret_cast<int *>(a1.take_bytes((size_t)rows1p * 4));
+        long long *Rt = reinterpret_cast<long long *>(a1.take_bytes((size_t)rows2 * 2 * nA * 8));
+        __nv_bfloat16 *A2 = reinterpret_cast<__nv_bfloat16 *>(a1.take_bytes((size_t)rows2p * KP2 * S * 2));
+        int *e2 = reinterpret_cast<int *>(a1.take_bytes((size_t)rows2p * 4));
+        if (!dp || !A1 || !e1 || !Rt || !A2 || !e2) return X2C_ERR_NOMEM;
+        X2C_TRY_CUDA(ctx, cudaMemcpyAsync(dp, cls.data() + c0, np * sizeof(PairDesc), cudaMemcpyHostToDevice, st));
+        ClassInfo ci{dp, d_mols, nA, nB, nc, inv4c2};
+        X2C_TRY(slice(ctx, st, MidRows{ci}, rows1, rows1p, 2 * nB, KP1, kTileM, k1p, A1, e1, "split_slice_mid"));
+        X2C_TRY(gemm_kp(ctx, st, KP1, A1, Fs, rows1p / kTileM, ntile1, Stage1Store{Rt, rows1, nA, cols1},
+                        "split_stage1"));
+        {
+          const int threads = 256;
+          const int blocks = (int)(((int64_t)rows2p * 32 + threads - 1) / threads);
+          tbegin(ctx, st);
+          slice_r_kernel<S><<<blocks, threads, 0, st>>>(Rt, e1, eF, k2p, np, nA, cols1, rows2p, KP2, A2, e2);
+          X2C_TRY(launched(ctx, "split_slice_r", st));
+        }
+        X2C_TRY(gemm_kp(ctx, st, KP2, A2, Gs, rows2p / kTileM, ntile2,
+                        Stage2Store{dp, d_mols, e2, eG, rows2, nA, nB, nc, S}, "split_stage2"));
+        // spin-orbit middle term (FP64): diagonal pairs, or all pairs in the general case
+        if (nc == 4) {
+          std::vector<PairDesc> so;
+          for (int i = 0; i < np; ++i)
+            if (so_all || cls[c0 + i].diag) so.push_back(cls[c0 + i]);
+          if (!so.empty()) {
+            Arena a2 = a1;
+            PairDesc *ds = reinterpret_cast<PairDesc *>(a2.take_bytes(so.size() * sizeof(PairDesc)));
+            const int64_t per = (int64_t)4 * nA * nB;
+            double *T1 = a2.take(so.size() * per);
+            if (!ds || !T1) return X2C_ERR_NOMEM;
+            X2C_TRY_CUDA(ctx, cudaMemcpyAsync(ds, so.data(), so.size() * sizeof(PairDesc), cudaMemcpyHostToDevice, st));
+            X2C_TRY((gemm_f64<TileSo>(ctx, st, (int)so.size(), 4 * nA, nB, SoLeftC{ds, d_mols, inv4c2},
+                                      UsStackC{ds, ut}, StoreT1{T1, per, nB}, SoDimsC{ds}, "split_spin_orbit")));
+            X2C_TRY((gemm_f64<TileSo>(ctx, st, (int)so.size(), 4 * nA, nB, UsAdjLeft{ds, ut}, T1Op{T1, per, nB},
+                                      AddH{ds, d_mols}, SoDims2{ds}, "split_spin_orbit")));
+          }
+        }
+      }
+    }
+    return X2C_OK;
+  }
+};
+
+}  // namespace
+
 x2c_status assemble_pairs_split(x2c_ctx *ctx, cudaStream_t st, double c, int nc, int so_all_pairs,
-                                const std::vector<PairDesc> &pairs, const MolDesc *d_mols,
-                                UTable ut, int max_n, int n_slices, Arena &ar) {
-  (void)ctx; (void)st; (void)c; (void)nc; (void)so_all_pairs; (void)pairs; (void)d_mols;
-  (void)ut; (void)max_n; (void)n_slices; (void)ar;
+                                const std::vector<PairDesc> &pairs, const MolDesc *d_mols, UTable ut,
+                                const std::vector<const double *> &hUL, const std::vector<const double *> &hUS,
+                                int n_slices, Arena &ar) {
+  if (pairs.empty()) return X2C_OK;
+  switch (n_slices) {
+    case 3: return Runner<3>::run(ctx, st, c, nc, so_all_pairs, pairs, d_mols, ut, hUL, hUS, ar);
+    case 4: return Runner<4>::run(ctx, st, c, nc, so_all_pairs, pairs, d_mols, ut, hUL, hUS, ar);
+    case 5: return Runner<5>::run(ctx, st, c, nc, so_all_pairs, pairs, d_mols, ut, hUL, hUS, ar);
+    case 6: return Runner<6>::run(ctx, st, c, nc, so_all_pairs, pairs, d_mols, ut, hUL, hUS, ar);
+  }
   return X2C_ERR_ARG;
 }
+
 }  // namespace x2c

@@ -1,0 +1,93 @@
+"""GPU parity of the split-precision (BF16 Ozaki, tcgen05) DLU pair assembly.
+
+The FP64 oracle decides.  The split path is exact up to the dropped digit products (S
+slices of 8 bits: relative 2^-8S of the row x column scales, per stage); the tolerance
+stated for it is max|dh| <= 1e-9 max|h| at the default S = 5, and the error must fall as
+S grows."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O
+import paper_1303_4446_gb300 as x
+from paper_1303_4446_gb300 import workload as w
+
+pytestmark = pytest.mark.gpu
+SPLIT_TOL = 1e-9
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = x.Context(0)
+    yield c
+    c.close()
+
+
+def dev(m):
+    return {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in m.items()}
+
+
+def rel_err(h, ref_full, two_c):
+    ref = list(O.quaternion_parts(ref_full)) if two_c else [ref_full]
+    scale = np.abs(ref_full).max()
+    return max(np.abs(g.cpu().numpy() - r).max() for g, r in zip(h, ref)) / scale
+
+
+@pytest.mark.parametrize("two_c", [False, True])
+def test_split_dlu_ag4(ctx, two_c):
+    mol = w.silver_cluster(4, "s30")
+    m = w.molecule_inputs(mol, two_c)
+    kind = w.atomic_inputs(47.0, "s30", two_c)
+    ref = O.x2c_dlu(m, mol.offsets, [kind] * 4)["h"]
+    g, gk = dev(m), dev(kind)
+    errs = {}
+    for S in (3, 4, 5, 6):
+        h = x.x2c_build_dlu(ctx, g, mol.offsets, [0] * 4, [gk], two_component=two_c,
+                            precision=x.PREC_SPLIT_BF16, n_slices=S)
+        ctx.status()
+        errs[S] = rel_err(h, ref, two_c)
+    assert errs[5] <= SPLIT_TOL, errs
+    assert errs[3] > errs[4] > errs[5], errs
+
+
+@pytest.mark.parametrize("two_c", [False, True])
+def test_split_dlu_mixed_basis(ctx, two_c):
+    """Kinds of 30 and 48 functions: four classes of (A, B) sizes, padded K."""
+    mol = w.Molecule(w.fcc_sites(5), np.full(5, 47.0), ["s30", "s48", "s30", "s48", "s48"])
+    m = w.molecule_inputs(mol, two_c)
+    k30, k48 = w.atomic_inputs(47.0, "s30", two_c), w.atomic_inputs(47.0, "s48", two_c)
+    idx = [0, 1, 0, 1, 1]
+    ref = O.x2c_dlu(m, mol.offsets, [k30 if i == 0 else k48 for i in idx])["h"]
+    h = x.x2c_build_dlu(ctx, dev(m), mol.offsets, idx, [dev(k30), dev(k48)], two_component=two_c,
+                        precision=x.PREC_SPLIT_BF16)
+    ctx.status()
+    assert rel_err(h, ref, two_c) <= SPLIT_TOL
+
+
+def test_split_matches_fp64_path_ag55_2c(ctx):
+    """Ag55 two-component (1540 pair blocks, several chunks of tiles): split vs the
+    parity-tested FP64 path on every element, and vs the oracle on sampled pair blocks."""
+    mol = w.silver_cluster(55, "s48")
+    m = w.molecule_inputs(mol, True)
+    kind = w.atomic_inputs(47.0, "s48", True)
+    g, gk = dev(m), dev(kind)
+    kinds = [0] * mol.natoms
+    h64 = x.x2c_build_dlu(ctx, g, mol.offsets, kinds, [gk], two_component=True)
+    hs = x.x2c_build_dlu(ctx, g, mol.offsets, kinds, [gk], two_component=True, precision=x.PREC_SPLIT_BF16)
+    ctx.status()
+    scale = max(a.abs().max().item() for a in h64)
+    err = max((a - b).abs().max().item() for a, b in zip(hs, h64)) / scale
+    assert err <= SPLIT_TOL, err
+    # oracle on a seeded sample of pair blocks
+    r = O.x2c_full(kind)
+    rng = np.random.default_rng(5)
+    N = mol.nbf
+    for _ in range(12):
+        A, B = sorted(rng.integers(0, mol.natoms, 2))
+        ra = slice(mol.offsets[A], mol.offsets[A + 1])
+        rb = slice(mol.offsets[B], mol.offsets[B + 1])
+        blocks = {k: v[ra, rb] for k, v in m.items() if k != "S"}
+        ref = O.dlu_pair_block(blocks, r["UL"], r["US"], r["UL"], r["US"])
+        got = O.from_quaternion(*[p[ra, rb].cpu().numpy() for p in hs])
+        assert np.abs(got - ref).max() <= SPLIT_TOL * scale
