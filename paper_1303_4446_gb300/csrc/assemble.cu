@@ -24,6 +24,7 @@ struct Stage1Dims {
   __device__ int M(int b) const { return 2 * p[b].nA; }
   __device__ int N(int b) const { return nc * p[b].nB; }
   __device__ int K(int b) const { return 2 * p[b].nB; }
+  __device__ int K0(int) const { return 0; }
 };
 
 // A operand of stage 1: Mid_AB gathered from the molecular V, T, W0.
@@ -76,6 +77,7 @@ struct SoDims {
   __device__ int M(int b) const { return 4 * p[b].nA; }
   __device__ int N(int b) const { return p[b].nB; }
   __device__ int K(int b) const { return 4 * p[b].nB; }
+  __device__ int K0(int) const { return 0; }
 };
 
 // A operand: Lq(Wso) with Wso = (0, Wx, Wy, Wz)_AB / 4c^2.
@@ -123,6 +125,7 @@ struct Stage2Dims {
   __device__ int M(int b) const { return nc * p[b].nA; }
   __device__ int N(int b) const { return p[b].nB; }
   __device__ int K(int b) const { return 2 * nc * p[b].nA; }
+  __device__ int K0(int) const { return 0; }
 };
 
 // A operand of stage 2: G_A = [Lq(U^L_A+) Lq(U^S_A+)], element ((l,i), (X,q,kk)).

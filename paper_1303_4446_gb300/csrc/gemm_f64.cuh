@@ -9,6 +9,8 @@
 // stores are coalesced).
 #pragma once
 
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace x2c {
@@ -20,12 +22,13 @@ struct TileCfg {
   static_assert(BM % TM == 0 && BN % TN == 0, "tile");
 };
 
-// Shapes: M(b), N(b), K(b) per batch entry.
+// Shapes: M(b), N(b), K(b) per batch entry; the K loop runs over [K0(b), K(b)).
 struct UniformDims {
   int m, n, k;
   __device__ int M(int) const { return m; }
   __device__ int N(int) const { return n; }
   __device__ int K(int) const { return k; }
+  __device__ int K0(int) const { return 0; }
 };
 
 // A plain strided matrix operand: element (r, k) (or (k, n) for B) of batch b.
@@ -113,7 +116,7 @@ __global__ void __launch_bounds__(Cfg::NT) gemm_f64_kernel(AOp A, BOp B, COp C, 
 #pragma unroll
     for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
 
-  for (int k0 = 0; k0 < K; k0 += KC) {
+  for (int k0 = D.K0(b); k0 < K; k0 += KC) {
     for (int idx = tid; idx < BM * KC; idx += NT) {
       int r, kk;
       if (AOp::k_contig) { r = idx / KC; kk = idx - r * KC; }
@@ -167,6 +170,78 @@ inline x2c_status gemm_f64(x2c_ctx *ctx, cudaStream_t st, int batch, int max_m, 
   tbegin(ctx, st);
   gemm_f64_kernel<Cfg><<<grid, Cfg::NT, 0, st>>>(A, B, C, D, tiles_n);
   return launched(ctx, name, st);
+}
+
+// ---- split-K: batch entry b' = split * batch + b computes the K range of its split into a
+// partial buffer; a second kernel sums the splits in a fixed order (deterministic) and
+// applies the epilogue.
+template <class Op>
+struct SplitOp {
+  Op op;
+  int batch;
+  static constexpr bool k_contig = Op::k_contig;
+  __device__ __forceinline__ double operator()(int b, int r, int k) const { return op(b % batch, r, k); }
+};
+template <class Op>
+struct SplitOpB {
+  Op op;
+  int batch;
+  static constexpr bool n_contig = Op::n_contig;
+  __device__ __forceinline__ double operator()(int b, int k, int n) const { return op(b % batch, k, n); }
+};
+struct SplitDims {
+  int m, n, k, kc, batch;
+  __device__ int M(int) const { return m; }
+  __device__ int N(int) const { return n; }
+  __device__ int K0(int b) const { return (b / batch) * kc; }
+  __device__ int K(int b) const { return min(k, (b / batch + 1) * kc); }
+};
+struct PartialStore {
+  double *part;
+  int64_t mn;
+  int n;
+  __device__ __forceinline__ void operator()(int b, int r, int c, double acc) const {
+    part[b * mn + static_cast<int64_t>(r) * n + c] = acc;
+  }
+};
+template <class COp>
+__global__ void splitk_reduce_kernel(const double *part, int splits, int batch, int m, int n, COp C) {
+  const int64_t mn = static_cast<int64_t>(m) * n;
+  const int64_t total = mn * batch;
+  for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
+       idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int b = static_cast<int>(idx / mn);
+    const int64_t rc = idx - b * mn;
+    double s = 0.0;
+    for (int sp = 0; sp < splits; ++sp) s += part[(static_cast<int64_t>(sp) * batch + b) * mn + rc];
+    C(b, static_cast<int>(rc / n), static_cast<int>(rc % n), s);
+  }
+}
+
+// Uniform-shape batched GEMM with split-K so that small products still fill the GPU.
+// `part` must hold splits * batch * m * n doubles (splits chosen by the caller).
+template <class Cfg, class AOp, class BOp, class COp>
+inline x2c_status gemm_f64_splitk(x2c_ctx *ctx, cudaStream_t st, int batch, int m, int n, int k, int splits,
+                                  double *part, const AOp &A, const BOp &B, const COp &C, const char *name) {
+  if (splits <= 1) return gemm_f64<Cfg>(ctx, st, batch, m, n, A, B, C, UniformDims{m, n, k}, name);
+  const int kc = ((k + splits - 1) / splits + Cfg::KC - 1) / Cfg::KC * Cfg::KC;
+  splits = (k + kc - 1) / kc;
+  X2C_TRY((gemm_f64<Cfg>(ctx, st, batch * splits, m, n, SplitOp<AOp>{A, batch}, SplitOpB<BOp>{B, batch},
+                         PartialStore{part, static_cast<int64_t>(m) * n, n}, SplitDims{m, n, k, kc, batch}, name)));
+  const int64_t total = static_cast<int64_t>(m) * n * batch;
+  const int blocks = static_cast<int>(std::min<int64_t>((total + 255) / 256, 152 * 8));
+  tbegin(ctx, st);
+  splitk_reduce_kernel<<<blocks, 256, 0, st>>>(part, splits, batch, m, n, C);
+  return launched(ctx, "splitk_reduce", st);
+}
+
+// Split count that gives about two waves of CTAs on 152 SMs.
+template <class Cfg>
+inline int choose_splits(int batch, int m, int n, int k) {
+  const int tiles = ((m + Cfg::BM - 1) / Cfg::BM) * ((n + Cfg::BN - 1) / Cfg::BN) * batch;
+  int s = (2 * 152 + tiles - 1) / tiles;
+  s = std::max(1, std::min(s, k / (2 * Cfg::KC)));
+  return s;
 }
 
 // Default tile for the dense (square-ish) products of the decoupling solve.

@@ -21,6 +21,7 @@
 //     U^S = K_S X' R' K_L^-1 = sqrt2 c M^-T P_SL P_LL^-1/2 L^T.
 // Two-component matrices are handled in the quaternion form (four real parts), so every
 // product is a real GEMM with the quaternion left-multiplication matrix read in place.
+#include <algorithm>
 #include <cmath>
 
 #include "common.cuh"
@@ -269,13 +270,23 @@ __global__ void identity_kernel(int n, int nc, double *X) {
 }
 
 // Quaternion product C = A B for nb problems (parts m x m): C_stack = Lq(A) B_stack.
+// Small problems are split along K into a partial buffer (`part`, see quat_part_doubles).
 template <class COp>
 x2c_status quat_gemm(x2c_ctx *ctx, cudaStream_t st, int nb, int m, int nc, const double *A,
-                     const double *B, double scale, const COp &C) {
+                     const double *B, double scale, const COp &C, double *part) {
   QuatLeft<false> a{A, m, (int64_t)nc * m * m, (int64_t)m * m, m, nc, scale};
   Mat<false> b{B, m, (int64_t)nc * m * m, 1.0};
-  UniformDims dims{nc * m, m, nc * m};
-  return gemm_f64<TileSolve>(ctx, st, nb, nc * m, m, a, b, C, dims, "solve_quat_gemm");
+  const int M = nc * m, K = nc * m;
+  const int splits = part ? choose_splits<TileSmall>(nb, M, m, K) : 1;
+  if (splits > 1) return gemm_f64_splitk<TileSmall>(ctx, st, nb, M, m, K, splits, part, a, b, C, "solve_quat_gemm");
+  return gemm_f64<TileSolve>(ctx, st, nb, M, m, a, b, C, UniformDims{M, m, K}, "solve_quat_gemm");
+}
+
+// Size of the split-K partial buffer for quat_gemm on nb problems of part size m.
+size_t quat_part_doubles(int nb, int m, int nc) {
+  const int M = nc * m, K = nc * m;
+  const int splits = choose_splits<TileSmall>(nb, M, m, K);
+  return splits > 1 ? (size_t)(splits + 1) * nb * M * m : 0;
 }
 
 inline StoreAxpby store_plain(double *out, int m, int nc) {
@@ -287,7 +298,8 @@ inline StoreAxpby store_plain(double *out, int m, int nc) {
 size_t solve_workspace_bytes(int nb, int n, int nc) {
   const size_t n2 = (size_t)n * n;
   const size_t per = (6 + 23 * (size_t)nc) * n2;
-  return arena_doubles(per * nb) + 16 * 256;
+  const size_t part = std::max(quat_part_doubles(nb, 2 * n, nc), quat_part_doubles(nb, n, nc));
+  return arena_doubles(per * nb) + arena_doubles(part) + 16 * 256;
 }
 
 x2c_status solve_transforms(x2c_ctx *ctx, cudaStream_t st, double c, int nb, int n, int nc,
@@ -306,6 +318,9 @@ x2c_status solve_transforms(x2c_ctx *ctx, cudaStream_t st, double c, int nb, int
   double *Yk2 = ar.take(nb * nc * n2), *Zk2 = ar.take(nb * nc * n2);
   double *XR = ar.take(nb * nc * n2), *tmp2 = ar.take(nb * nc * n2);
   if (!tmp2) return X2C_ERR_NOMEM;
+  const size_t part_n = std::max(quat_part_doubles(nb, d, nc), quat_part_doubles(nb, n, nc));
+  double *part = part_n ? ar.take(part_n) : nullptr;
+  if (part_n && !part) return X2C_ERR_NOMEM;
   int *status = ctx->d_status;
 
   // 1. Cholesky factors and inverses of S and T.
@@ -342,10 +357,10 @@ x2c_status solve_transforms(x2c_ctx *ctx, cudaStream_t st, double c, int nb, int
   // 3. Sign function by the scaled Newton-Schulz schedule.
   const std::vector<double> sched = sign_schedule(kSignLowerBound);
   for (double a : sched) {
-    X2C_TRY(quat_gemm(ctx, st, nb, d, nc, Z, Z, 1.0, store_plain(Y, d, nc)));
+    X2C_TRY(quat_gemm(ctx, st, nb, d, nc, Z, Z, 1.0, store_plain(Y, d, nc), part));
     // Zn = (3a/2) Z - (a^3/2) Z Y
     StoreAxpby upd{Zn, Z, d, (int64_t)nc * d2, -0.5 * a * a * a, 1.5 * a};
-    X2C_TRY(quat_gemm(ctx, st, nb, d, nc, Z, Y, 1.0, upd));
+    X2C_TRY(quat_gemm(ctx, st, nb, d, nc, Z, Y, 1.0, upd, part));
     std::swap(Z, Zn);
   }
   tbegin(ctx, st);
@@ -361,9 +376,9 @@ x2c_status solve_transforms(x2c_ctx *ctx, cudaStream_t st, double c, int nb, int
   X2C_TRY(launched(ctx, "identity_kernel", st));
   for (int it = 0; it < kSqrtIters; ++it) {
     StoreShiftIdentity tm{Tm, n, (int64_t)nc * n2, n, -0.5, 1.5};
-    X2C_TRY(quat_gemm(ctx, st, nb, n, nc, Zk, Yk, 1.0, tm));
-    X2C_TRY(quat_gemm(ctx, st, nb, n, nc, Yk, Tm, 1.0, store_plain(Yk2, n, nc)));
-    X2C_TRY(quat_gemm(ctx, st, nb, n, nc, Tm, Zk, 1.0, store_plain(Zk2, n, nc)));
+    X2C_TRY(quat_gemm(ctx, st, nb, n, nc, Zk, Yk, 1.0, tm, part));
+    X2C_TRY(quat_gemm(ctx, st, nb, n, nc, Yk, Tm, 1.0, store_plain(Yk2, n, nc), part));
+    X2C_TRY(quat_gemm(ctx, st, nb, n, nc, Tm, Zk, 1.0, store_plain(Zk2, n, nc), part));
     std::swap(Yk, Yk2);
     std::swap(Zk, Zk2);
   }
@@ -371,7 +386,7 @@ x2c_status solve_transforms(x2c_ctx *ctx, cudaStream_t st, double c, int nb, int
   check_kernel<<<nb, 256, 0, st>>>(n, nc, Tm, nullptr, kSqrtTol, 0, status);
   X2C_TRY(launched(ctx, "check_kernel", st));
   // 5. X'R' = P_SL P_LL^-1/2
-  X2C_TRY(quat_gemm(ctx, st, nb, n, nc, PSL, Zk, 1.0, store_plain(XR, n, nc)));
+  X2C_TRY(quat_gemm(ctx, st, nb, n, nc, PSL, Zk, 1.0, store_plain(XR, n, nc), part));
   // 6. U^L_q = L^-T (R'_q L^T),  U^S_q = sqrt2 c M^-T (X'R'_q L^T)   (batch over problem x part)
   {
     UniformDims dims{n, n, n};

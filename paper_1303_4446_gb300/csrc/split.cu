@@ -107,16 +107,6 @@ __device__ __forceinline__ size_t core_off(int r, int k, int TR, int KP, int S, 
          static_cast<size_t>((rr >> 3) * (KP >> 3) + (k >> 3)) * 64 + (rr & 7) * 8 + (k & 7);
 }
 
-// Exact integer value of an FP32 holding an integer of magnitude < 2^31 (integer ops only).
-__device__ __forceinline__ long long f32_exact_int(uint32_t b) {
-  const int be = static_cast<int>((b >> 23) & 0xFF);
-  if (be == 0) return 0;
-  const long long m = static_cast<long long>((b & 0x7FFFFFu) | 0x800000u);
-  const int sh = 150 - be;
-  const long long v = sh >= 0 ? (sh >= 32 ? 0 : (m >> sh)) : (m << (-sh));
-  return (b >> 31) ? -v : v;
-}
-
 // BF16 bits of a small integer |d| <= 256 (exact; integer ops only).
 __device__ __forceinline__ __nv_bfloat16 int_to_bf16(int d) {
   if (d == 0) return __ushort_as_bfloat16(0);
@@ -183,77 +173,103 @@ struct GtRows {
   }
 };
 
-// One warp per row: exponent, fixed point, digits, BF16 slices in the core layout.  The
-// value of column k is taken as x 2^kexp[k] (exact K-equilibration; kexp may be NULL).
+// One warp per group of `grp` consecutive rows (the rows of one quaternion group share a
+// power-of-two exponent, so the stage-2 epilogue can add their products without aligning):
+// exponent, fixed point, digits, BF16 slices in the core layout.  The value of column k is
+// taken as x 2^kexp[k] (exact K-equilibration; kexp may be NULL).
 template <int S, class Src>
-__global__ void slice_fp64_kernel(Src src, int rows, int rows_pad, int K, int KP, int TR, const int *kexp,
-                                  __nv_bfloat16 *out, int *rexp) {
-  const int r = static_cast<int>((blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5);
+__global__ void slice_fp64_kernel(Src src, int rows, int rows_pad, int K, int KP, int TR, int grp,
+                                  const int *kexp, __nv_bfloat16 *out, int *rexp) {
+  const int g = static_cast<int>((blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
-  if (r >= rows_pad) return;
-  double v[4];
+  if (g * grp >= rows_pad) return;
   int kx[4];
-  int e = kNoExp;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int k = lane + 32 * i;
-    v[i] = (r < rows && k < K) ? src(r, k) : 0.0;
     kx[i] = (kexp && k < K) ? kexp[k] : 0;
-    const int ei = frexp_exp(v[i]);
-    if (ei != kNoExp) e = max(e, ei + kx[i]);
+  }
+  int e = kNoExp;
+  for (int rr = 0; rr < grp; ++rr) {
+    const int r = g * grp + rr;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int k = lane + 32 * i;
+      const double v = (r < rows && k < K) ? src(r, k) : 0.0;
+      const int ei = frexp_exp(v);
+      if (ei != kNoExp) e = max(e, ei + kx[i]);
+    }
   }
   e = warp_max(e);
   if (e == kNoExp) e = 0;
-  if (lane == 0) rexp[r] = e;
+  for (int rr = 0; rr < grp; ++rr) {
+    const int r = g * grp + rr;
+    if (r >= rows_pad) break;
+    if (lane == 0) rexp[r] = e;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int k = lane + 32 * i;
-    if (k >= KP) break;
-    int d[S];
-    digits<S>(fixed_point(v[i], 8 * S - e + kx[i]), d);
+    for (int i = 0; i < 4; ++i) {
+      const int k = lane + 32 * i;
+      if (k >= KP) break;
+      const double v = (r < rows && k < K) ? src(r, k) : 0.0;
+      int d[S];
+      digits<S>(fixed_point(v, 8 * S - e + kx[i]), d);
 #pragma unroll
-    for (int s = 0; s < S; ++s) out[core_off(r, k, TR, KP, S, s)] = int_to_bf16(d[s]);
+      for (int s2 = 0; s2 < S; ++s2) out[core_off(r, k, TR, KP, S, s2)] = int_to_bf16(d[s2]);
+    }
   }
 }
 
 // Stage-2 A rows from the int64 stage-1 result: row (pair, c), K = (Y, i) of atom A, value
-// Rt[pair][c][k] 2^(e1[pair][k] + eF[c] - 8(S+1)).  Writes the row exponent e2.
+// Rt[pair][c][k] 2^(e1[pair][k] + kexp[k] + eF[c] - 8(S+1)).  One warp per group of `grp`
+// rows (same j, shared exponent; eF is shared by the group too).  Writes the exponent e2.
 template <int S>
 __global__ void slice_r_kernel(const long long *Rt, const int *e1, const int *eF, const int *kexp, int n_pairs,
-                               int nA, int cols1, int rows_pad, int KP, __nv_bfloat16 *out, int *e2) {
-  const int r = static_cast<int>((blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5);
+                               int nA, int cols1, int rows_pad, int KP, int grp, __nv_bfloat16 *out, int *e2) {
+  const int g = static_cast<int>((blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
-  if (r >= rows_pad) return;
+  if (g * grp >= rows_pad) return;
   const int K = 2 * nA;
   const int rows = n_pairs * cols1;
-  const int p = r / cols1, c = r - p * cols1;
-  long long I[4];
-  int ek[4], bl = kNoExp;
+  int bl = kNoExp;
+  for (int rr = 0; rr < grp; ++rr) {
+    const int r = g * grp + rr;
+    if (r >= rows) break;
+    const int p = r / cols1, c = r - p * cols1;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int k = lane + 32 * i;
-    I[i] = 0;
-    ek[i] = 0;
-    if (r < rows && k < K) {
-      I[i] = Rt[(static_cast<int64_t>(p) * cols1 + c) * K + k];
-      ek[i] = e1[p * K + k] + kexp[k];
-      if (I[i] != 0) {
-        const unsigned long long a = I[i] < 0 ? static_cast<unsigned long long>(-I[i]) : static_cast<unsigned long long>(I[i]);
-        bl = max(bl, 64 - __clzll(static_cast<long long>(a)) + ek[i]);
+    for (int i = 0; i < 4; ++i) {
+      const int k = lane + 32 * i;
+      if (k < K) {
+        const long long I = Rt[(static_cast<int64_t>(p) * cols1 + c) * K + k];
+        if (I != 0) {
+          const unsigned long long a = I < 0 ? static_cast<unsigned long long>(-I) : static_cast<unsigned long long>(I);
+          bl = max(bl, 64 - __clzll(static_cast<long long>(a)) + e1[p * K + k] + kexp[k]);
+        }
       }
     }
   }
   bl = warp_max(bl);
   if (bl == kNoExp) bl = 0;
-  if (lane == 0) e2[r] = (r < rows) ? bl + eF[c] - 8 * (S + 1) : 0;
+  for (int rr = 0; rr < grp; ++rr) {
+    const int r = g * grp + rr;
+    if (r >= rows_pad) break;
+    const bool valid = r < rows;
+    const int p = valid ? r / cols1 : 0, c = valid ? r - p * cols1 : 0;
+    if (lane == 0) e2[r] = valid ? bl + eF[c] - 8 * (S + 1) : 0;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int k = lane + 32 * i;
-    if (k >= KP) break;
-    int d[S];
-    digits<S>(shift_round(I[i], ek[i] - bl + 8 * S), d);
+    for (int i = 0; i < 4; ++i) {
+      const int k = lane + 32 * i;
+      if (k >= KP) break;
+      long long I = 0;
+      int ek = 0;
+      if (valid && k < K) {
+        I = Rt[(static_cast<int64_t>(p) * cols1 + c) * K + k];
+        ek = e1[p * K + k] + kexp[k];
+      }
+      int d[S];
+      digits<S>(shift_round(I, ek - bl + 8 * S), d);
 #pragma unroll
-    for (int s = 0; s < S; ++s) out[core_off(r, k, kTileM, KP, S, s)] = int_to_bf16(d[s]);
+      for (int s2 = 0; s2 < S; ++s2) out[core_off(r, k, kTileM, KP, S, s2)] = int_to_bf16(d[s2]);
+    }
   }
 }
 
@@ -273,121 +289,178 @@ __global__ void kexp_kernel(Src src, int rows, int K, int *kexp_pos, int *kexp_n
   }
 }
 
-// ------------------------------------------------------------------ epilogues
-// Stage 1: Rt[pair][(j,q)][(Y,i)] = I.
-struct Stage1Store {
-  long long *Rt;
-  int rows, nA, cols1;
-  __device__ __forceinline__ void operator()(int r, int c0, const long long (&I)[16], int) const {
-    if (r >= rows) return;
-    const int per = 2 * nA;
-    const int p = r / per, rr = r - p * per;
-    long long *base = Rt + static_cast<int64_t>(p) * cols1 * per + rr;
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      const int c = c0 + j;
-      if (c < cols1) base[static_cast<int64_t>(c) * per] = I[j];
-    }
-  }
-};
+// ------------------------------------------------------------------ warp-specialised GEMM
+// Roles (576 threads): warp 0 lane 0 streams A digit slices through a kStages ring of bulk
+// copies; warp 1 lane 0 issues the tcgen05 MMAs; warps 2..17 (four per TMEM lane quarter,
+// each owning a quarter of the tile's columns) drain the S accumulators of a tile into int64
+// registers, release TMEM so the next tile's MMAs can start, and then run the epilogue.
+constexpr int kEpiWarps = 16;
+constexpr int kGemmThreads = 64 + 32 * kEpiWarps;
+constexpr int kStages = 4;
 
-// Stage 2: quaternion combination over the 4 lanes of one j, FP64 write of h and its mirror.
-struct Stage2Store {
-  const PairDesc *pairs;
-  const MolDesc *mols;
-  const int *e2, *eG;
-  int rows, nA, nB, nc, S;
-  __device__ __forceinline__ void operator()(int r, int c0, const long long (&I)[16], int lane) const {
-    const bool valid = r < rows;
-    const int per = nc * nB;
-    const int p = valid ? r / per : 0;
-    const int rr = valid ? r - p * per : 0;
-    const int j = rr / nc, pq = rr - j * nc;
-    const PairDesc P = pairs[p];
-    const MolDesc &m = mols[P.mol];
-    const int er = valid ? e2[r] : 0;
-    const int cols = nc * nA;
-    if (nc == 1) {
-      if (!valid) return;
-#pragma unroll
-      for (int t = 0; t < 16; ++t) {
-        const int ip = c0 + t;
-        if (ip >= cols) break;
-        const double v = scaled_to_double(I[t], er + eG[ip] - 8 * (S + 1));
-        m.h[0][static_cast<int64_t>(P.offA + ip) * m.ld + (P.offB + j)] = v;
-        if (!P.diag) m.h[0][static_cast<int64_t>(P.offB + j) * m.ld + (P.offA + ip)] = v;
-      }
-      return;
-    }
-#pragma unroll
-    for (int g = 0; g < 4; ++g) {  // four i' per 16 columns
-      const int ip = (c0 >> 2) + g;
-      const bool colv = (c0 + 4 * g) < cols;
-      long long mine = 0;
-      int emine = 0;
-#pragma unroll
-      for (int l = 0; l < 4; ++l) {
-        const int a = l ^ pq;
-        long long term = valid && colv ? I[4 * g + a] : 0;
-        if (quat_sign_adj(l, pq) < 0) term = -term;
-        const int E = er + (colv ? eG[ip * 4 + a] : 0);
-        int Em = E;
-        Em = max(Em, __shfl_xor_sync(0xffffffffu, Em, 1));
-        Em = max(Em, __shfl_xor_sync(0xffffffffu, Em, 2));
-        const int sh = Em - E;
-        long long t = sh >= 62 ? 0 : (term >> sh);
-        t += __shfl_xor_sync(0xffffffffu, t, 1);
-        t += __shfl_xor_sync(0xffffffffu, t, 2);
-        if (l == pq) {
-          mine = t;
-          emine = Em;
-        }
-      }
-      if (valid && colv) {
-        const double v = scaled_to_double(mine, emine - 8 * (S + 1));
-        double *h = m.h[pq];
-        h[static_cast<int64_t>(P.offA + ip) * m.ld + (P.offB + j)] = v;
-        if (!P.diag) h[static_cast<int64_t>(P.offB + j) * m.ld + (P.offA + ip)] = (pq == 0) ? v : -v;
-      }
-    }
-    (void)lane;
-  }
-};
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"r"(32 * kEpiWarps) : "memory"); }
 
-// ------------------------------------------------------------------ tcgen05 GEMM
-// C = sum_{s+t<S} A_s B_t^T for BF16 digit slices; A: [m_tiles][S][128 x KP] core layout,
-// B: [n_tiles][S][NT x KP].  One CTA per SM-slot, 128 threads; thread 0 streams A slices
-// (double buffered bulk copies) and issues the MMAs, then all four warps drain TMEM.
+// True on every epilogue thread iff `v` holds on all of them (named barrier 1 with an AND
+// reduction), so the epilogue warps always take the same branch and meet at every barrier.
+__device__ __forceinline__ bool epi_all(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}"
+      : "=r"(r)
+      : "r"(static_cast<uint32_t>(v)), "r"(32 * kEpiWarps)
+      : "memory");
+  return r != 0;
+}
+
 template <int S, int NT, int KP>
 struct GemmShape {
   static constexpr int KG = KP / 8;
   static constexpr uint32_t A_TILE = kTileM * KP * 2;
   static constexpr uint32_t B_TILE = NT * KP * 2;
-  // at least 116 KB so that one CTA (which takes all 512 TMEM columns) occupies an SM alone
-  static constexpr uint32_t SMEM_RAW = S * B_TILE + 2 * A_TILE + 128;
-  static constexpr uint32_t SMEM = SMEM_RAW > 118784u ? SMEM_RAW : 118784u;
+  static constexpr int COLS_PER_WARP = NT / 4;  // per epilogue warp
   static constexpr uint32_t TMEM_COLS = 512;
   static_assert(S * NT <= 512, "accumulators exceed TMEM");
   static_assert(KP % 16 == 0 && KP <= 128, "K");
   static_assert(NT % 16 == 0 && NT >= 16 && NT <= 256, "N");
+  static_assert(COLS_PER_WARP % 8 == 0, "columns per epilogue warp");
+};
+
+// Stage 1 epilogue: Rt[pair][(j,q)][(Y,i)] = I (coalesced along the rows of one column).
+struct Stage1Store {
+  long long *Rt;
+  int rows, nA, cols1;
+  template <int NC>
+  __device__ __forceinline__ void operator()(int mt, int nt, int NT, int rloc, int c0, const long long (&I)[NC],
+                                             int, uint8_t *) const {
+    const int r = mt * kTileM + rloc;
+    if (r < rows) {
+      const int per = 2 * nA;
+      const int p = r / per, rr = r - p * per;
+      long long *base = Rt + static_cast<int64_t>(p) * cols1 * per + rr;
+#pragma unroll
+      for (int j = 0; j < NC; ++j) {
+        const int c = nt * NT + c0 + j;
+        if (c < cols1) base[static_cast<int64_t>(c) * per] = I[j];
+      }
+    }
+  }
+};
+
+// Stage 2 epilogue: rows (pair, j, p), columns (i', a); the exponents of a row group (4 p of
+// one j) and of a column group (4 a of one i') are shared, so h_l[i'][j] =
+// sum_p sign+(l,p) O[(j,p),(i', l^p)] is an integer reduce-scatter over the 4 lanes of a j.
+// Values are staged in shared memory and written with coalesced stores (h_AB rows along j,
+// the mirror h_BA rows along i').
+struct Stage2Store {
+  const PairDesc *pairs;
+  const MolDesc *mols;
+  const int *e2, *eG;
+  int rows, nA, nB, nc, S;
+  // staging: [part][i' (NT/nc)][j (128/nc)] doubles = NT * 128 * 8 / nc bytes
+  template <int NC>
+  __device__ __forceinline__ void operator()(int mt, int nt, int NT, int rloc, int c0, const long long (&I)[NC],
+                                             int lane, uint8_t *stage) const {
+    double *sv = reinterpret_cast<double *>(stage);
+    const int JT = kTileM / nc;   // j values per tile
+    const int IT = NT / nc;       // i' values per tile
+    const int r = mt * kTileM + rloc;
+    const bool valid = r < rows;
+    const int pq = rloc % nc;     // p of this row (rows of a j are consecutive)
+    const int jl = rloc / nc;     // j slot within the tile
+    const int E = (valid ? e2[r] : 0) - 8 * (S + 1);
+    if (nc == 4) {
+#pragma unroll
+      for (int g = 0; g < NC / 4; ++g) {
+        const int il = (c0 >> 2) + g;  // i' slot within the tile
+        const int ip = nt * IT + il;
+        const bool colv = ip < nA;
+        long long t[4];
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+          const long long v = (valid && colv) ? I[4 * g + (l ^ pq)] : 0;
+          t[l] = quat_sign_adj(l, pq) < 0 ? -v : v;
+        }
+        // reduce-scatter over the quad: lane with pq = l ends up with sum_p t[l]
+        const int b0 = pq & 1, b1 = (pq >> 1) & 1;
+        long long keep0 = b0 ? t[1] : t[0], keep1 = b0 ? t[3] : t[2];
+        long long send0 = b0 ? t[0] : t[1], send1 = b0 ? t[2] : t[3];
+        keep0 += __shfl_xor_sync(0xffffffffu, send0, 1);
+        keep1 += __shfl_xor_sync(0xffffffffu, send1, 1);
+        long long keep = b1 ? keep1 : keep0, send = b1 ? keep0 : keep1;
+        keep += __shfl_xor_sync(0xffffffffu, send, 2);
+        const double h = (valid && colv) ? scaled_to_double(keep, E + eG[ip * 4]) : 0.0;
+        sv[(pq * IT + il) * JT + jl] = h;
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < NC; ++t) {
+        const int il = c0 + t;
+        const int ip = nt * IT + il;
+        const double h = (valid && ip < nA) ? scaled_to_double(I[t], E + eG[ip]) : 0.0;
+        sv[il * JT + jl] = h;
+      }
+    }
+    epi_sync();
+    // coalesced writes: thread -> (part, i', j) along j for h_AB, along i' for the mirror
+    const int tid = threadIdx.x - 64;
+    const int nthr = 32 * kEpiWarps;
+    const int total = nc * IT * JT;
+    for (int idx = tid; idx < total; idx += nthr) {
+      const int jl2 = idx % JT, rest = idx / JT;
+      const int il2 = rest % IT, part = rest / IT;
+      const int r2 = mt * kTileM + jl2 * nc;
+      const int ip = nt * IT + il2;
+      if (r2 >= rows || ip >= nA) continue;
+      const int per = nc * nB;
+      const int pi = r2 / per, j = (r2 - pi * per) / nc;
+      const PairDesc &P = pairs[pi];
+      const MolDesc &m = mols[P.mol];
+      m.h[part][static_cast<int64_t>(P.offA + ip) * m.ld + (P.offB + j)] = sv[(part * IT + il2) * JT + jl2];
+    }
+    for (int idx = tid; idx < total; idx += nthr) {
+      const int il2 = idx % IT, rest = idx / IT;
+      const int jl2 = rest % JT, part = rest / JT;
+      const int r2 = mt * kTileM + jl2 * nc;
+      const int ip = nt * IT + il2;
+      if (r2 >= rows || ip >= nA) continue;
+      const int per = nc * nB;
+      const int pi = r2 / per, j = (r2 - pi * per) / nc;
+      const PairDesc &P = pairs[pi];
+      if (P.diag) continue;
+      const MolDesc &m = mols[P.mol];
+      const double v = sv[(part * IT + il2) * JT + jl2];
+      m.h[part][static_cast<int64_t>(P.offB + j) * m.ld + (P.offA + ip)] = (part == 0) ? v : -v;
+    }
+    epi_sync();
+  }
 };
 
 template <int S, int NT, int KP, class Epi>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(kGemmThreads, 1)
     ozaki_gemm_kernel(const __nv_bfloat16 *__restrict__ A, const __nv_bfloat16 *__restrict__ B, int m_tiles,
-                      Epi epi, int *status) {
+                      Epi epi, int stage_bytes, int *status) {
   using G = GemmShape<S, NT, KP>;
   extern __shared__ __align__(128) uint8_t smem[];
   uint8_t *sB = smem;
-  uint8_t *sA = smem + S * G::B_TILE;
-  uint64_t *bars = reinterpret_cast<uint64_t *>(sA + 2 * G::A_TILE);  // 0: B, 1-2: A, 3-4: MMA done
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 6);
+  uint8_t *sA = sB + S * G::B_TILE;
+  uint8_t *sStage = sA + kStages * G::A_TILE;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(sStage + ((stage_bytes + 127) / 128) * 128);
+  uint64_t *bar_b = bars, *full = bars + 1, *empty = bars + 1 + kStages;
+  uint64_t *acc_full = bars + 1 + 2 * kStages, *acc_empty = acc_full + 1;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 1);
+  __shared__ int abort_flag_s;
+  volatile int &abort_flag = abort_flag_s;
   const int nt = blockIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __shared__ int failed;
   if (threadIdx.x == 0) {
-    failed = 0;
-    for (int i = 0; i < 5; ++i) umma::mbar_init(&bars[i], 1);
+    abort_flag = 0;
+    umma::mbar_init(bar_b, 1);
+    for (int i = 0; i < kStages; ++i) {
+      umma::mbar_init(&full[i], 1);
+      umma::mbar_init(&empty[i], 1);
+    }
+    umma::mbar_init(acc_full, 1);
+    umma::mbar_init(acc_empty, kEpiWarps);
     umma::fence_barrier_init();
   }
   if (warp == 0) {
@@ -397,89 +470,118 @@ __global__ void __launch_bounds__(128, 1)
   __syncthreads();
   umma::fence_after_sync();
   const uint32_t tmem = *tmem_slot;
-  constexpr uint32_t idesc = umma::idesc_bf16_f32(kTileM, NT);
-  uint32_t phA[2] = {0, 0}, phM[2] = {0, 0};
-  bool ok = true;
-  if (threadIdx.x == 0) {
-    umma::mbar_expect_tx(&bars[0], S * G::B_TILE);
-    for (int t = 0; t < S; ++t)
-      umma::bulk_g2s(sB + t * G::B_TILE, B + (static_cast<size_t>(nt) * S + t) * (G::B_TILE / 2), G::B_TILE, &bars[0]);
-    ok = umma::mbar_wait(&bars[0], 0, kWaitBudget);
-  }
-  for (int mt = blockIdx.y; mt < m_tiles; mt += gridDim.y) {
-    if (threadIdx.x == 0 && !ok) failed = 1;
-    if (threadIdx.x == 0 && ok) {
-      const __nv_bfloat16 *Atile = A + static_cast<size_t>(mt) * S * (G::A_TILE / 2);
-      umma::mbar_expect_tx(&bars[1], G::A_TILE);
-      umma::bulk_g2s(sA, Atile, G::A_TILE, &bars[1]);
-      for (int s = 0; s < S && ok; ++s) {
-        const int buf = s & 1;
-        if (s + 1 < S) {
-          const int nb = (s + 1) & 1;
-          if (s + 1 >= 2) {  // buffer nb was read by the MMAs of slice s-1
-            ok = umma::mbar_wait(&bars[3 + nb], phM[nb], kWaitBudget);
-            phM[nb] ^= 1;
-            if (!ok) break;
+  const int n_my = (m_tiles > static_cast<int>(blockIdx.y))
+                       ? (m_tiles - static_cast<int>(blockIdx.y) + static_cast<int>(gridDim.y) - 1) / static_cast<int>(gridDim.y)
+                       : 0;
+
+  if (warp == 0) {
+    if (lane == 0) {  // ---------------- producer
+      umma::mbar_expect_tx(bar_b, S * G::B_TILE);
+      for (int t = 0; t < S; ++t)
+        umma::bulk_g2s(sB + t * G::B_TILE, B + (static_cast<size_t>(nt) * S + t) * (G::B_TILE / 2), G::B_TILE, bar_b);
+      long long it = 0;
+      for (int ti = 0; ti < n_my && !abort_flag; ++ti) {
+        const int mt = blockIdx.y + ti * gridDim.y;
+        const __nv_bfloat16 *At = A + static_cast<size_t>(mt) * S * (G::A_TILE / 2);
+        for (int s2 = 0; s2 < S; ++s2, ++it) {
+          const int slot = static_cast<int>(it % kStages);
+          const uint32_t use = static_cast<uint32_t>(it / kStages);
+          if (use > 0 && !umma::mbar_wait(&empty[slot], (use - 1) & 1, kWaitBudget)) {
+            abort_flag = 1;
+            break;
           }
-          umma::mbar_expect_tx(&bars[1 + nb], G::A_TILE);
-          umma::bulk_g2s(sA + nb * G::A_TILE, Atile + static_cast<size_t>(s + 1) * (G::A_TILE / 2), G::A_TILE,
-                         &bars[1 + nb]);
+          umma::mbar_expect_tx(&full[slot], G::A_TILE);
+          umma::bulk_g2s(sA + slot * G::A_TILE, At + static_cast<size_t>(s2) * (G::A_TILE / 2), G::A_TILE, &full[slot]);
         }
-        ok = umma::mbar_wait(&bars[1 + buf], phA[buf], kWaitBudget);
-        phA[buf] ^= 1;
-        if (!ok) break;
-        umma::fence_after_sync();
-        const uint32_t a0 = umma::smem_u32(sA + buf * G::A_TILE);
-        for (int t = 0; t + s < S; ++t) {
-          const uint32_t b0 = umma::smem_u32(sB + t * G::B_TILE);
-          const uint32_t d = tmem + static_cast<uint32_t>((s + t) * NT);
-#pragma unroll
-          for (int kk = 0; kk < KP / 16; ++kk) {
-            const uint64_t ad = umma::smem_desc(a0 + kk * 256, 128, G::KG * 128);
-            const uint64_t bd = umma::smem_desc(b0 + kk * 256, 128, G::KG * 128);
-            umma::mma_bf16(d, ad, bd, idesc, (s > 0 || kk > 0) ? 1u : 0u);
-          }
-        }
-        umma::mma_commit(&bars[3 + buf]);
       }
-      // consume the commits of the last two slices: afterwards every MMA of this tile is done
-      for (int s = (S >= 2 ? S - 2 : 0); s < S && ok; ++s) {
-        const int buf = s & 1;
-        ok = umma::mbar_wait(&bars[3 + buf], phM[buf], kWaitBudget);
-        phM[buf] ^= 1;
+      // before the CTA may exit, every issued copy must have landed
+      for (long long j = (it > kStages ? it - kStages : 0); j < it; ++j) {
+        const int slot = static_cast<int>(j % kStages);
+        umma::mbar_wait(&full[slot], static_cast<uint32_t>(j / kStages) & 1, kWaitBudget);
       }
-      if (!ok) failed = 1;
     }
-    __syncthreads();
-    if (failed) break;
-    umma::fence_after_sync();
-    const int row = mt * kTileM + warp * 32 + lane;
-    const uint32_t lane_addr = tmem + (static_cast<uint32_t>(warp * 32) << 16);
-#pragma unroll 1
-    for (int c = 0; c < NT; c += 16) {
-      long long I[16];
+  } else if (warp == 1) {
+    if (lane == 0) {  // ---------------- MMA issuer
+      constexpr uint32_t idesc = umma::idesc_bf16_f32(kTileM, NT);
+      bool ok = umma::mbar_wait(bar_b, 0, kWaitBudget);
+      long long it = 0;
+      for (int ti = 0; ti < n_my && ok && !abort_flag; ++ti) {
+        if (ti > 0 && !umma::mbar_wait(acc_empty, (ti - 1) & 1, kWaitBudget)) {
+          ok = false;
+          break;
+        }
+        umma::fence_after_sync();
+        for (int s2 = 0; s2 < S; ++s2, ++it) {
+          const int slot = static_cast<int>(it % kStages);
+          if (!umma::mbar_wait(&full[slot], static_cast<uint32_t>(it / kStages) & 1, kWaitBudget)) {
+            ok = false;
+            break;
+          }
+          umma::fence_after_sync();
+          const uint32_t a0 = umma::smem_u32(sA + slot * G::A_TILE);
+          for (int t = 0; t + s2 < S; ++t) {
+            const uint32_t b0 = umma::smem_u32(sB + t * G::B_TILE);
+            const uint32_t d = tmem + static_cast<uint32_t>((s2 + t) * NT);
 #pragma unroll
-      for (int j = 0; j < 16; ++j) I[j] = 0;
+            for (int kk = 0; kk < KP / 16; ++kk) {
+              const uint64_t ad = umma::smem_desc(a0 + kk * 256, 128, G::KG * 128);
+              const uint64_t bd = umma::smem_desc(b0 + kk * 256, 128, G::KG * 128);
+              umma::mma_bf16(d, ad, bd, idesc, (s2 > 0 || kk > 0) ? 1u : 0u);
+            }
+          }
+          umma::mma_commit(&empty[slot]);  // slot reusable once these MMAs are done
+        }
+        if (!ok) break;
+        umma::mma_commit(acc_full);  // all MMAs of this tile done -> epilogue
+      }
+      if (!ok) {
+        abort_flag = 1;
+        flag_error(status, X2C_DEV_NOCONV);
+        umma::mma_commit(acc_full);  // fires once every MMA issued so far has completed
+        umma::mbar_wait(acc_full, 0, kWaitBudget);
+        umma::mbar_wait(acc_full, 1, kWaitBudget);
+      }
+    }
+  } else {  // ---------------- epilogue warps
+    const int e = warp - 2;
+    const int quarter = warp & 3;              // TMEM lanes 32*quarter .. +31
+    const int sub = e >> 2;                    // which quarter of the columns
+    constexpr int CW = G::COLS_PER_WARP;
+    const int rloc = quarter * 32 + lane;
+    const uint32_t lane_addr = tmem + (static_cast<uint32_t>(quarter * 32) << 16);
+    for (int ti = 0; ti < n_my; ++ti) {
+      const int mt = blockIdx.y + ti * gridDim.y;
+      const bool ok = umma::mbar_wait(acc_full, ti & 1, kWaitBudget);
+      if (!epi_all(ok)) {
+        if (threadIdx.x == 64) {
+          abort_flag = 1;
+          flag_error(status, X2C_DEV_NOCONV);
+        }
+        break;
+      }
+      umma::fence_after_sync();
+      long long I[CW];
+#pragma unroll
+      for (int j = 0; j < CW; ++j) I[j] = 0;
 #pragma unroll
       for (int g = 0; g < S; ++g) {
-        uint32_t v[16];
-        umma::tmem_ld16(lane_addr + static_cast<uint32_t>(g * NT + c), v);
-        umma::tmem_ld_wait();
 #pragma unroll
-        for (int j = 0; j < 16; ++j) I[j] = I[j] * 256 + f32_exact_int(v[j]);
+        for (int c = 0; c < CW; c += 8) {
+          uint32_t v[8];
+          asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                       : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                       : "r"(lane_addr + static_cast<uint32_t>(g * NT + sub * CW + c))
+                       : "memory");
+          umma::tmem_ld_wait();
+#pragma unroll
+          for (int j = 0; j < 8; ++j) I[c + j] = I[c + j] * 256 + __float2int_rn(__uint_as_float(v[j]));
+        }
       }
-      epi(row, nt * NT + c, I, lane);
+      umma::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(umma::smem_u32(acc_empty)) : "memory");
+      epi.template operator()<CW>(mt, nt, NT, rloc, sub * CW, I, lane, sStage);
     }
-    umma::fence_before_sync();
-    __syncthreads();
-  }
-  if (threadIdx.x == 0 && (failed || !ok)) {
-    flag_error(status, X2C_DEV_NOCONV);
-    // drain: give outstanding copies and MMAs time to land before the CTA releases TMEM
-    umma::mbar_wait(&bars[1], phA[0], kWaitBudget);
-    umma::mbar_wait(&bars[2], phA[1], kWaitBudget);
-    umma::mbar_wait(&bars[3], phM[0], kWaitBudget);
-    umma::mbar_wait(&bars[4], phM[1], kWaitBudget);
   }
   __syncthreads();
   if (warp == 0) umma::tmem_dealloc(tmem, G::TMEM_COLS);
@@ -491,6 +593,7 @@ struct SoDimsC {
   __device__ int M(int b) const { return 4 * p[b].nA; }
   __device__ int N(int b) const { return p[b].nB; }
   __device__ int K(int b) const { return 4 * p[b].nB; }
+  __device__ int K0(int) const { return 0; }
 };
 struct SoLeftC {
   const PairDesc *p;
@@ -529,6 +632,7 @@ struct SoDims2 {
   __device__ int M(int b) const { return 4 * p[b].nA; }
   __device__ int N(int b) const { return p[b].nB; }
   __device__ int K(int b) const { return 4 * p[b].nA; }
+  __device__ int K0(int) const { return 0; }
 };
 // A operand: Lq(U^S_A+), element ((l,i'), (q,i)) = sign+(l,q) U^S_{A, l^q}[i][i'].
 struct UsAdjLeft {
@@ -569,48 +673,62 @@ using TileSo = TileCfg<96, 48, 16, 6, 3>;
 // ------------------------------------------------------------------ host orchestration
 template <int S>
 struct Runner {
-  static constexpr int NT = (S <= 5) ? 96 : 64;
-
-  template <int KP, class Epi>
+  template <int NT, int KP, class Epi>
   static x2c_status gemm(x2c_ctx *ctx, cudaStream_t st, const __nv_bfloat16 *A, const __nv_bfloat16 *B,
-                         int m_tiles, int n_tiles, const Epi &epi, const char *name) {
+                         int m_tiles, int n_tiles, const Epi &epi, int stage_bytes, const char *name) {
     using Gs = GemmShape<S, NT, KP>;
     auto kern = ozaki_gemm_kernel<S, NT, KP, Epi>;
-    X2C_TRY_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Gs::SMEM));
+    const int smem = static_cast<int>(S * Gs::B_TILE + kStages * Gs::A_TILE + (stage_bytes + 127) / 128 * 128 + 256);
+    if (smem > 232448) return X2C_ERR_ARG;
+    X2C_TRY_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int per_n = std::max(1, std::min(m_tiles, std::max(1, sms / n_tiles)));
     dim3 grid(n_tiles, per_n);
     tbegin(ctx, st);
-    kern<<<grid, 128, Gs::SMEM, st>>>(A, B, m_tiles, epi, ctx->d_status);
+    kern<<<grid, kGemmThreads, smem, st>>>(A, B, m_tiles, epi, stage_bytes, ctx->d_status);
     return launched(ctx, name, st);
   }
 
-  template <class Epi>
+  template <int NT, class Epi>
   static x2c_status gemm_kp(x2c_ctx *ctx, cudaStream_t st, int KP, const __nv_bfloat16 *A, const __nv_bfloat16 *B,
-                            int m_tiles, int n_tiles, const Epi &epi, const char *name) {
+                            int m_tiles, int n_tiles, const Epi &epi, int stage_bytes, const char *name) {
     switch (KP) {
-      case 16: return gemm<16>(ctx, st, A, B, m_tiles, n_tiles, epi, name);
-      case 32: return gemm<32>(ctx, st, A, B, m_tiles, n_tiles, epi, name);
-      case 48: return gemm<48>(ctx, st, A, B, m_tiles, n_tiles, epi, name);
-      case 64: return gemm<64>(ctx, st, A, B, m_tiles, n_tiles, epi, name);
-      case 80: return gemm<80>(ctx, st, A, B, m_tiles, n_tiles, epi, name);
-      case 96: return gemm<96>(ctx, st, A, B, m_tiles, n_tiles, epi, name);
-      case 112: return gemm<112>(ctx, st, A, B, m_tiles, n_tiles, epi, name);
-      case 128: return gemm<128>(ctx, st, A, B, m_tiles, n_tiles, epi, name);
+      case 32: return gemm<NT, 32>(ctx, st, A, B, m_tiles, n_tiles, epi, stage_bytes, name);
+      case 64: return gemm<NT, 64>(ctx, st, A, B, m_tiles, n_tiles, epi, stage_bytes, name);
+      case 96: return gemm<NT, 96>(ctx, st, A, B, m_tiles, n_tiles, epi, stage_bytes, name);
+      case 128: return gemm<NT, 128>(ctx, st, A, B, m_tiles, n_tiles, epi, stage_bytes, name);
     }
     return X2C_ERR_ARG;
   }
 
+  // N tile: two-component products have 4 n columns (96 per tile, 64 when S = 6 to keep the
+  // S accumulators within 512 TMEM columns); spin-free ones n columns (64, or 32 when S = 6).
+  template <class Epi>
+  static x2c_status gemm_any(x2c_ctx *ctx, cudaStream_t st, int nc, int KP, const __nv_bfloat16 *A,
+                             const __nv_bfloat16 *B, int m_tiles, int cols, const Epi &epi, bool staged,
+                             const char *name) {
+    if (nc == 4) {
+      constexpr int NT = (S <= 5) ? 96 : 64;
+      const int stage = staged ? NT * kTileM * 8 / 4 : 0;
+      return gemm_kp<NT>(ctx, st, KP, A, B, m_tiles, (cols + NT - 1) / NT, epi, stage, name);
+    }
+    constexpr int NT = (S <= 5) ? 64 : 32;
+    const int stage = staged ? NT * kTileM * 8 : 0;
+    return gemm_kp<NT>(ctx, st, KP, A, B, m_tiles, (cols + NT - 1) / NT, epi, stage, name);
+  }
+
+  static int ntile(int nc) { return nc == 4 ? ((S <= 5) ? 96 : 64) : ((S <= 5) ? 64 : 32); }
+
   template <class Src>
   static x2c_status slice(x2c_ctx *ctx, cudaStream_t st, const Src &src, int rows, int rows_pad, int K, int KP,
-                          int TR, const int *kexp, __nv_bfloat16 *out, int *rexp, const char *name) {
+                          int TR, int grp, const int *kexp, __nv_bfloat16 *out, int *rexp, const char *name) {
     const int threads = 256;
-    const int64_t warps = rows_pad;
+    const int64_t warps = (rows_pad + grp - 1) / grp;
     const int blocks = static_cast<int>((warps * 32 + threads - 1) / threads);
     tbegin(ctx, st);
-    slice_fp64_kernel<S, Src><<<blocks, threads, 0, st>>>(src, rows, rows_pad, K, KP, TR, kexp, out, rexp);
+    slice_fp64_kernel<S, Src><<<blocks, threads, 0, st>>>(src, rows, rows_pad, K, KP, TR, grp, kexp, out, rexp);
     return launched(ctx, name, st);
   }
 
@@ -626,6 +744,7 @@ struct Runner {
                         const std::vector<const double *> &hUL, const std::vector<const double *> &hUS,
                         Arena &ar) {
     const double inv4c2 = 1.0 / (4.0 * c * c);
+    const int NT = ntile(nc);
     // classes: pairs sharing (uA, uB) (and so nA, nB)
     std::map<std::pair<int, int>, std::vector<PairDesc>> classes;
     for (const auto &P : pairs_in) classes[{P.uA, P.uB}].push_back(P);
@@ -634,7 +753,7 @@ struct Runner {
       const auto &cls = kv.second;
       const int nA = cls[0].nA, nB = cls[0].nB;
       if (2 * nA > 128 || 2 * nB > 128) return X2C_ERR_ARG;
-      const int KP1 = (2 * nB + 15) / 16 * 16, KP2 = (2 * nA + 15) / 16 * 16;
+      const int KP1 = (2 * nB + 31) / 32 * 32, KP2 = (2 * nA + 31) / 32 * 32;
       const int cols1 = nc * nB, cols2 = nc * nA;
       const int ntile1 = (cols1 + NT - 1) / NT, ntile2 = (cols2 + NT - 1) / NT;
       // per-kind B operands: F (stage 1) of U_B, G' (stage 2) of U_A
@@ -651,8 +770,8 @@ struct Runner {
       const GtRows gt{hUL[kv.first.first], hUS[kv.first.first], nA, nc};
       X2C_TRY(kexp(ctx, st, ft, cols1, 2 * nB, k1p, k1n));
       X2C_TRY(kexp(ctx, st, gt, cols2, 2 * nA, k2p, k2n));
-      X2C_TRY(slice(ctx, st, ft, cols1, ntile1 * NT, 2 * nB, KP1, NT, k1n, Fs, eF, "split_slice_u"));
-      X2C_TRY(slice(ctx, st, gt, cols2, ntile2 * NT, 2 * nA, KP2, NT, k2n, Gs, eG, "split_slice_u"));
+      X2C_TRY(slice(ctx, st, ft, cols1, ntile1 * NT, 2 * nB, KP1, NT, nc, k1n, Fs, eF, "split_slice_u"));
+      X2C_TRY(slice(ctx, st, gt, cols2, ntile2 * NT, 2 * nA, KP2, NT, nc, k2n, Gs, eG, "split_slice_u"));
       // chunk the pairs so the per-chunk buffers fit the arena
       const size_t per_pair = (size_t)2 * nA * KP1 * S * 2 + (size_t)2 * nA * 4 + (size_t)cols1 * 2 * nA * 8 +
                               (size_t)cols1 * KP2 * S * 2 + (size_t)cols1 * 4 +
@@ -676,18 +795,19 @@ struct Runner {
         if (!dp || !A1 || !e1 || !Rt || !A2 || !e2) return X2C_ERR_NOMEM;
         X2C_TRY_CUDA(ctx, cudaMemcpyAsync(dp, cls.data() + c0, np * sizeof(PairDesc), cudaMemcpyHostToDevice, st));
         ClassInfo ci{dp, d_mols, nA, nB, nc, inv4c2};
-        X2C_TRY(slice(ctx, st, MidRows{ci}, rows1, rows1p, 2 * nB, KP1, kTileM, k1p, A1, e1, "split_slice_mid"));
-        X2C_TRY(gemm_kp(ctx, st, KP1, A1, Fs, rows1p / kTileM, ntile1, Stage1Store{Rt, rows1, nA, cols1},
-                        "split_stage1"));
+        X2C_TRY(slice(ctx, st, MidRows{ci}, rows1, rows1p, 2 * nB, KP1, kTileM, 1, k1p, A1, e1, "split_slice_mid"));
+        X2C_TRY(gemm_any(ctx, st, nc, KP1, A1, Fs, rows1p / kTileM, cols1, Stage1Store{Rt, rows1, nA, cols1},
+                         false, "split_stage1"));
         {
           const int threads = 256;
-          const int blocks = (int)(((int64_t)rows2p * 32 + threads - 1) / threads);
+          const int64_t warps = rows2p / nc;
+          const int blocks = (int)((warps * 32 + threads - 1) / threads);
           tbegin(ctx, st);
-          slice_r_kernel<S><<<blocks, threads, 0, st>>>(Rt, e1, eF, k2p, np, nA, cols1, rows2p, KP2, A2, e2);
+          slice_r_kernel<S><<<blocks, threads, 0, st>>>(Rt, e1, eF, k2p, np, nA, cols1, rows2p, KP2, nc, A2, e2);
           X2C_TRY(launched(ctx, "split_slice_r", st));
         }
-        X2C_TRY(gemm_kp(ctx, st, KP2, A2, Gs, rows2p / kTileM, ntile2,
-                        Stage2Store{dp, d_mols, e2, eG, rows2, nA, nB, nc, S}, "split_stage2"));
+        X2C_TRY(gemm_any(ctx, st, nc, KP2, A2, Gs, rows2p / kTileM, cols2,
+                         Stage2Store{dp, d_mols, e2, eG, rows2, nA, nB, nc, S}, true, "split_stage2"));
         // spin-orbit middle term (FP64): diagonal pairs, or all pairs in the general case
         if (nc == 4) {
           std::vector<PairDesc> so;
