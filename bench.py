@@ -290,7 +290,19 @@ def main():
     sizes = np.diff(mol.offsets)
     dom_flops = sum(kernel_flops(dom_name, sizes[a], sizes[b], nc, a == b) for a, b in pairs) * args.steps
     peaks = measured_peaks()
-    if dom_name.startswith("dlu_") and args.precision == "fp64":
+    S_sl = args.slices or 5
+    if dom_name in ("split_slice_r", "split_slice_mid"):
+        # memory-bound digit slicers: algorithmic bytes read + written per pair block
+        KPb = lambda n: (2 * n + 31) // 32 * 32
+        def slice_bytes(nA, nB):
+            if dom_name == "split_slice_mid":
+                return 3 * nA * nB * 8 + 2 * nA * KPb(nB) * S_sl * 2
+            return nc * nB * 2 * nA * 8 + nc * nB * KPb(nA) * S_sl * 2
+        byt = sum(slice_bytes(sizes[a], sizes[b]) for a, b in pairs) * args.steps
+        hbm = peaks.get("hbm_gbs", 6684.8)
+        roof = {"bound": "hbm", "achieved": byt / (dom_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                "kernel": dom_name, "peak_source": "MEASURED_PEAKS.json hbm_gbs, of measured"}
+    elif dom_name.startswith("dlu_") and args.precision == "fp64":
         roof = {"bound": "alu", "achieved": dom_flops / (dom_ms * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "kernel": dom_name,
                 "peak_source": "152 SMs x 2 DFMA/clk (measured by peak_probe.cu) x 2.07 GHz max clock"}

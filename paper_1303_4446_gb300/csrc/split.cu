@@ -16,7 +16,7 @@
 // Pair assembly (Eq. 8 with Eq. 42), per class of pairs sharing (U_A, U_B) and sizes:
 //   stage 1   R_AB = Mid_AB F_B          rows (Y,i) of A, K = (X,k) of B, cols (j,q)
 //             Mid = [[V, T], [T, W/4c^2 - T]]_AB,  F[(X,k),(j,q)] = U^X_{B,q}[k][j]
-//             stored transposed as int64: Rt[pair][(j,q)][(Y,i)]
+//             (one pair per tile; its epilogue cuts R_AB^T straight into the stage-2 digits)
 //   stage 2   O[(j,p),(i',a)] = sum_(Y,i) R_AB[(Y,i),(j,p)] U^Y_{A,a}[i][i']   (K = 2 nA)
 //             h_l[i'][j] = sum_p sign+(l,p) O[(j,p),(i', l xor p)]   (quaternion adjoint
 //             product U_A+ R_AB, combined across the 4 TMEM lanes of one j with shuffles)
@@ -37,66 +37,9 @@ namespace {
 
 constexpr int kTileM = 128;
 constexpr long long kWaitBudget = 4000000000ll;  // ~2 s of SM clock per wait
-constexpr int kNoExp = -4000;
 
-// ------------------------------------------------------------------ integer helpers
-__device__ __forceinline__ int frexp_exp(double x) {  // |x| < 2^e  (normal x); kNoExp for 0
-  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
-  const int be = static_cast<int>((b >> 52) & 0x7FF);
-  return be == 0 ? kNoExp : be - 1022;
-}
 
-// round(x 2^shift) for |x 2^shift| < 2^62 from the IEEE bits (subnormals flush to 0).
-__device__ __forceinline__ long long fixed_point(double x, int shift) {
-  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
-  const int be = static_cast<int>((b >> 52) & 0x7FF);
-  if (be == 0) return 0;
-  const long long m = static_cast<long long>((b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull);
-  const int e = be - 1075 + shift;
-  long long v;
-  if (e >= 0) v = m << e;
-  else if (e <= -62) v = 0;
-  else v = (m + (1ll << (-e - 1))) >> (-e);
-  return (b >> 63) ? -v : v;
-}
-
-// round(I 2^shift) for integers, with |I 2^shift| < 2^62.
-__device__ __forceinline__ long long shift_round(long long I, int shift) {
-  if (shift >= 0) return I << shift;
-  if (shift <= -62) return 0;
-  return (I + (1ll << (-shift - 1))) >> (-shift);
-}
-
-template <int S>
-__device__ __forceinline__ void digits(long long F, int (&d)[S]) {
-#pragma unroll
-  for (int s = S - 1; s >= 1; --s) {
-    const long long q = (F + 128) >> 8;
-    d[s] = static_cast<int>(F - (q << 8));
-    F = q;
-  }
-  d[0] = static_cast<int>(F);
-}
-
-// I 2^E as a double, using integer operations only (round half up on the magnitude).
-__device__ __forceinline__ double scaled_to_double(long long I, int E) {
-  if (I == 0) return 0.0;
-  const unsigned long long neg = I < 0;
-  unsigned long long v = neg ? static_cast<unsigned long long>(-I) : static_cast<unsigned long long>(I);
-  const int lz = __clzll(static_cast<long long>(v));
-  const unsigned long long m = v << lz;
-  unsigned long long mant = (m >> 11) + ((m >> 10) & 1ull);
-  int ex = 63 - lz + E;
-  if (mant >> 53) {
-    mant >>= 1;
-    ex += 1;
-  }
-  const int be = ex + 1023;
-  if (be <= 0) return neg ? -0.0 : 0.0;
-  if (be >= 2047) return __longlong_as_double(static_cast<long long>((neg << 63) | (0x7FFull << 52)));
-  const unsigned long long bits = (neg << 63) | (static_cast<unsigned long long>(be) << 52) | (mant & 0xFFFFFFFFFFFFFull);
-  return __longlong_as_double(static_cast<long long>(bits));
-}
+#include "split_int.cuh"
 
 // Offset (elements) of digit slice s of element (r, k) in the core-matrix tiled layout:
 // tiles of TR rows, each tile holding S slices of TR x KP BF16 values arranged as
@@ -107,14 +50,10 @@ __device__ __forceinline__ size_t core_off(int r, int k, int TR, int KP, int S, 
          static_cast<size_t>((rr >> 3) * (KP >> 3) + (k >> 3)) * 64 + (rr & 7) * 8 + (k & 7);
 }
 
-// BF16 bits of a small integer |d| <= 256 (exact; integer ops only).
+// BF16 of a small integer |d| <= 256: the FP32 value has at most 8 significant bits, so its
+// upper 16 bits are the exact BF16 encoding.
 __device__ __forceinline__ __nv_bfloat16 int_to_bf16(int d) {
-  if (d == 0) return __ushort_as_bfloat16(0);
-  const uint32_t sgn = d < 0 ? 0x8000u : 0u;
-  const uint32_t a = static_cast<uint32_t>(d < 0 ? -d : d);
-  const int msb = 31 - __clz(a);
-  const uint32_t mant = msb <= 7 ? ((a << (7 - msb)) & 0x7Fu) : ((a >> (msb - 7)) & 0x7Fu);
-  return __ushort_as_bfloat16(static_cast<unsigned short>(sgn | (static_cast<uint32_t>(msb + 127) << 7) | mant));
+  return __ushort_as_bfloat16(static_cast<unsigned short>(__float_as_uint(static_cast<float>(d)) >> 16));
 }
 
 __device__ __forceinline__ int warp_max(int v) {
@@ -138,6 +77,24 @@ struct MidRows {
   __device__ __forceinline__ double operator()(int r, int k) const {
     const int per = 2 * ci.nA;
     const int p = r / per, rr = r - p * per;
+    const PairDesc &P = ci.pairs[p];
+    const MolDesc &m = ci.mols[P.mol];
+    const int Y = rr >= ci.nA, X = k >= ci.nB;
+    const int i = rr - Y * ci.nA, kk = k - X * ci.nB;
+    const int64_t o = static_cast<int64_t>(P.offA + i) * m.ld + (P.offB + kk);
+    if (!Y && !X) return m.V[o];
+    if (Y != X) return m.T[o];
+    return m.W0[o] * ci.inv4c2 - m.T[o];
+  }
+};
+
+// Stage-1 A rows laid out one pair per tile of TRA rows (rows 2 nA..TRA-1 are zero).
+struct MidRowsPadded {
+  ClassInfo ci;
+  int TRA;
+  __device__ __forceinline__ double operator()(int r, int k) const {
+    const int p = r / TRA, rr = r - p * TRA;
+    if (rr >= 2 * ci.nA) return 0.0;
     const PairDesc &P = ci.pairs[p];
     const MolDesc &m = ci.mols[P.mol];
     const int Y = rr >= ci.nA, X = k >= ci.nB;
@@ -173,103 +130,58 @@ struct GtRows {
   }
 };
 
-// One warp per group of `grp` consecutive rows (the rows of one quaternion group share a
-// power-of-two exponent, so the stage-2 epilogue can add their products without aligning):
-// exponent, fixed point, digits, BF16 slices in the core layout.  The value of column k is
-// taken as x 2^kexp[k] (exact K-equilibration; kexp may be NULL).
+// Slicers: one CTA of 8 warps per group of 8 rows (one core-matrix row group, whose slice s
+// is a single contiguous chunk of 8 KP BF16 values); warp rr handles row r0 + rr with
+// coalesced loads along k.  Digits are staged in shared memory in the chunk layout and the
+// CTA writes each chunk with 16-byte stores.  Rows of a quaternion group (grp = 1 or 4,
+// dividing 8) share their exponent.
 template <int S, class Src>
-__global__ void slice_fp64_kernel(Src src, int rows, int rows_pad, int K, int KP, int TR, int grp,
-                                  const int *kexp, __nv_bfloat16 *out, int *rexp) {
-  const int g = static_cast<int>((blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5);
-  const int lane = threadIdx.x & 31;
-  if (g * grp >= rows_pad) return;
+__global__ void __launch_bounds__(256) slice8_fp64_kernel(Src src, int rows, int rows_pad, int K, int KP, int TR,
+                                                          int grp, const int *kexp, __nv_bfloat16 *out, int *rexp) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int sexp[8];
+  const int rr = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r0 = blockIdx.x * 8;
+  const int r = r0 + rr;
+  __nv_bfloat16 *stg = reinterpret_cast<__nv_bfloat16 *>(smem_raw);
+  double v[4];
   int kx[4];
+  int em = kNoExp;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int k = lane + 32 * i;
     kx[i] = (kexp && k < K) ? kexp[k] : 0;
+    v[i] = (r < rows && k < K) ? src(r, k) : 0.0;
   }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int ei = frexp_exp(v[i]);
+    if (ei != kNoExp) em = max(em, ei + kx[i]);
+  }
+  em = warp_max(em);
+  if (lane == 0) sexp[rr] = em;
+  __syncthreads();
   int e = kNoExp;
-  for (int rr = 0; rr < grp; ++rr) {
-    const int r = g * grp + rr;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int k = lane + 32 * i;
-      const double v = (r < rows && k < K) ? src(r, k) : 0.0;
-      const int ei = frexp_exp(v);
-      if (ei != kNoExp) e = max(e, ei + kx[i]);
-    }
-  }
-  e = warp_max(e);
+  const int g0 = (rr / grp) * grp;
+  for (int q = g0; q < g0 + grp; ++q) e = max(e, sexp[q]);
   if (e == kNoExp) e = 0;
-  for (int rr = 0; rr < grp; ++rr) {
-    const int r = g * grp + rr;
-    if (r >= rows_pad) break;
-    if (lane == 0) rexp[r] = e;
+  if (lane == 0 && r < rows_pad) rexp[r] = e;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int k = lane + 32 * i;
-      if (k >= KP) break;
-      const double v = (r < rows && k < K) ? src(r, k) : 0.0;
+  for (int i = 0; i < 4; ++i) {
+    const int k = lane + 32 * i;
+    if (k < KP) {
       int d[S];
-      digits<S>(fixed_point(v, 8 * S - e + kx[i]), d);
+      digits<S>(fixed_point(v[i], 8 * S - e + kx[i]), d);
 #pragma unroll
-      for (int s2 = 0; s2 < S; ++s2) out[core_off(r, k, TR, KP, S, s2)] = int_to_bf16(d[s2]);
+      for (int s2 = 0; s2 < S; ++s2) stg[s2 * 8 * KP + (k >> 3) * 64 + rr * 8 + (k & 7)] = int_to_bf16(d[s2]);
     }
   }
-}
-
-// Stage-2 A rows from the int64 stage-1 result: row (pair, c), K = (Y, i) of atom A, value
-// Rt[pair][c][k] 2^(e1[pair][k] + kexp[k] + eF[c] - 8(S+1)).  One warp per group of `grp`
-// rows (same j, shared exponent; eF is shared by the group too).  Writes the exponent e2.
-template <int S>
-__global__ void slice_r_kernel(const long long *Rt, const int *e1, const int *eF, const int *kexp, int n_pairs,
-                               int nA, int cols1, int rows_pad, int KP, int grp, __nv_bfloat16 *out, int *e2) {
-  const int g = static_cast<int>((blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5);
-  const int lane = threadIdx.x & 31;
-  if (g * grp >= rows_pad) return;
-  const int K = 2 * nA;
-  const int rows = n_pairs * cols1;
-  int bl = kNoExp;
-  for (int rr = 0; rr < grp; ++rr) {
-    const int r = g * grp + rr;
-    if (r >= rows) break;
-    const int p = r / cols1, c = r - p * cols1;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int k = lane + 32 * i;
-      if (k < K) {
-        const long long I = Rt[(static_cast<int64_t>(p) * cols1 + c) * K + k];
-        if (I != 0) {
-          const unsigned long long a = I < 0 ? static_cast<unsigned long long>(-I) : static_cast<unsigned long long>(I);
-          bl = max(bl, 64 - __clzll(static_cast<long long>(a)) + e1[p * K + k] + kexp[k]);
-        }
-      }
-    }
-  }
-  bl = warp_max(bl);
-  if (bl == kNoExp) bl = 0;
-  for (int rr = 0; rr < grp; ++rr) {
-    const int r = g * grp + rr;
-    if (r >= rows_pad) break;
-    const bool valid = r < rows;
-    const int p = valid ? r / cols1 : 0, c = valid ? r - p * cols1 : 0;
-    if (lane == 0) e2[r] = valid ? bl + eF[c] - 8 * (S + 1) : 0;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int k = lane + 32 * i;
-      if (k >= KP) break;
-      long long I = 0;
-      int ek = 0;
-      if (valid && k < K) {
-        I = Rt[(static_cast<int64_t>(p) * cols1 + c) * K + k];
-        ek = e1[p * K + k] + kexp[k];
-      }
-      int d[S];
-      digits<S>(shift_round(I, ek - bl + 8 * S), d);
-#pragma unroll
-      for (int s2 = 0; s2 < S; ++s2) out[core_off(r, k, kTileM, KP, S, s2)] = int_to_bf16(d[s2]);
-    }
+  __syncthreads();
+  const int words = KP;  // 16-byte words per slice chunk (8 KP bf16)
+  for (int t = threadIdx.x; t < S * words; t += blockDim.x) {
+    const int s2 = t / words, wd = t - s2 * words;
+    reinterpret_cast<uint4 *>(out + core_off(r0, 0, TR, KP, S, s2))[wd] =
+        reinterpret_cast<const uint4 *>(stg + s2 * 8 * KP)[wd];
   }
 }
 
@@ -325,24 +237,71 @@ struct GemmShape {
   static_assert(COLS_PER_WARP % 8 == 0, "columns per epilogue warp");
 };
 
-// Stage 1 epilogue: Rt[pair][(j,q)][(Y,i)] = I (coalesced along the rows of one column).
-struct Stage1Store {
-  long long *Rt;
-  int rows, nA, cols1;
+// Stage 1 epilogue fused with the slicing of the stage-2 A operand.  A tile is one pair:
+// rows (Y, i) of atom A (2 nA <= 128), columns c = (j, q) of the N tile.  For each group of
+// NCQ columns (one j) the stage-2 row exponent is the maximum over the pair's rows of
+// bitlen(I) + e1[row] + kexp2[row]; the digits of I 2^(e1 + kexp2 - bl + 8S) go straight to
+// the stage-2 A slices (row r2 = pair * cols1 + c, k = (Y, i)) with e2[r2] = bl + eF[c] - 8(S+1).
+template <int S, int NCQ>
+struct Stage1Fused {
+  const int *e1, *k2p, *eF;
+  __nv_bfloat16 *A2;
+  int *e2;
+  int n_pairs, nA, cols1, KP2, tra;
+  static int stage_bytes(int NT) { return 4 * NT * 4 + 64; }  // per (quarter, column) maxima
   template <int NC>
   __device__ __forceinline__ void operator()(int mt, int nt, int NT, int rloc, int c0, const long long (&I)[NC],
-                                             int, uint8_t *) const {
-    const int r = mt * kTileM + rloc;
-    if (r < rows) {
-      const int per = 2 * nA;
-      const int p = r / per, rr = r - p * per;
-      long long *base = Rt + static_cast<int64_t>(p) * cols1 * per + rr;
+                                             int lane, uint8_t *stage) const {
+    int *red = reinterpret_cast<int *>(stage);  // [4 quarters][NT columns]
+    const int p = mt;
+    const int rows_p = 2 * nA;
+    const bool rowv = rloc < rows_p;
+    const int ek = rowv ? e1[p * tra + rloc] + k2p[rloc] : 0;
+    const int quarter = rloc >> 5;
+    // per-column exponent contribution of this row, reduced over the warp's 32 rows
 #pragma unroll
-      for (int j = 0; j < NC; ++j) {
-        const int c = nt * NT + c0 + j;
-        if (c < cols1) base[static_cast<int64_t>(c) * per] = I[j];
+    for (int j = 0; j < NC; ++j) {
+      int m = kNoExp;
+      if (rowv && I[j] != 0) {
+        const unsigned long long a = I[j] < 0 ? static_cast<unsigned long long>(-I[j]) : static_cast<unsigned long long>(I[j]);
+        m = 64 - __clzll(static_cast<long long>(a)) + ek;
       }
+      m = warp_max(m);
+      if (lane == 0) red[quarter * NT + c0 + j] = m;
     }
+    epi_sync();
+    const int cbase = nt * NT + c0;
+    int bl[NC];
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+      int m = max(max(red[c0 + j], red[NT + c0 + j]), max(red[2 * NT + c0 + j], red[3 * NT + c0 + j]));
+      bl[j] = m;
+    }
+    // share the exponent within each group of NCQ columns (one j)
+#pragma unroll
+    for (int j = 0; j < NC; j += NCQ) {
+      int m = kNoExp;
+#pragma unroll
+      for (int q = 0; q < NCQ; ++q) m = max(m, bl[j + q]);
+      if (m == kNoExp) m = 0;
+#pragma unroll
+      for (int q = 0; q < NCQ; ++q) bl[j + q] = m;
+    }
+    const bool kvalid = rloc < KP2;  // rows 2nA..KP2-1 write the zero padding of K
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+      const int c = cbase + j;
+      if (c >= cols1 || !kvalid) continue;
+      const int r2 = p * cols1 + c;
+      int d[S];
+      digits<S>(rowv ? shift_round(I[j], ek - bl[j] + 8 * S) : 0, d);
+      const size_t o0 = core_off(r2, rloc, kTileM, KP2, S, 0);
+      const size_t slice_stride = static_cast<size_t>(kTileM) * KP2;
+#pragma unroll
+      for (int s2 = 0; s2 < S; ++s2) A2[o0 + s2 * slice_stride] = int_to_bf16(d[s2]);
+      if (rloc == 0) e2[r2] = bl[j] + eF[c] - 8 * (S + 1);
+    }
+    epi_sync();
   }
 };
 
@@ -350,25 +309,40 @@ struct Stage1Store {
 // one j) and of a column group (4 a of one i') are shared, so h_l[i'][j] =
 // sum_p sign+(l,p) O[(j,p),(i', l^p)] is an integer reduce-scatter over the 4 lanes of a j.
 // Values are staged in shared memory and written with coalesced stores (h_AB rows along j,
-// the mirror h_BA rows along i').
+// the mirror h_BA rows along i').  NCQ = number of quaternion parts (4, or 1 spin-free).
+template <int NCQ>
 struct Stage2Store {
   const PairDesc *pairs;
   const MolDesc *mols;
   const int *e2, *eG;
-  int rows, nA, nB, nc, S;
-  // staging: [part][i' (NT/nc)][j (128/nc)] doubles = NT * 128 * 8 / nc bytes
+  int rows, nA, nB, S;
+  // staging: [part][i' (NT/NCQ)][j (128/NCQ)] doubles, then per-j-slot pair info
+  static int stage_bytes(int NT) { return NT * kTileM * 8 / NCQ + (kTileM / NCQ) * 16; }
   template <int NC>
   __device__ __forceinline__ void operator()(int mt, int nt, int NT, int rloc, int c0, const long long (&I)[NC],
                                              int lane, uint8_t *stage) const {
+    constexpr int JT = kTileM / NCQ;  // j slots per tile
+    const int IT = NT / NCQ;          // i' slots per tile
     double *sv = reinterpret_cast<double *>(stage);
-    const int JT = kTileM / nc;   // j values per tile
-    const int IT = NT / nc;       // i' values per tile
+    int4 *slot = reinterpret_cast<int4 *>(stage + static_cast<size_t>(NT) * kTileM * 8 / NCQ);
     const int r = mt * kTileM + rloc;
     const bool valid = r < rows;
-    const int pq = rloc % nc;     // p of this row (rows of a j are consecutive)
-    const int jl = rloc / nc;     // j slot within the tile
+    const int pq = rloc % NCQ;
+    const int jl = rloc / NCQ;
     const int E = (valid ? e2[r] : 0) - 8 * (S + 1);
-    if (nc == 4) {
+    const int tid = threadIdx.x - 64;
+    if (tid < JT) {  // pair of each j slot: (offA, offB + j, diag, mol), or (-1, ...) if padding
+      const int r2 = mt * kTileM + tid * NCQ;
+      int4 info = make_int4(-1, 0, 0, 0);
+      if (r2 < rows) {
+        const int per = NCQ * nB;
+        const int pi = r2 / per, j = (r2 - pi * per) / NCQ;
+        const PairDesc &P = pairs[pi];
+        info = make_int4(P.offA, P.offB + j, P.diag, P.mol);
+      }
+      slot[tid] = info;
+    }
+    if (NCQ == 4) {
 #pragma unroll
       for (int g = 0; g < NC / 4; ++g) {
         const int il = (c0 >> 2) + g;  // i' slot within the tile
@@ -383,53 +357,45 @@ struct Stage2Store {
         // reduce-scatter over the quad: lane with pq = l ends up with sum_p t[l]
         const int b0 = pq & 1, b1 = (pq >> 1) & 1;
         long long keep0 = b0 ? t[1] : t[0], keep1 = b0 ? t[3] : t[2];
-        long long send0 = b0 ? t[0] : t[1], send1 = b0 ? t[2] : t[3];
+        const long long send0 = b0 ? t[0] : t[1], send1 = b0 ? t[2] : t[3];
         keep0 += __shfl_xor_sync(0xffffffffu, send0, 1);
         keep1 += __shfl_xor_sync(0xffffffffu, send1, 1);
-        long long keep = b1 ? keep1 : keep0, send = b1 ? keep0 : keep1;
+        long long keep = b1 ? keep1 : keep0;
+        const long long send = b1 ? keep0 : keep1;
         keep += __shfl_xor_sync(0xffffffffu, send, 2);
-        const double h = (valid && colv) ? scaled_to_double(keep, E + eG[ip * 4]) : 0.0;
-        sv[(pq * IT + il) * JT + jl] = h;
+        sv[(pq * IT + il) * JT + jl] = (valid && colv) ? scaled_to_double(keep, E + eG[ip * 4]) : 0.0;
       }
     } else {
 #pragma unroll
       for (int t = 0; t < NC; ++t) {
         const int il = c0 + t;
         const int ip = nt * IT + il;
-        const double h = (valid && ip < nA) ? scaled_to_double(I[t], E + eG[ip]) : 0.0;
-        sv[il * JT + jl] = h;
+        sv[il * JT + jl] = (valid && ip < nA) ? scaled_to_double(I[t], E + eG[ip]) : 0.0;
       }
     }
+    (void)lane;
     epi_sync();
-    // coalesced writes: thread -> (part, i', j) along j for h_AB, along i' for the mirror
-    const int tid = threadIdx.x - 64;
-    const int nthr = 32 * kEpiWarps;
-    const int total = nc * IT * JT;
-    for (int idx = tid; idx < total; idx += nthr) {
+    constexpr int nthr = 32 * kEpiWarps;
+    const int iv = min(IT, nA - nt * IT);  // valid i' slots of this N tile
+    const int ip0 = nt * IT;
+    // h_AB: rows offA + i', contiguous along j
+    for (int idx = tid; idx < NCQ * IT * JT; idx += nthr) {
       const int jl2 = idx % JT, rest = idx / JT;
       const int il2 = rest % IT, part = rest / IT;
-      const int r2 = mt * kTileM + jl2 * nc;
-      const int ip = nt * IT + il2;
-      if (r2 >= rows || ip >= nA) continue;
-      const int per = nc * nB;
-      const int pi = r2 / per, j = (r2 - pi * per) / nc;
-      const PairDesc &P = pairs[pi];
-      const MolDesc &m = mols[P.mol];
-      m.h[part][static_cast<int64_t>(P.offA + ip) * m.ld + (P.offB + j)] = sv[(part * IT + il2) * JT + jl2];
+      const int4 info = slot[jl2];
+      if (info.x < 0 || il2 >= iv) continue;
+      const MolDesc &m = mols[info.w];
+      m.h[part][static_cast<int64_t>(info.x + ip0 + il2) * m.ld + info.y] = sv[(part * IT + il2) * JT + jl2];
     }
-    for (int idx = tid; idx < total; idx += nthr) {
+    // mirror h_BA = h_AB+: rows offB + j, contiguous along i'
+    for (int idx = tid; idx < NCQ * IT * JT; idx += nthr) {
       const int il2 = idx % IT, rest = idx / IT;
       const int jl2 = rest % JT, part = rest / JT;
-      const int r2 = mt * kTileM + jl2 * nc;
-      const int ip = nt * IT + il2;
-      if (r2 >= rows || ip >= nA) continue;
-      const int per = nc * nB;
-      const int pi = r2 / per, j = (r2 - pi * per) / nc;
-      const PairDesc &P = pairs[pi];
-      if (P.diag) continue;
-      const MolDesc &m = mols[P.mol];
+      const int4 info = slot[jl2];
+      if (info.x < 0 || info.z || il2 >= iv) continue;
+      const MolDesc &m = mols[info.w];
       const double v = sv[(part * IT + il2) * JT + jl2];
-      m.h[part][static_cast<int64_t>(P.offB + j) * m.ld + (P.offA + ip)] = (part == 0) ? v : -v;
+      m.h[part][static_cast<int64_t>(info.y) * m.ld + (info.x + ip0 + il2)] = (part == 0) ? v : -v;
     }
     epi_sync();
   }
@@ -438,7 +404,7 @@ struct Stage2Store {
 template <int S, int NT, int KP, class Epi>
 __global__ void __launch_bounds__(kGemmThreads, 1)
     ozaki_gemm_kernel(const __nv_bfloat16 *__restrict__ A, const __nv_bfloat16 *__restrict__ B, int m_tiles,
-                      Epi epi, int stage_bytes, int *status) {
+                      int a_rows, Epi epi, int stage_bytes, int *status) {
   using G = GemmShape<S, NT, KP>;
   extern __shared__ __align__(128) uint8_t smem[];
   uint8_t *sB = smem;
@@ -467,9 +433,17 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     umma::tmem_alloc(tmem_slot, G::TMEM_COLS);
     umma::tmem_relinquish();
   }
+  // A tiles of a_rows < 128 rows leave rows a_rows..127 of every ring slot at zero for good
+  if (a_rows < kTileM) {
+    const uint32_t row_bytes = KP * 2;  // one row spread over core matrices: zero whole 8-row groups
+    const uint32_t first = static_cast<uint32_t>(a_rows / 8) * 8 * row_bytes;
+    for (uint32_t o = first + threadIdx.x * 16; o < G::A_TILE; o += blockDim.x * 16)
+      for (int st = 0; st < kStages; ++st) *reinterpret_cast<uint4 *>(sA + st * G::A_TILE + o) = make_uint4(0, 0, 0, 0);
+  }
   __syncthreads();
   umma::fence_after_sync();
   const uint32_t tmem = *tmem_slot;
+  const uint32_t a_bytes = static_cast<uint32_t>(a_rows) * KP * 2;
   const int n_my = (m_tiles > static_cast<int>(blockIdx.y))
                        ? (m_tiles - static_cast<int>(blockIdx.y) + static_cast<int>(gridDim.y) - 1) / static_cast<int>(gridDim.y)
                        : 0;
@@ -482,7 +456,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       long long it = 0;
       for (int ti = 0; ti < n_my && !abort_flag; ++ti) {
         const int mt = blockIdx.y + ti * gridDim.y;
-        const __nv_bfloat16 *At = A + static_cast<size_t>(mt) * S * (G::A_TILE / 2);
+        const __nv_bfloat16 *At = A + static_cast<size_t>(mt) * S * (a_bytes / 2);
         for (int s2 = 0; s2 < S; ++s2, ++it) {
           const int slot = static_cast<int>(it % kStages);
           const uint32_t use = static_cast<uint32_t>(it / kStages);
@@ -490,8 +464,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             abort_flag = 1;
             break;
           }
-          umma::mbar_expect_tx(&full[slot], G::A_TILE);
-          umma::bulk_g2s(sA + slot * G::A_TILE, At + static_cast<size_t>(s2) * (G::A_TILE / 2), G::A_TILE, &full[slot]);
+          umma::mbar_expect_tx(&full[slot], a_bytes);
+          umma::bulk_g2s(sA + slot * G::A_TILE, At + static_cast<size_t>(s2) * (a_bytes / 2), a_bytes, &full[slot]);
         }
       }
       // before the CTA may exit, every issued copy must have landed
@@ -675,7 +649,7 @@ template <int S>
 struct Runner {
   template <int NT, int KP, class Epi>
   static x2c_status gemm(x2c_ctx *ctx, cudaStream_t st, const __nv_bfloat16 *A, const __nv_bfloat16 *B,
-                         int m_tiles, int n_tiles, const Epi &epi, int stage_bytes, const char *name) {
+                         int m_tiles, int n_tiles, const Epi &epi, int stage_bytes, int a_rows, const char *name) {
     using Gs = GemmShape<S, NT, KP>;
     auto kern = ozaki_gemm_kernel<S, NT, KP, Epi>;
     const int smem = static_cast<int>(S * Gs::B_TILE + kStages * Gs::A_TILE + (stage_bytes + 127) / 128 * 128 + 256);
@@ -687,36 +661,37 @@ struct Runner {
     const int per_n = std::max(1, std::min(m_tiles, std::max(1, sms / n_tiles)));
     dim3 grid(n_tiles, per_n);
     tbegin(ctx, st);
-    kern<<<grid, kGemmThreads, smem, st>>>(A, B, m_tiles, epi, stage_bytes, ctx->d_status);
+    kern<<<grid, kGemmThreads, smem, st>>>(A, B, m_tiles, a_rows, epi, stage_bytes, ctx->d_status);
     return launched(ctx, name, st);
   }
 
   template <int NT, class Epi>
   static x2c_status gemm_kp(x2c_ctx *ctx, cudaStream_t st, int KP, const __nv_bfloat16 *A, const __nv_bfloat16 *B,
-                            int m_tiles, int n_tiles, const Epi &epi, int stage_bytes, const char *name) {
+                            int m_tiles, int n_tiles, const Epi &epi, int stage_bytes, int a_rows, const char *name) {
     switch (KP) {
-      case 32: return gemm<NT, 32>(ctx, st, A, B, m_tiles, n_tiles, epi, stage_bytes, name);
-      case 64: return gemm<NT, 64>(ctx, st, A, B, m_tiles, n_tiles, epi, stage_bytes, name);
-      case 96: return gemm<NT, 96>(ctx, st, A, B, m_tiles, n_tiles, epi, stage_bytes, name);
-      case 128: return gemm<NT, 128>(ctx, st, A, B, m_tiles, n_tiles, epi, stage_bytes, name);
+      case 32: return gemm<NT, 32>(ctx, st, A, B, m_tiles, n_tiles, epi, stage_bytes, a_rows, name);
+      case 64: return gemm<NT, 64>(ctx, st, A, B, m_tiles, n_tiles, epi, stage_bytes, a_rows, name);
+      case 96: return gemm<NT, 96>(ctx, st, A, B, m_tiles, n_tiles, epi, stage_bytes, a_rows, name);
+      case 128: return gemm<NT, 128>(ctx, st, A, B, m_tiles, n_tiles, epi, stage_bytes, a_rows, name);
     }
     return X2C_ERR_ARG;
   }
 
   // N tile: two-component products have 4 n columns (96 per tile, 64 when S = 6 to keep the
   // S accumulators within 512 TMEM columns); spin-free ones n columns (64, or 32 when S = 6).
+  // stage_kind: 1 = fused stage-1 epilogue, 2 = stage-2 epilogue (sizes of their smem staging)
   template <class Epi>
   static x2c_status gemm_any(x2c_ctx *ctx, cudaStream_t st, int nc, int KP, const __nv_bfloat16 *A,
-                             const __nv_bfloat16 *B, int m_tiles, int cols, const Epi &epi, bool staged,
-                             const char *name) {
+                             const __nv_bfloat16 *B, int m_tiles, int cols, const Epi &epi, int stage_kind,
+                             int a_rows, const char *name) {
     if (nc == 4) {
       constexpr int NT = (S <= 5) ? 96 : 64;
-      const int stage = staged ? NT * kTileM * 8 / 4 : 0;
-      return gemm_kp<NT>(ctx, st, KP, A, B, m_tiles, (cols + NT - 1) / NT, epi, stage, name);
+      const int stage = stage_kind == 2 ? Stage2Store<4>::stage_bytes(NT) : Stage1Fused<S, 4>::stage_bytes(NT);
+      return gemm_kp<NT>(ctx, st, KP, A, B, m_tiles, (cols + NT - 1) / NT, epi, stage, a_rows, name);
     }
     constexpr int NT = (S <= 5) ? 64 : 32;
-    const int stage = staged ? NT * kTileM * 8 : 0;
-    return gemm_kp<NT>(ctx, st, KP, A, B, m_tiles, (cols + NT - 1) / NT, epi, stage, name);
+    const int stage = stage_kind == 2 ? Stage2Store<1>::stage_bytes(NT) : Stage1Fused<S, 1>::stage_bytes(NT);
+    return gemm_kp<NT>(ctx, st, KP, A, B, m_tiles, (cols + NT - 1) / NT, epi, stage, a_rows, name);
   }
 
   static int ntile(int nc) { return nc == 4 ? ((S <= 5) ? 96 : 64) : ((S <= 5) ? 64 : 32); }
@@ -724,11 +699,11 @@ struct Runner {
   template <class Src>
   static x2c_status slice(x2c_ctx *ctx, cudaStream_t st, const Src &src, int rows, int rows_pad, int K, int KP,
                           int TR, int grp, const int *kexp, __nv_bfloat16 *out, int *rexp, const char *name) {
-    const int threads = 256;
-    const int64_t warps = (rows_pad + grp - 1) / grp;
-    const int blocks = static_cast<int>((warps * 32 + threads - 1) / threads);
+    const int blocks = rows_pad / 8;  // rows_pad is a multiple of 8
+    const int smem = 8 * KP * S * 2;
+    auto kern = slice8_fp64_kernel<S, Src>;
     tbegin(ctx, st);
-    slice_fp64_kernel<S, Src><<<blocks, threads, 0, st>>>(src, rows, rows_pad, K, KP, TR, grp, kexp, out, rexp);
+    kern<<<blocks, 256, smem, st>>>(src, rows, rows_pad, K, KP, TR, grp, kexp, out, rexp);
     return launched(ctx, name, st);
   }
 
@@ -773,9 +748,9 @@ struct Runner {
       X2C_TRY(slice(ctx, st, ft, cols1, ntile1 * NT, 2 * nB, KP1, NT, nc, k1n, Fs, eF, "split_slice_u"));
       X2C_TRY(slice(ctx, st, gt, cols2, ntile2 * NT, 2 * nA, KP2, NT, nc, k2n, Gs, eG, "split_slice_u"));
       // chunk the pairs so the per-chunk buffers fit the arena
-      const size_t per_pair = (size_t)2 * nA * KP1 * S * 2 + (size_t)2 * nA * 4 + (size_t)cols1 * 2 * nA * 8 +
-                              (size_t)cols1 * KP2 * S * 2 + (size_t)cols1 * 4 +
-                              (size_t)4 * nA * nB * 8 + 2 * sizeof(PairDesc);  // + spin-orbit scratch
+      const int TRA = (2 * nA + 7) / 8 * 8;  // stage-1 A rows per pair tile
+      const size_t per_pair = (size_t)TRA * KP1 * S * 2 + (size_t)TRA * 4 + (size_t)cols1 * KP2 * S * 2 +
+                              (size_t)cols1 * 4 + (size_t)4 * nA * nB * 8 + 2 * sizeof(PairDesc);
       const size_t avail = a0.cap - a0.off;
       const size_t fixed = 4 * (size_t)(kTileM * 128 * S * 2) + 64 * 1024;
       if (avail < fixed + per_pair) return X2C_ERR_NOMEM;
@@ -785,29 +760,34 @@ struct Runner {
         const int np = (int)std::min(chunk, cls.size() - c0);
         Arena a1 = a0;
         PairDesc *dp = reinterpret_cast<PairDesc *>(a1.take_bytes(np * sizeof(PairDesc)));
-        const int rows1 = np * 2 * nA, rows1p = (rows1 + kTileM - 1) / kTileM * kTileM;
+        // stage-1 A: per pair a tile of TRA rows (2 nA real rows, zero padding to 8)
+        const int rows1 = np * TRA;
         const int rows2 = np * cols1, rows2p = (rows2 + kTileM - 1) / kTileM * kTileM;
-        __nv_bfloat16 *A1 = reinterpret_cast<__nv_bfloat16 *>(a1.take_bytes((size_t)rows1p * KP1 * S * 2));
-        int *e1 = reinterpret_cast<int *>(a1.take_bytes((size_t)rows1p * 4));
-        long long *Rt = reinterpret_cast<long long *>(a1.take_bytes((size_t)rows2 * 2 * nA * 8));
+        __nv_bfloat16 *A1 = reinterpret_cast<__nv_bfloat16 *>(a1.take_bytes((size_t)rows1 * KP1 * S * 2));
+        int *e1 = reinterpret_cast<int *>(a1.take_bytes((size_t)rows1 * 4));
         __nv_bfloat16 *A2 = reinterpret_cast<__nv_bfloat16 *>(a1.take_bytes((size_t)rows2p * KP2 * S * 2));
         int *e2 = reinterpret_cast<int *>(a1.take_bytes((size_t)rows2p * 4));
-        if (!dp || !A1 || !e1 || !Rt || !A2 || !e2) return X2C_ERR_NOMEM;
+        if (!dp || !A1 || !e1 || !A2 || !e2) return X2C_ERR_NOMEM;
         X2C_TRY_CUDA(ctx, cudaMemcpyAsync(dp, cls.data() + c0, np * sizeof(PairDesc), cudaMemcpyHostToDevice, st));
-        ClassInfo ci{dp, d_mols, nA, nB, nc, inv4c2};
-        X2C_TRY(slice(ctx, st, MidRows{ci}, rows1, rows1p, 2 * nB, KP1, kTileM, 1, k1p, A1, e1, "split_slice_mid"));
-        X2C_TRY(gemm_any(ctx, st, nc, KP1, A1, Fs, rows1p / kTileM, cols1, Stage1Store{Rt, rows1, nA, cols1},
-                         false, "split_stage1"));
-        {
-          const int threads = 256;
-          const int64_t warps = rows2p / nc;
-          const int blocks = (int)((warps * 32 + threads - 1) / threads);
-          tbegin(ctx, st);
-          slice_r_kernel<S><<<blocks, threads, 0, st>>>(Rt, e1, eF, k2p, np, nA, cols1, rows2p, KP2, nc, A2, e2);
-          X2C_TRY(launched(ctx, "split_slice_r", st));
+        if (rows2p > rows2) {  // the stage-2 tail rows are never written by the fused epilogue
+          const size_t tail0 = (size_t)(rows2p - kTileM) * KP2 * S * 2;
+          X2C_TRY_CUDA(ctx, cudaMemsetAsync(reinterpret_cast<char *>(A2) + tail0, 0, (size_t)kTileM * KP2 * S * 2, st));
         }
-        X2C_TRY(gemm_any(ctx, st, nc, KP2, A2, Gs, rows2p / kTileM, cols2,
-                         Stage2Store{dp, d_mols, e2, eG, rows2, nA, nB, nc, S}, true, "split_stage2"));
+        ClassInfo ci{dp, d_mols, nA, nB, nc, inv4c2};
+        X2C_TRY(slice(ctx, st, MidRowsPadded{ci, TRA}, rows1, rows1, 2 * nB, KP1, TRA, 1, k1p, A1, e1,
+                      "split_slice_mid"));
+        if (nc == 4)
+          X2C_TRY(gemm_any(ctx, st, nc, KP1, A1, Fs, np, cols1,
+                           Stage1Fused<S, 4>{e1, k2p, eF, A2, e2, np, nA, cols1, KP2, TRA}, 1, TRA, "split_stage1"));
+        else
+          X2C_TRY(gemm_any(ctx, st, nc, KP1, A1, Fs, np, cols1,
+                           Stage1Fused<S, 1>{e1, k2p, eF, A2, e2, np, nA, cols1, KP2, TRA}, 1, TRA, "split_stage1"));
+        if (nc == 4)
+          X2C_TRY(gemm_any(ctx, st, nc, KP2, A2, Gs, rows2p / kTileM, cols2,
+                           Stage2Store<4>{dp, d_mols, e2, eG, rows2, nA, nB, S}, 2, kTileM, "split_stage2"));
+        else
+          X2C_TRY(gemm_any(ctx, st, nc, KP2, A2, Gs, rows2p / kTileM, cols2,
+                           Stage2Store<1>{dp, d_mols, e2, eG, rows2, nA, nB, S}, 2, kTileM, "split_stage2"));
         // spin-orbit middle term (FP64): diagonal pairs, or all pairs in the general case
         if (nc == 4) {
           std::vector<PairDesc> so;
