@@ -30,6 +30,7 @@
 
 #include "common.cuh"
 #include "gemm_f64.cuh"
+#include "split_int.cuh"
 #include "umma.cuh"
 
 namespace x2c {
@@ -38,8 +39,6 @@ namespace {
 constexpr int kTileM = 128;
 constexpr long long kWaitBudget = 4000000000ll;  // ~2 s of SM clock per wait
 
-
-#include "split_int.cuh"
 
 // Offset (elements) of digit slice s of element (r, k) in the core-matrix tiled layout:
 // tiles of TR rows, each tile holding S slices of TR x KP BF16 values arranged as
