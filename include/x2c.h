@@ -200,11 +200,14 @@ x2c_status x2c_ctx_counters(x2c_ctx *ctx, x2c_counters *out);
  * launches is bracketed by CUDA events recorded on the launching stream (this adds a little
  * host overhead); enabling also clears the accumulated times.  x2c_ctx_kernel_times()
  * waits for the recorded events and returns, per kernel name (NUL-terminated, 32 bytes per
- * entry in `names`), the accumulated milliseconds and the number of launches; at most
- * max_entries entries are written and *n_entries receives the number written. */
+ * entry in `names`), the accumulated milliseconds, the number of launches and the
+ * accumulated algorithmic flops (2 m n k per real GEMM product for the FP64 GEMM kernels; 0
+ * for kernels whose launcher does not count them); any of names, ms, launches and flops may
+ * be NULL.  At most max_entries entries are written and *n_entries receives the number
+ * written. */
 x2c_status x2c_ctx_set_timing(x2c_ctx *ctx, int32_t enable);
 x2c_status x2c_ctx_kernel_times(x2c_ctx *ctx, int32_t max_entries, char *names, double *ms,
-                                int64_t *launches, int32_t *n_entries);
+                                int64_t *launches, double *flops, int32_t *n_entries);
 
 #ifdef __cplusplus
 }

@@ -50,16 +50,22 @@ class Context:
         """x2c_ctx_set_timing: bracket every kernel launch with CUDA events (clears totals)."""
         abi.check(self.lib.x2c_ctx_set_timing(self.handle, int(bool(enable))), "x2c_ctx_set_timing")
 
-    def kernel_times(self, max_entries: int = 64):
-        """x2c_ctx_kernel_times: {kernel name: (total ms, launches)} since timing was enabled."""
+    def kernel_times(self, max_entries: int = 64, with_flops: bool = False):
+        """x2c_ctx_kernel_times: {kernel name: (total ms, launches)} since timing was enabled,
+        or (total ms, launches, algorithmic flops) with with_flops=True."""
         names = ctypes.create_string_buffer(32 * max_entries)
         ms = (ctypes.c_double * max_entries)()
         cnt = (ctypes.c_int64 * max_entries)()
+        fl = (ctypes.c_double * max_entries)()
         n = ctypes.c_int32()
-        abi.check(self.lib.x2c_ctx_kernel_times(self.handle, max_entries, names, ms, cnt, ctypes.byref(n)),
+        abi.check(self.lib.x2c_ctx_kernel_times(self.handle, max_entries, names, ms, cnt, fl, ctypes.byref(n)),
                   "x2c_ctx_kernel_times", self.handle)
         raw = names.raw
-        return {raw[32 * i:32 * i + 32].split(b"\0")[0].decode(): (ms[i], cnt[i]) for i in range(n.value)}
+        out = {}
+        for i in range(n.value):
+            key = raw[32 * i:32 * i + 32].split(b"\0")[0].decode()
+            out[key] = (ms[i], cnt[i], fl[i]) if with_flops else (ms[i], cnt[i])
+        return out
 
     def counters(self):
         c = abi.Counters()

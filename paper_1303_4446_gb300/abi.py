@@ -82,7 +82,7 @@ _SIGS = {
     "x2c_ctx_set_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "x2c_ctx_kernel_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_char_p,
                                             ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
-                                            ctypes.POINTER(ctypes.c_int32)]),
+                                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]),
 }
 
 

@@ -370,17 +370,18 @@ x2c_status x2c_ctx_set_timing(x2c_ctx *ctx, int32_t enable) {
 }
 
 x2c_status x2c_ctx_kernel_times(x2c_ctx *ctx, int32_t max_entries, char *names, double *ms,
-                                int64_t *launches, int32_t *n_entries) {
+                                int64_t *launches, double *flops, int32_t *n_entries) {
   if (!ctx || max_entries < 0 || !n_entries) return X2C_ERR_ARG;
   X2C_TRY_CUDA(ctx, cudaSetDevice(ctx->device));
   for (auto &p : ctx->pending) {
-    cudaEvent_t b = ctx->ev_pool[p.second], e = ctx->ev_pool[p.second + 1];
+    cudaEvent_t b = ctx->ev_pool[p.begin], e = ctx->ev_pool[p.begin + 1];
     X2C_TRY_CUDA(ctx, cudaEventSynchronize(e));
     float t = 0.f;
     X2C_TRY_CUDA(ctx, cudaEventElapsedTime(&t, b, e));
-    auto &acc = ctx->kernel_ms[p.first];
-    acc.first += t;
-    acc.second += 1;
+    auto &acc = ctx->kernel_ms[p.name];
+    acc.ms += t;
+    acc.flops += p.flops;
+    acc.launches += 1;
   }
   ctx->pending.clear();
   ctx->ev_used = 0;
@@ -391,8 +392,9 @@ x2c_status x2c_ctx_kernel_times(x2c_ctx *ctx, int32_t max_entries, char *names, 
       std::strncpy(names + 32 * i, kv.first.c_str(), 31);
       names[32 * i + 31] = 0;
     }
-    if (ms) ms[i] = kv.second.first;
-    if (launches) launches[i] = kv.second.second;
+    if (ms) ms[i] = kv.second.ms;
+    if (launches) launches[i] = kv.second.launches;
+    if (flops) flops[i] = kv.second.flops;
     ++i;
   }
   *n_entries = i;

@@ -32,8 +32,17 @@ struct x2c_ctx {
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
-  std::vector<std::pair<std::string, size_t>> pending;  // kernel name, index of its begin event
-  std::map<std::string, std::pair<double, int64_t>> kernel_ms;  // accumulated ms, launches
+  struct Pending {
+    std::string name;
+    size_t begin;  // index of its begin event
+    double flops;  // algorithmic flops of the launch (0 where the launcher does not count them)
+  };
+  struct KernelTotals {
+    double ms = 0, flops = 0;
+    int64_t launches = 0;
+  };
+  std::vector<Pending> pending;
+  std::map<std::string, KernelTotals> kernel_ms;
   std::string names_buf;
 };
 
@@ -79,8 +88,9 @@ inline void tbegin(x2c_ctx *ctx, cudaStream_t st) {
   if (e) cudaEventRecord(e, st);
 }
 
-// Check the launch that was just enqueued and count it.
-inline x2c_status launched(x2c_ctx *ctx, const char *name, cudaStream_t st = nullptr) {
+// Check the launch that was just enqueued and count it; `flops` = the launch's algorithmic
+// flops, reported with its time when timing is enabled.
+inline x2c_status launched(x2c_ctx *ctx, const char *name, cudaStream_t st = nullptr, double flops = 0) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, e, name);
   ctx->launches++;
@@ -89,7 +99,7 @@ inline x2c_status launched(x2c_ctx *ctx, const char *name, cudaStream_t st = nul
     cudaEvent_t ev = next_event(ctx);
     if (ev) {
       cudaEventRecord(ev, st);
-      ctx->pending.push_back({name, begin});
+      ctx->pending.push_back({name, begin, flops});
     }
   }
   return X2C_OK;

@@ -158,6 +158,13 @@ __global__ void __launch_bounds__(Cfg::NT) gemm_f64_kernel(AOp A, BOp B, COp C, 
   }
 }
 
+// Algorithmic flops of one launch, where the shape is uniform (0 otherwise).
+template <class Dims>
+inline double dims_flops(const Dims &, int) { return 0.0; }
+inline double dims_flops(const UniformDims &d, int batch) { return 2.0 * d.m * d.n * d.k * batch; }
+struct SplitDims;
+inline double dims_flops(const SplitDims &d, int);
+
 // Launch helper: grid.x = batch entries, grid.y = tiles of the largest M x N.
 template <class Cfg, class AOp, class BOp, class COp, class Dims>
 inline x2c_status gemm_f64(x2c_ctx *ctx, cudaStream_t st, int batch, int max_m, int max_n,
@@ -169,7 +176,7 @@ inline x2c_status gemm_f64(x2c_ctx *ctx, cudaStream_t st, int batch, int max_m, 
   dim3 grid(batch, tiles_m * tiles_n);
   tbegin(ctx, st);
   gemm_f64_kernel<Cfg><<<grid, Cfg::NT, 0, st>>>(A, B, C, D, tiles_n);
-  return launched(ctx, name, st);
+  return launched(ctx, name, st, dims_flops(D, batch));
 }
 
 // ---- split-K: batch entry b' = split * batch + b computes the K range of its split into a
@@ -196,6 +203,7 @@ struct SplitDims {
   __device__ int K0(int b) const { return (b / batch) * kc; }
   __device__ int K(int b) const { return min(k, (b / batch + 1) * kc); }
 };
+inline double dims_flops(const SplitDims &d, int) { return 2.0 * d.m * d.n * d.k * d.batch; }
 struct PartialStore {
   double *part;
   int64_t mn;

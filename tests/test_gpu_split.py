@@ -91,3 +91,25 @@ def test_split_matches_fp64_path_ag55_2c(ctx):
         ref = O.dlu_pair_block(blocks, r["UL"], r["US"], r["UL"], r["US"])
         got = O.from_quaternion(*[p[ra, rb].cpu().numpy() for p in hs])
         assert np.abs(got - ref).max() <= SPLIT_TOL * scale
+
+
+def test_batched_uneven_molecules_split_and_fp64(ctx):
+    """Batched DLU over uneven clusters with both bases (the 64-molecule workload's recipe,
+    8 molecules here): every molecule's h from the batched launch equals its own build, and
+    matches the oracle."""
+    mols = w.batched_molecules(count=8, lo=2, hi=9, seed=11)
+    kinds = {b: w.atomic_inputs(47.0, b, False) for b in ("s30", "s48")}
+    dk = {b: dev(v) for b, v in kinds.items()}
+    ms = [w.molecule_inputs(m, False) for m in mols]
+    gs = [dev(m) for m in ms]
+    order = ["s30", "s48"]
+    lays = [(m.offsets, [order.index(b) for b in m.basis], [dk["s30"], dk["s48"]]) for m in mols]
+    for prec, tol in ((x.PREC_FP64, 1e-10), (x.PREC_SPLIT_BF16, SPLIT_TOL)):
+        outs = x.x2c_build_dlu_batched(ctx, gs, lays, precision=prec)
+        ctx.status()
+        for mol, m, g, lay, hb in zip(mols, ms, gs, lays, outs):
+            hs = x.x2c_build_dlu(ctx, g, *lay, precision=prec)
+            ctx.status()
+            assert (hb[0] - hs[0]).abs().max().item() <= 1e-13 * hs[0].abs().max().item()
+            ref = O.x2c_dlu(m, mol.offsets, [kinds[b] for b in mol.basis])["h"]
+            assert np.abs(hb[0].cpu().numpy() - ref).max() <= tol * np.abs(ref).max()
