@@ -40,6 +40,10 @@ WORKLOADS = {
     "ag309_2c": dict(L=309, basis="s48", two_c=True),
     # 64 uneven spin-free clusters, n ~ U[2, 43], basis s30/s48 50/50, one batched launch
     "batch64_sf": dict(L=None, basis=None, two_c=False, batch=64),
+    # 2000 Poisson requests at 50/s through the server: Ag_n, n log-uniform in [2, 147],
+    # s30/s48, 30 % two-component; inputs are leading blocks of the Ag147 matrices in pinned
+    # host memory (copied in by the server), results stay on the device
+    "serving": dict(L=None, basis=None, two_c=None, serving=2000),
     "ag55_2c": dict(L=55, basis="s48", two_c=True),
     "ag55_sf": dict(L=55, basis="s48", two_c=False),
     "ag4_sf": dict(L=4, basis="s30", two_c=False),
@@ -320,6 +324,145 @@ def run_batched(args, cfg):
     print(json.dumps(line), flush=True)
 
 
+def serving_inputs(seed=w.DEFAULT_SEED):
+    """Pinned host matrices of Ag147 per basis (two-component set; spin-free requests use S,
+    T, V, W0) and the free-atom kinds, host and device."""
+    import torch
+    big, kinds = {}, {}
+    for b in ("s30", "s48"):
+        mol = w.silver_cluster(147, b)
+        m = w.molecule_inputs(mol, True, seed)
+        big[b] = {k: torch.from_numpy(v).pin_memory() for k, v in m.items()}
+        for tc in (False, True):
+            kinds[(b, tc)] = {k: torch.from_numpy(v).pin_memory()
+                              for k, v in w.atomic_inputs(47.0, b, tc, seed).items()}
+    return big, kinds
+
+
+def serve_stream(srv, reqs, big, kinds, precision, n_slices, t_lead=0.05):
+    """Open-loop submission at the scheduled arrival times (server clock) of every request;
+    latency is counted from the scheduled arrival.  Results are released as they complete."""
+    import threading
+    import paper_1303_4446_gb300 as x
+    keys = {(b, tc): 1 + 2 * ("s30", "s48").index(b) + int(tc) for b in ("s30", "s48") for tc in (False, True)}
+    pending = []
+    lock = threading.Condition()
+    done = {"n": 0, "failed": 0}
+    h2d = [0]
+
+    def reaper():
+        # waits for the requests in submission order and releases their results
+        while True:
+            with lock:
+                while not pending and not done.get("stop"):
+                    lock.wait(0.05)
+                if not pending:
+                    return
+                t = pending.pop(0)
+            r = srv.wait(t, timeout_ms=600000)
+            if r["status"] != 0:
+                done["failed"] += 1
+            srv.release(t)
+            done["n"] += 1
+
+    th = threading.Thread(target=reaper, daemon=True)
+    th.start()
+    t0 = srv.now() + t_lead
+    for rq in reqs:
+        b, tc, L = rq["basis"], rq["two_component"], rq["natoms"]
+        nb = w.BASES[b][2]
+        N = L * nb
+        m = {k: v[:N, :N] for k, v in big[b].items() if tc or k in ("S", "T", "V", "W0")}
+        target = t0 + rq["t_arrive"]
+        while True:
+            dt = target - srv.now()
+            if dt <= 0:
+                break
+            time.sleep(dt - 0.0005 if dt > 0.001 else 0)
+        offs = np.arange(L + 1, dtype=np.int32) * nb
+        t = srv.submit_dlu(m, offs, [0] * L, [kinds[(b, tc)]], kind_keys=[keys[(b, tc)]], two_component=tc,
+                           precision=precision, n_slices=n_slices, host=True, t_arrival=target)
+        h2d[0] += 8 * N * N * (3 + (3 if tc else 0))
+        with lock:
+            pending.append(t)
+            lock.notify()
+    with lock:
+        done["stop"] = True
+        lock.notify()
+    th.join()
+    return done, h2d[0]
+
+
+def run_serving(args, cfg):
+    """The serving workload: continuous batching of a Poisson request stream (x2c_server_*)."""
+    import torch
+    import paper_1303_4446_gb300 as x
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    torch.cuda.set_device(local)
+    t_gen = time.perf_counter()
+    big, kinds = serving_inputs()
+    reqs = w.serving_requests(count=args.requests or cfg["serving"], rate=args.rate, seed=w.DEFAULT_SEED + rank)
+    t_gen = time.perf_counter() - t_gen
+    prec = x.PREC_SPLIT_BF16 if args.precision == "split" else x.PREC_FP64
+    srv = x.Server(local, max_inflight=args.slots, max_batch=16, hbm_budget_bytes=150 * 10 ** 9)
+    # warm-up: a few requests of every (basis, spin) kind through the server (the transforms
+    # cache fills, the slots' workspaces grow), then the statistics are cleared
+    combos = [(n, b, tc) for n in (147, 24, 5) for b in ("s30", "s48") for tc in (False, True)]
+    warm = [dict(t_arrive=0.002 * i, natoms=n, basis=b, two_component=tc) for i, (n, b, tc) in enumerate(combos)]
+    serve_stream(srv, warm, big, kinds, prec, args.slices)
+    srv.reset_stats()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        done, h2d = serve_stream(srv, reqs, big, kinds, prec, args.slices)
+    st = srv.stats()
+    srv.close()
+    n_ok = st["completed"]
+    line = {"metric": METRIC, "value": world * st["builds_per_s"], "unit": "builds/s", "n_gpus": world,
+            "steps": len(reqs), "warmup": len(warm), "ms_per_step": 1e3 / st["builds_per_s"] if st["builds_per_s"] else None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "bf16x-split", "data": "synthetic",
+            "config": {"workload": f"serving: {len(reqs)} Poisson requests at {args.rate:g}/s, Ag_n DLU, n log-uniform "
+                                   "in [2,147], s30/s48, 30% two-component, 150 GB budget",
+                       "slots": args.slots, "max_batch": 16, "precision": args.precision,
+                       "inputs": "leading n x n blocks of the Ag147 matrices, pinned host memory, "
+                                 "copied in by the server; results stay on the device",
+                       "parallelism": f"independent replicas x{world}"},
+            "serving": {"p50_ms": st["latency_p50_ms"], "p99_ms": st["latency_p99_ms"],
+                        "mean_ms": st["latency_mean_ms"], "max_ms": st["latency_max_ms"],
+                        "completed": n_ok, "failed": st["failed"], "builds_launched": st["builds_launched"],
+                        "cache_hits": st["cache_hits"], "cache_misses": st["cache_misses"],
+                        "peak_bytes": st["peak_bytes"], "max_concurrent": st["max_concurrent"],
+                        "latency": "completion (device event) - scheduled arrival"},
+            "gpu_launches": int(st["kernel_launches"]), "roofline": None,
+            "roofline_note": "latency-bound request stream; kernel rooflines are on the Ag309 line",
+            "clocks": clk.summary(), "input_generation_s": t_gen,
+            "e2e": {"value": world * st["builds_per_s"], "unit": "builds/s",
+                    "h2d_bytes_per_step": int(h2d / max(1, len(reqs))), "d2h_bytes_per_step": 0,
+                    "path": "x2c_server_submit with pinned host inputs (H2D inside each request)"}}
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        t0 = time.perf_counter()
+        cnt = 0
+        for rq in reqs:
+            b, tc, L = rq["basis"], rq["two_component"], rq["natoms"]
+            nb = w.BASES[b][2]
+            N = L * nb
+            m = {k: v[:N, :N].numpy().copy() for k, v in big[b].items() if tc or k in ("S", "T", "V", "W0")}
+            kd = {k: v.numpy() for k, v in kinds[(b, tc)].items()}
+            oracle.x2c_dlu(m, np.arange(L + 1) * nb, [kd] * L)
+            cnt += 1
+            if time.perf_counter() - t0 > args.cpu_budget:
+                break
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": cnt / dt, "unit": "builds/s", "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": f"dense oracle DLU of the first {cnt} requests of the stream ({dt:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -335,12 +478,17 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--requests", type=int, default=0, help="serving: requests in the stream (0 = 2000)")
+    ap.add_argument("--rate", type=float, default=50.0, help="serving: mean arrivals per second")
+    ap.add_argument("--slots", type=int, default=4, help="serving: concurrent builds")
     args = ap.parse_args()
     cfg = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, cfg)
     if cfg.get("batch"):
         return run_batched(args, cfg)
+    if cfg.get("serving"):
+        return run_serving(args, cfg)
 
     import torch
     import paper_1303_4446_gb300 as x

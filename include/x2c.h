@@ -142,6 +142,16 @@ x2c_status x2c_build_dlu_batched(x2c_ctx *ctx, const x2c_options *opt, int32_t n
                                  const x2c_layout *layouts, const x2c_mats *mols,
                                  const x2c_hout *h, void *stream);
 
+/* DLU (free-atom mode) from given atomic transforms: kind_U (HOST array, layout->n_kinds
+ * entries, device matrices of the kinds' sizes, e.g. from x2c_atomic_transforms) replaces the
+ * per-kind solve, and h is assembled from them exactly as in x2c_build_dlu (Eq. 42 with the
+ * U_AA of Eq. 43 given).  Only layout->kinds[k].n is read from the kinds' input sets.
+ * The transforms are copied into the context's staging area first (the staging area grows,
+ * synchronising the device, when a larger call comes). */
+x2c_status x2c_build_dlu_with_transforms(x2c_ctx *ctx, const x2c_options *opt, const x2c_layout *layout,
+                                         const x2c_uout *kind_U, const x2c_mats *mol, const x2c_hout *h,
+                                         void *stream);
+
 /* Atomic (or any) decoupling transforms U^L, U^S of n_problems independent input sets in
  * one batched solve (the matrix function of Eq. 43).  inputs, U: HOST arrays. */
 x2c_status x2c_atomic_transforms(x2c_ctx *ctx, const x2c_options *opt, int32_t n_problems,
@@ -208,6 +218,111 @@ x2c_status x2c_ctx_counters(x2c_ctx *ctx, x2c_counters *out);
 x2c_status x2c_ctx_set_timing(x2c_ctx *ctx, int32_t enable);
 x2c_status x2c_ctx_kernel_times(x2c_ctx *ctx, int32_t max_entries, char *names, double *ms,
                                 int64_t *launches, double *flops, int32_t *n_entries);
+
+/* ---------------------------------------------------------------------------------------
+ * Serving: a device-resident request loop with continuous batching.
+ *
+ * A server owns max_inflight slots (a CUDA stream and a context each), a device-memory pool
+ * and a cache of atomic transforms U^L_A, U^S_A keyed by the caller's kind keys (element,
+ * basis, spin-orbit blocks).  One scheduler thread takes requests in arrival order: when a
+ * slot is free and the head request fits the memory budget it starts, together with later
+ * queued requests of the same options (free-atom DLU) up to max_batch, as one batched build
+ * (x2c_build_dlu_batched with the cached transforms); kinds missing from the cache are
+ * solved once, in that build's slot, and cached for every later request.  Builds on
+ * different slots overlap on the device.  The paper has no serving layer: this is the
+ * interface around Eqs. 42-43 (DLU) and Sec. II.A (full X2C) for a stream of molecules.
+ *
+ * Memory: the budget covers everything the server allocates (copies of inputs, outputs it
+ * allocates, cached transforms, the slots' workspaces); a request that could never fit is
+ * refused at submission with X2C_ERR_ADMISSION, one that does not fit now waits (and the
+ * requests behind it wait too: first come, first served).  Unused cache entries are evicted,
+ * least recently used first, when the head request needs their memory.  Results the server
+ * allocated stay counted until x2c_server_release().
+ *
+ * Clock: times are seconds since the server was created (x2c_server_now()); t_start and
+ * t_end are device timestamps (CUDA events) on that clock.  Latency = t_end - t_arrival.
+ * Thread safety: every x2c_server_* call may come from any host thread.
+ * ------------------------------------------------------------------------------------- */
+typedef struct x2c_server x2c_server;
+
+typedef enum { X2C_REQ_DLU = 0, X2C_REQ_FULL = 1 } x2c_request_kind;
+typedef enum { X2C_MEM_DEVICE = 0, X2C_MEM_HOST = 1 } x2c_memory;
+typedef enum { X2C_STATE_QUEUED = 0, X2C_STATE_RUNNING = 1, X2C_STATE_DONE = 2 } x2c_request_state;
+
+typedef struct {
+  int32_t device;           /* CUDA device */
+  int32_t max_inflight;     /* slots = builds running at once, 1..16 (0 = 4) */
+  int32_t max_batch;        /* requests one build may hold, 1..256 (0 = 16) */
+  int32_t reserved0;        /* must be zero */
+  uint64_t hbm_budget_bytes;/* device memory the server may hold (0 = 150 GB) */
+  int32_t reserved[4];      /* must be zero */
+} x2c_server_options;
+
+typedef struct {
+  x2c_options opt;          /* as for the build calls */
+  int32_t kind;             /* x2c_request_kind */
+  int32_t memory;           /* x2c_memory: where mol, layout.kinds and out point */
+  x2c_layout layout;        /* DLU: atoms and kinds (copied at submission); ignored for FULL */
+  const uint64_t *kind_key; /* HOST, layout.n_kinds entries, or NULL: cache key of each kind's
+                               transforms (0 = do not cache that kind).  Requests that give
+                               the same key must give the same free-atom inputs for it. */
+  x2c_mats mol;             /* molecular matrices (FULL: the whole system) */
+  int32_t ld;               /* leading dimension (elements) of mol's matrices, 0 = mol.n */
+  int32_t reserved0;        /* must be zero */
+  x2c_hout out;             /* DEVICE: the caller's device outputs, or h[0] = NULL for
+                               outputs the server allocates (valid until release).
+                               HOST: the caller's host outputs, filled before the request
+                               completes, or h[0] = NULL for server-allocated device outputs */
+  double t_arrival;         /* scheduled arrival on the server clock, < 0 = at submission */
+} x2c_request;
+
+typedef struct {
+  int32_t state;            /* x2c_request_state */
+  int32_t status;           /* x2c_status of the build, once DONE */
+  const double *h[4];       /* device result (NULL when delivered to host outputs) */
+  double t_arrival, t_submit, t_admit, t_start, t_end;
+  int32_t batch_size;       /* requests built in the same launch */
+  int32_t cache_hits;       /* kinds whose transforms came from the cache */
+  int32_t cache_misses;     /* kinds solved for this request */
+  int32_t slot;
+} x2c_result;
+
+typedef struct {
+  int64_t submitted, completed, failed, cancelled, queued, running;
+  int64_t builds_launched;  /* batched builds started */
+  int64_t cache_hits, cache_misses, cache_entries, cache_evictions;
+  double latency_p50_ms, latency_p99_ms, latency_mean_ms, latency_max_ms; /* completed OK */
+  double builds_per_s;      /* completed OK / (last completion - first arrival) */
+  double first_arrival, last_completion;
+  uint64_t bytes_in_use, peak_bytes, budget_bytes;
+  int64_t kernel_launches;  /* kernels the builds launched */
+  int32_t max_concurrent;   /* most requests running at once */
+  int32_t reserved;
+} x2c_server_stats;
+
+/* Create a server (allocates its slots and starts its scheduler thread). */
+x2c_status x2c_server_create(const x2c_server_options *opt, x2c_server **out);
+/* Stop: cancel queued requests, wait for running builds, free everything.  NULL is allowed. */
+x2c_status x2c_server_destroy(x2c_server *s);
+/* Seconds since the server was created. */
+x2c_status x2c_server_now(x2c_server *s, double *t);
+/* Queue a request; *ticket identifies it.  The request's matrices must stay valid and
+ * unchanged until it is DONE (host and device inputs are read when it starts).
+ * X2C_ERR_ARG for an invalid request, X2C_ERR_ADMISSION if it can never fit the budget. */
+x2c_status x2c_server_submit(x2c_server *s, const x2c_request *req, uint64_t *ticket);
+/* Current state of a request (never blocks).  X2C_ERR_NOT_FOUND for an unknown ticket. */
+x2c_status x2c_server_poll(x2c_server *s, uint64_t ticket, x2c_result *res);
+/* Wait until the request is DONE or timeout_ms passes (X2C_ERR_TIMEOUT; it keeps running). */
+x2c_status x2c_server_wait(x2c_server *s, uint64_t ticket, uint32_t timeout_ms, x2c_result *res);
+/* Cancel a queued request (it completes with X2C_ERR_CANCELLED).  X2C_ERR_ARG if it has
+ * already started or finished. */
+x2c_status x2c_server_cancel(x2c_server *s, uint64_t ticket);
+/* Forget a DONE request and free the outputs the server allocated for it.  The caller must
+ * have finished reading them (stream work that reads them must have completed). */
+x2c_status x2c_server_release(x2c_server *s, uint64_t ticket);
+x2c_status x2c_server_get_stats(x2c_server *s, x2c_server_stats *out);
+/* Clear the latency samples and counters (not the cache, budget or requests). */
+x2c_status x2c_server_reset_stats(x2c_server *s);
 
 #ifdef __cplusplus
 }

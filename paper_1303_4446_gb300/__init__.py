@@ -312,3 +312,216 @@ def x2c_quaternion_to_dense(h_parts: list, stream=None):
     abi.check(abi.load().x2c_quaternion_to_dense(arr, n, ctypes.c_void_p(out.data_ptr()), _stream(stream)),
               "x2c_quaternion_to_dense")
     return out
+
+
+def x2c_build_dlu_with_transforms(ctx: Context, m: dict, offsets, atom_kind, kinds_U, kind_sizes,
+                                  two_component=False, c=None, precision=PREC_FP64, so_same_atom_only=True,
+                                  n_slices=0, out=None, stream=None):
+    """DLU build (free-atom mode) from given per-kind transforms: kinds_U is a list of
+    (UL parts, US parts) CUDA tensors (e.g. from x2c_atomic_transforms), kind_sizes the
+    kinds' basis sizes.  Returns the list of h parts."""
+    nc = 4 if two_component else 1
+    ms = mats_struct(m, two_component)
+    h = out if out is not None else _alloc_parts(ms.n, nc, m["S"].device)
+    kind_structs = []
+    for n in kind_sizes:
+        k = abi.Mats()
+        k.n = int(n)
+        kind_structs.append(k)
+    lay = LayoutHolder(offsets, atom_kind, kind_structs, two_component)
+    us = (abi.UOut * len(kinds_U))()
+    for i, (UL, US) in enumerate(kinds_U):
+        for q in range(nc):
+            us[i].UL[q] = UL[q].data_ptr()
+            us[i].US[q] = US[q].data_ptr()
+    o = options(two_component, c, precision, DLU_FREE_ATOM, so_same_atom_only, n_slices)
+    ho = _hout(h)
+    abi.check(ctx.lib.x2c_build_dlu_with_transforms(ctx.handle, ctypes.byref(o), ctypes.byref(lay.s), us,
+                                                    ctypes.byref(ms), ctypes.byref(ho), _stream(stream)),
+              "x2c_build_dlu_with_transforms", ctx.handle)
+    return h
+
+
+# ---- serving ------------------------------------------------------------------------------
+
+REQ_DLU, REQ_FULL = 0, 1
+MEM_DEVICE, MEM_HOST = 0, 1
+STATE_QUEUED, STATE_RUNNING, STATE_DONE = 0, 1, 2
+
+
+class _DeviceView:
+    """__cuda_array_interface__ of a float64 n x n matrix the server owns (no ownership here)."""
+
+    def __init__(self, ptr, n):
+        self.__cuda_array_interface__ = {"shape": (n, n), "typestr": "<f8", "data": (int(ptr), False),
+                                         "version": 3, "strides": None}
+
+
+def _mat_ptr_ld(a, host):
+    """(address, leading dimension) of a row-major float64 matrix or a row-major view of one."""
+    if a is None:
+        return None, 0
+    if isinstance(a, np.ndarray):
+        if not host:
+            raise ValueError("numpy arrays are host memory")
+        if a.dtype != np.float64 or a.ndim != 2 or a.strides[1] != 8:
+            raise ValueError("host matrices must be float64 with unit column stride")
+        return a.ctypes.data, a.strides[0] // 8
+    torch = _torch()
+    if not isinstance(a, torch.Tensor) or a.dtype != torch.float64 or a.dim() != 2 or a.stride(1) != 1:
+        raise ValueError("matrices must be float64 tensors with unit column stride")
+    if a.is_cuda == host:
+        raise ValueError("device request needs CUDA tensors, host request CPU tensors")
+    return a.data_ptr(), a.stride(0)
+
+
+class Server:
+    """x2c_server_*: continuous-batching X2C/DLU server on one GPU.
+
+    Requests keep references to their input (and host output) arrays until release(); the
+    arrays must not change until the request is DONE."""
+
+    def __init__(self, device=0, max_inflight=4, max_batch=16, hbm_budget_bytes=0):
+        self.lib = abi.load()
+        o = abi.ServerOptions()
+        o.device, o.max_inflight, o.max_batch = int(device), int(max_inflight), int(max_batch)
+        o.hbm_budget_bytes = int(hbm_budget_bytes)
+        h = ctypes.c_void_p()
+        abi.check(self.lib.x2c_server_create(ctypes.byref(o), ctypes.byref(h)), "x2c_server_create")
+        self.handle = h
+        self.device = device
+        self._keep = {}
+        self._shape = {}
+
+    def close(self):
+        if self.handle:
+            self.lib.x2c_server_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def now(self):
+        t = ctypes.c_double()
+        abi.check(self.lib.x2c_server_now(self.handle, ctypes.byref(t)), "x2c_server_now")
+        return t.value
+
+    def _submit(self, req, keep, n, nc):
+        t = ctypes.c_uint64()
+        abi.check(self.lib.x2c_server_submit(self.handle, ctypes.byref(req), ctypes.byref(t)), "x2c_server_submit")
+        self._keep[t.value] = (req,) + tuple(keep)
+        self._shape[t.value] = (n, nc)
+        return t.value
+
+    def _mats(self, m, two_component, host):
+        s = abi.Mats()
+        lds = set()
+        n = None
+        for k in _MAT_KEYS:
+            a = m.get(k) if (two_component or k in ("S", "T", "V", "W0")) else None
+            p, ld = _mat_ptr_ld(a, host)
+            setattr(s, k, p)
+            if a is not None:
+                lds.add(ld)
+                n = a.shape[0] if n is None else n
+                if tuple(a.shape) != (n, n):
+                    raise ValueError("all matrices must be n x n")
+        if len(lds) != 1:
+            raise ValueError("all molecular matrices must share one leading dimension")
+        s.n = n
+        return s, lds.pop()
+
+    def submit_dlu(self, m, offsets, atom_kind, kinds, kind_keys=None, two_component=False, c=None,
+                   precision=PREC_FP64, n_slices=0, so_same_atom_only=True, dlu_potential=DLU_FREE_ATOM,
+                   out=None, host=False, t_arrival=-1.0):
+        """Queue a DLU build.  m: molecular matrices (CUDA tensors, or host arrays with
+        host=True; row-major views such as big[:n, :n] are allowed); kinds: free-atom input
+        dicts; kind_keys: one integer cache key per kind (0 = not cached); out: result
+        buffers (device, or host with host=True), None = server-allocated device result."""
+        nc = 4 if two_component else 1
+        req = abi.Request()
+        req.opt = options(two_component, c, precision, dlu_potential, so_same_atom_only, n_slices)
+        req.kind, req.memory = REQ_DLU, (MEM_HOST if host else MEM_DEVICE)
+        req.mol, ld = self._mats(m, two_component, host)
+        req.ld = ld
+        kstructs = []
+        for k in (kinds or []):
+            ks, _ = self._mats(k, two_component, host)
+            kstructs.append(ks)
+        lay = LayoutHolder(offsets, atom_kind, kstructs, two_component)
+        req.layout = lay.s
+        keys = None
+        if kind_keys is not None:
+            keys = (ctypes.c_uint64 * len(kind_keys))(*[int(k) for k in kind_keys])
+            req.kind_key = ctypes.cast(keys, ctypes.POINTER(ctypes.c_uint64))
+        outs = []
+        if out is not None:
+            for q in range(nc):
+                p, _ = _mat_ptr_ld(out[q], host)
+                req.out.h[q] = p
+            outs = list(out)
+        req.t_arrival = float(t_arrival)
+        return self._submit(req, (m, kinds, lay, keys, outs), req.mol.n, nc)
+
+    def submit_full(self, m, two_component=False, c=None, out=None, host=False, t_arrival=-1.0):
+        """Queue a full X2C build of the whole system (see submit_dlu for the arguments)."""
+        nc = 4 if two_component else 1
+        req = abi.Request()
+        req.opt = options(two_component, c)
+        req.kind, req.memory = REQ_FULL, (MEM_HOST if host else MEM_DEVICE)
+        req.mol, ld = self._mats(m, two_component, host)
+        req.ld = ld
+        outs = []
+        if out is not None:
+            for q in range(nc):
+                p, _ = _mat_ptr_ld(out[q], host)
+                req.out.h[q] = p
+            outs = list(out)
+        req.t_arrival = float(t_arrival)
+        return self._submit(req, (m, outs), req.mol.n, nc)
+
+    def _result(self, ticket, r):
+        d = {k: getattr(r, k) for k in ("state", "status", "t_arrival", "t_submit", "t_admit", "t_start", "t_end",
+                                        "batch_size", "cache_hits", "cache_misses", "slot")}
+        d["h_ptr"] = [r.h[q] for q in range(4)]
+        return d
+
+    def poll(self, ticket):
+        r = abi.Result()
+        abi.check(self.lib.x2c_server_poll(self.handle, int(ticket), ctypes.byref(r)), "x2c_server_poll")
+        return self._result(ticket, r)
+
+    def wait(self, ticket, timeout_ms=120000):
+        """Wait for a request; returns its result dict (status X2C_ERR_TIMEOUT = 9 is raised)."""
+        r = abi.Result()
+        abi.check(self.lib.x2c_server_wait(self.handle, int(ticket), int(timeout_ms), ctypes.byref(r)),
+                  "x2c_server_wait")
+        return self._result(ticket, r)
+
+    def result_tensors(self, ticket, res=None):
+        """The device result of a DONE request as torch tensors viewing server memory (valid
+        until release)."""
+        torch = _torch()
+        res = res or self.poll(ticket)
+        n, nc = self._shape[ticket]
+        return [torch.as_tensor(_DeviceView(res["h_ptr"][q], n), device=f"cuda:{self.device}") for q in range(nc)]
+
+    def cancel(self, ticket):
+        abi.check(self.lib.x2c_server_cancel(self.handle, int(ticket)), "x2c_server_cancel")
+
+    def release(self, ticket):
+        abi.check(self.lib.x2c_server_release(self.handle, int(ticket)), "x2c_server_release")
+        self._keep.pop(ticket, None)
+        self._shape.pop(ticket, None)
+
+    def stats(self):
+        s = abi.ServerStats()
+        abi.check(self.lib.x2c_server_get_stats(self.handle, ctypes.byref(s)), "x2c_server_get_stats")
+        return {k: getattr(s, k) for k, _ in abi.ServerStats._fields_ if k != "reserved"}
+
+    def reset_stats(self):
+        abi.check(self.lib.x2c_server_reset_stats(self.handle), "x2c_server_reset_stats")

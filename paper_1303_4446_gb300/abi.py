@@ -54,6 +54,36 @@ class Counters(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int64), ("credited_flops", ctypes.c_double)]
 
 
+class ServerOptions(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("max_inflight", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_uint64),
+                ("reserved", ctypes.c_int32 * 4)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("opt", Options), ("kind", ctypes.c_int32), ("memory", ctypes.c_int32), ("layout", Layout),
+                ("kind_key", ctypes.POINTER(ctypes.c_uint64)), ("mol", Mats), ("ld", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32), ("out", HOut), ("t_arrival", ctypes.c_double)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("status", ctypes.c_int32), ("h", ctypes.c_void_p * 4),
+                ("t_arrival", ctypes.c_double), ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_start", ctypes.c_double), ("t_end", ctypes.c_double), ("batch_size", ctypes.c_int32),
+                ("cache_hits", ctypes.c_int32), ("cache_misses", ctypes.c_int32), ("slot", ctypes.c_int32)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in ("submitted", "completed", "failed", "cancelled", "queued", "running",
+                                              "builds_launched", "cache_hits", "cache_misses", "cache_entries",
+                                              "cache_evictions")] + \
+               [(k, ctypes.c_double) for k in ("latency_p50_ms", "latency_p99_ms", "latency_mean_ms",
+                                               "latency_max_ms", "builds_per_s", "first_arrival",
+                                               "last_completion")] + \
+               [(k, ctypes.c_uint64) for k in ("bytes_in_use", "peak_bytes", "budget_bytes")] + \
+               [("kernel_launches", ctypes.c_int64), ("max_concurrent", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 _LIB = None
 
 # name -> (restype, argtypes)
@@ -83,6 +113,19 @@ _SIGS = {
     "x2c_ctx_kernel_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_char_p,
                                             ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
                                             ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]),
+    "x2c_build_dlu_with_transforms": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Options), ctypes.POINTER(Layout),
+                                                     ctypes.POINTER(UOut), ctypes.POINTER(Mats), ctypes.POINTER(HOut),
+                                                     ctypes.c_void_p]),
+    "x2c_server_create": (ctypes.c_int, [ctypes.POINTER(ServerOptions), ctypes.POINTER(ctypes.c_void_p)]),
+    "x2c_server_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "x2c_server_now": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    "x2c_server_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
+    "x2c_server_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(Result)]),
+    "x2c_server_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.POINTER(Result)]),
+    "x2c_server_cancel": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
+    "x2c_server_release": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
+    "x2c_server_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ServerStats)]),
+    "x2c_server_reset_stats": (ctypes.c_int, [ctypes.c_void_p]),
 }
 
 

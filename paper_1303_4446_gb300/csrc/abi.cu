@@ -8,16 +8,26 @@
 
 namespace x2c {
 
-x2c_status ensure_workspace(x2c_ctx *ctx, size_t bytes, Arena *out) {
+x2c_status ensure_workspace(x2c_ctx *ctx, size_t bytes, Arena *out, cudaStream_t st) {
   if (bytes > ctx->ws_bytes) {
-    X2C_TRY_CUDA(ctx, cudaDeviceSynchronize());
-    if (ctx->ws) cudaFree(ctx->ws);
-    ctx->ws = nullptr;
-    ctx->ws_bytes = 0;
     const size_t want = bytes + bytes / 8;
-    cudaError_t e = cudaMalloc(&ctx->ws, want);
+    cudaError_t e;
+    if (ctx->pool) {
+      // stream-ordered: the old workspace is only ever used on this stream
+      if (ctx->ws) cudaFreeAsync(ctx->ws, st);
+      ctx->ws = nullptr;
+      ctx->ws_bytes = 0;
+      e = cudaMallocFromPoolAsync(reinterpret_cast<void **>(&ctx->ws), want, ctx->pool, st);
+    } else {
+      X2C_TRY_CUDA(ctx, cudaDeviceSynchronize());
+      if (ctx->ws) cudaFree(ctx->ws);
+      ctx->ws = nullptr;
+      ctx->ws_bytes = 0;
+      e = cudaMalloc(&ctx->ws, want);
+    }
     if (e != cudaSuccess) {
       cudaGetLastError();
+      ctx->ws = nullptr;
       ctx->last_error = std::string("workspace allocation: ") + cudaGetErrorString(e);
       return X2C_ERR_NOMEM;
     }
@@ -29,7 +39,9 @@ x2c_status ensure_workspace(x2c_ctx *ctx, size_t bytes, Arena *out) {
   return X2C_OK;
 }
 
-namespace {
+size_t workspace_after_growth(const x2c_ctx *ctx, size_t bytes) {
+  return bytes > ctx->ws_bytes ? bytes + bytes / 8 : ctx->ws_bytes;
+}
 
 bool mats_ok(const x2c_mats *m, int nc) {
   if (!m || m->n < 1 || !m->S || !m->T || !m->V || !m->W0) return false;
@@ -47,6 +59,8 @@ x2c_status check_options(const x2c_options *o) {
     if (r != 0) return X2C_ERR_ARG;
   return X2C_OK;
 }
+
+namespace {
 
 double credited_pair_flops(int nA, int nB, int nc, bool diag, bool so) {
   const double a = nA, b = nB;
@@ -67,6 +81,8 @@ double credited_solve_flops(int n, int nc) {
 struct Problem {
   InputDesc in;
   int n;
+  const double *preUL = nullptr;  // precomputed transforms (device, nc n^2 each): no solve
+  const double *preUS = nullptr;
 };
 
 // One logical build: a set of decoupling problems (grouped by size), a U table indexed by
@@ -81,12 +97,14 @@ struct BuildPlan {
 };
 
 x2c_status run_plan(x2c_ctx *ctx, const x2c_options *opt, BuildPlan &plan, cudaStream_t st,
-                    std::vector<double *> *UL_out = nullptr, std::vector<double *> *US_out = nullptr) {
+                    std::vector<double *> *UL_out = nullptr, std::vector<double *> *US_out = nullptr,
+                    size_t *dry_bytes = nullptr) {
   const double c = speed_of_light(opt);
   const int nc = plan.nc;
-  // group problems by size
+  // group the problems that need a solve by size
   std::map<int, std::vector<int>> groups;
-  for (size_t i = 0; i < plan.problems.size(); ++i) groups[plan.problems[i].n].push_back((int)i);
+  for (size_t i = 0; i < plan.problems.size(); ++i)
+    if (!plan.problems[i].preUL) groups[plan.problems[i].n].push_back((int)i);
   size_t u_doubles = 0, solve_ws = 0, desc_bytes = 0;
   for (auto &g : groups) {
     const size_t n2 = (size_t)g.first * g.first;
@@ -100,14 +118,23 @@ x2c_status run_plan(x2c_ctx *ctx, const x2c_options *opt, BuildPlan &plan, cudaS
   const size_t asm_ws = assemble_workspace_bytes(plan.pairs, nc, plan.max_n, opt->precision);
   const size_t total = arena_doubles(u_doubles) + desc_bytes + table_bytes + mol_bytes +
                        std::max(solve_ws, asm_ws) + 8192;
+  if (dry_bytes) {
+    *dry_bytes = total;
+    return X2C_OK;
+  }
   Arena ar;
-  X2C_TRY(ensure_workspace(ctx, total, &ar));
-  double *Ustore = ar.take(u_doubles);
+  X2C_TRY(ensure_workspace(ctx, total, &ar, st));
+  double *Ustore = ar.take(std::max<size_t>(1, u_doubles));
   double **dUL = reinterpret_cast<double **>(ar.take_bytes(np * sizeof(double *)));
   double **dUS = reinterpret_cast<double **>(ar.take_bytes(np * sizeof(double *)));
   MolDesc *dmols = reinterpret_cast<MolDesc *>(ar.take_bytes(std::max<size_t>(1, plan.mols.size()) * sizeof(MolDesc)));
   if (!Ustore || !dUL || !dUS || !dmols) return X2C_ERR_NOMEM;
   std::vector<double *> hUL(np), hUS(np);
+  for (size_t i = 0; i < np; ++i)
+    if (plan.problems[i].preUL) {
+      hUL[i] = const_cast<double *>(plan.problems[i].preUL);
+      hUS[i] = const_cast<double *>(plan.problems[i].preUS);
+    }
   // solve each size group
   size_t uoff = 0;
   std::vector<InputDesc *> ddescs;
@@ -142,7 +169,9 @@ x2c_status run_plan(x2c_ctx *ctx, const x2c_options *opt, BuildPlan &plan, cudaS
       X2C_TRY(solve_transforms(ctx, st, c, nb, n, nc, ddescs[gi++], UL, US, scratch));
     }
   }
-  ctx->counters.atomic_solves = (int64_t)np;
+  size_t solved = 0;
+  for (auto &g : groups) solved += g.second.size();
+  ctx->counters.atomic_solves = (int64_t)solved;
   if (UL_out) *UL_out = hUL;
   if (US_out) *US_out = hUS;
   if (plan.pairs.empty()) return X2C_OK;
@@ -194,10 +223,12 @@ InputDesc input_desc(const x2c_mats *m, int nc, int64_t off, int64_t ld) {
 }
 
 // Add one molecule's problems (molecular-block mode) or kind references and its pairs.
+using KindIndex = std::map<std::tuple<const double *, const double *, const double *, const double *,
+                                      const double *>, int>;
+
 x2c_status add_molecule(BuildPlan &plan, const x2c_options *opt, const x2c_layout *lay,
-                        const x2c_mats *mol, const x2c_hout *h, int mol_index,
-                        std::map<std::tuple<const double *, const double *, const double *, const double *,
-                                            const double *>, int> &kind_index) {
+                        const x2c_mats *mol, const x2c_hout *h, int mol_index, KindIndex &kind_index,
+                        const KindTransforms *ku = nullptr) {
   const int nc = plan.nc;
   if (!lay || lay->n_atoms < 1 || !lay->atom_offset || !mats_ok(mol, nc) || !h) return X2C_ERR_ARG;
   for (int q = 0; q < nc; ++q)
@@ -221,6 +252,24 @@ x2c_status add_molecule(BuildPlan &plan, const x2c_options *opt, const x2c_layou
       if (k < 0 || k >= lay->n_kinds) return X2C_ERR_ARG;
       const x2c_mats *km = &lay->kinds[k];
       const int n = lay->atom_offset[a + 1] - lay->atom_offset[a];
+      const bool pre = ku && ku->UL && ku->UL[k] && ku->US && ku->US[k];
+      if (pre) {
+        if (km->n != n) return X2C_ERR_ARG;
+        auto key = std::make_tuple(ku->UL[k], ku->US[k], (const double *)nullptr, (const double *)nullptr,
+                                   (const double *)nullptr);
+        auto it = kind_index.find(key);
+        if (it == kind_index.end()) {
+          Problem p{};
+          p.n = n;
+          p.preUL = ku->UL[k];
+          p.preUS = ku->US[k];
+          const int id = (int)plan.problems.size();
+          plan.problems.push_back(p);
+          it = kind_index.emplace(key, id).first;
+        }
+        uidx[a] = it->second;
+        continue;
+      }
       if (!mats_ok(km, nc) || km->n != n || n > kMaxSolveN) return X2C_ERR_ARG;
       auto key = std::make_tuple(km->S, km->T, km->V, km->W0, nc == 4 ? km->Wx : nullptr);
       auto it = kind_index.find(key);
@@ -283,6 +332,97 @@ void end_call(x2c_ctx *ctx, const BuildPlan &plan) {
 }
 
 }  // namespace
+
+x2c_status ensure_stage(x2c_ctx *ctx, size_t bytes) {
+  if (bytes <= ctx->stage_bytes) return X2C_OK;
+  X2C_TRY_CUDA(ctx, cudaDeviceSynchronize());
+  if (ctx->stage) cudaFree(ctx->stage);
+  ctx->stage = nullptr;
+  ctx->stage_bytes = 0;
+  cudaError_t e = cudaMalloc(&ctx->stage, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    ctx->last_error = std::string("staging allocation: ") + cudaGetErrorString(e);
+    return X2C_ERR_NOMEM;
+  }
+  ctx->stage_bytes = bytes;
+  return X2C_OK;
+}
+
+x2c_status full_build(x2c_ctx *ctx, const x2c_options *opt, const x2c_mats *mol, const x2c_hout *h,
+                      const x2c_uout *U, cudaStream_t st, size_t *dry_bytes) {
+  X2C_TRY(begin_call(ctx));
+  X2C_TRY(check_options(opt));
+  const int nc = opt->two_component ? 4 : 1;
+  if (!mats_ok(mol, nc) || !h) return X2C_ERR_ARG;
+  if (mol->n > kMaxSolveN) return X2C_ERR_ARG;
+  x2c_options o = *opt;
+  o.dlu_potential = X2C_DLU_MOLECULAR_BLOCK;
+  o.precision = X2C_PREC_FP64;
+  o.so_same_atom_only = 1;  // one atom: the only pair is the diagonal one
+  int32_t offs[2] = {0, mol->n};
+  x2c_layout lay{1, offs, nullptr, 0, nullptr};
+  BuildPlan plan;
+  plan.nc = nc;
+  KindIndex kinds;
+  X2C_TRY(add_molecule(plan, &o, &lay, mol, h, 0, kinds));
+  std::vector<double *> ULp, USp;
+  X2C_TRY(run_plan(ctx, &o, plan, st, &ULp, &USp, dry_bytes));
+  if (dry_bytes) return X2C_OK;
+  if (U) {
+    const size_t n2 = (size_t)mol->n * mol->n;
+    for (int q = 0; q < nc; ++q) {
+      if (U->UL[q]) X2C_TRY_CUDA(ctx, cudaMemcpyAsync(U->UL[q], ULp[0] + q * n2, n2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      if (U->US[q]) X2C_TRY_CUDA(ctx, cudaMemcpyAsync(U->US[q], USp[0] + q * n2, n2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    }
+  }
+  end_call(ctx, plan);
+  return X2C_OK;
+}
+
+x2c_status dlu_build(x2c_ctx *ctx, const x2c_options *opt, int n_mol, const x2c_layout *layouts,
+                     const x2c_mats *mols, const x2c_hout *h, const KindTransforms *ku, cudaStream_t st,
+                     size_t *dry_bytes) {
+  X2C_TRY(begin_call(ctx));
+  X2C_TRY(check_options(opt));
+  if (n_mol < 1 || !layouts || !mols || !h) return X2C_ERR_ARG;
+  BuildPlan plan;
+  plan.nc = opt->two_component ? 4 : 1;
+  KindIndex kinds;
+  for (int i = 0; i < n_mol; ++i)
+    X2C_TRY(add_molecule(plan, opt, &layouts[i], &mols[i], &h[i], i, kinds, ku ? &ku[i] : nullptr));
+  X2C_TRY(run_plan(ctx, opt, plan, st, nullptr, nullptr, dry_bytes));
+  if (!dry_bytes) end_call(ctx, plan);
+  return X2C_OK;
+}
+
+x2c_status transforms_build(x2c_ctx *ctx, const x2c_options *opt, int n_problems, const x2c_mats *inputs,
+                            const x2c_uout *U, cudaStream_t st, size_t *dry_bytes) {
+  X2C_TRY(begin_call(ctx));
+  X2C_TRY(check_options(opt));
+  if (n_problems < 1 || !inputs || !U) return X2C_ERR_ARG;
+  BuildPlan plan;
+  plan.nc = opt->two_component ? 4 : 1;
+  for (int i = 0; i < n_problems; ++i) {
+    if (!mats_ok(&inputs[i], plan.nc) || inputs[i].n > kMaxSolveN) return X2C_ERR_ARG;
+    for (int q = 0; q < plan.nc; ++q)
+      if (!U[i].UL[q] || !U[i].US[q]) return X2C_ERR_ARG;
+    plan.problems.push_back({input_desc(&inputs[i], plan.nc, 0, inputs[i].n), inputs[i].n});
+  }
+  std::vector<double *> ULp, USp;
+  X2C_TRY(run_plan(ctx, opt, plan, st, &ULp, &USp, dry_bytes));
+  if (dry_bytes) return X2C_OK;
+  for (int i = 0; i < n_problems; ++i) {
+    const size_t n2 = (size_t)inputs[i].n * inputs[i].n;
+    for (int q = 0; q < plan.nc; ++q) {
+      X2C_TRY_CUDA(ctx, cudaMemcpyAsync(U[i].UL[q], ULp[i] + q * n2, n2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      X2C_TRY_CUDA(ctx, cudaMemcpyAsync(U[i].US[q], USp[i] + q * n2, n2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    }
+  }
+  end_call(ctx, plan);
+  return X2C_OK;
+}
+
 }  // namespace x2c
 
 using namespace x2c;
@@ -403,79 +543,63 @@ x2c_status x2c_ctx_kernel_times(x2c_ctx *ctx, int32_t max_entries, char *names, 
 
 x2c_status x2c_build_full(x2c_ctx *ctx, const x2c_options *opt, const x2c_mats *mol,
                           const x2c_hout *h, const x2c_uout *U, void *stream) {
-  X2C_TRY(begin_call(ctx));
-  X2C_TRY(check_options(opt));
-  const int nc = opt->two_component ? 4 : 1;
-  if (!mats_ok(mol, nc) || !h) return X2C_ERR_ARG;
-  if (mol->n > kMaxSolveN) return X2C_ERR_ARG;
-  x2c_options o = *opt;
-  o.dlu_potential = X2C_DLU_MOLECULAR_BLOCK;
-  o.precision = X2C_PREC_FP64;
-  o.so_same_atom_only = 1;  // one atom: the only pair is the diagonal one
-  int32_t offs[2] = {0, mol->n};
-  x2c_layout lay{1, offs, nullptr, 0, nullptr};
-  BuildPlan plan;
-  plan.nc = nc;
-  std::map<std::tuple<const double *, const double *, const double *, const double *, const double *>, int> kinds;
-  X2C_TRY(add_molecule(plan, &o, &lay, mol, h, 0, kinds));
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  std::vector<double *> ULp, USp;
-  X2C_TRY(run_plan(ctx, &o, plan, st, &ULp, &USp));
-  if (U) {
-    const size_t n2 = (size_t)mol->n * mol->n;
-    for (int q = 0; q < nc; ++q) {
-      if (U->UL[q]) X2C_TRY_CUDA(ctx, cudaMemcpyAsync(U->UL[q], ULp[0] + q * n2, n2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
-      if (U->US[q]) X2C_TRY_CUDA(ctx, cudaMemcpyAsync(U->US[q], USp[0] + q * n2, n2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    }
-  }
-  end_call(ctx, plan);
-  return X2C_OK;
+  return full_build(ctx, opt, mol, h, U, static_cast<cudaStream_t>(stream), nullptr);
 }
 
 x2c_status x2c_build_dlu(x2c_ctx *ctx, const x2c_options *opt, const x2c_layout *layout,
                          const x2c_mats *mol, const x2c_hout *h, void *stream) {
-  return x2c_build_dlu_batched(ctx, opt, 1, layout, mol, h, stream);
+  return dlu_build(ctx, opt, 1, layout, mol, h, nullptr, static_cast<cudaStream_t>(stream), nullptr);
 }
 
 x2c_status x2c_build_dlu_batched(x2c_ctx *ctx, const x2c_options *opt, int32_t n_mol,
                                  const x2c_layout *layouts, const x2c_mats *mols,
                                  const x2c_hout *h, void *stream) {
+  return dlu_build(ctx, opt, n_mol, layouts, mols, h, nullptr, static_cast<cudaStream_t>(stream), nullptr);
+}
+
+x2c_status x2c_build_dlu_with_transforms(x2c_ctx *ctx, const x2c_options *opt, const x2c_layout *layout,
+                                         const x2c_uout *kind_U, const x2c_mats *mol, const x2c_hout *h,
+                                         void *stream) {
   X2C_TRY(begin_call(ctx));
   X2C_TRY(check_options(opt));
-  if (n_mol < 1 || !layouts || !mols || !h) return X2C_ERR_ARG;
-  BuildPlan plan;
-  plan.nc = opt->two_component ? 4 : 1;
-  std::map<std::tuple<const double *, const double *, const double *, const double *, const double *>, int> kinds;
-  for (int i = 0; i < n_mol; ++i) X2C_TRY(add_molecule(plan, opt, &layouts[i], &mols[i], &h[i], i, kinds));
-  X2C_TRY(run_plan(ctx, opt, plan, static_cast<cudaStream_t>(stream)));
-  end_call(ctx, plan);
-  return X2C_OK;
+  if (!layout || !kind_U || !mol || layout->n_kinds < 1 || !layout->kinds ||
+      opt->dlu_potential != X2C_DLU_FREE_ATOM)
+    return X2C_ERR_ARG;
+  const int nc = opt->two_component ? 4 : 1;
+  const int nk = layout->n_kinds;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // the assembly reads each kind's parts contiguously (part-major): gather them into the
+  // staging area unless they already are
+  std::vector<size_t> off(nk + 1, 0);
+  for (int k = 0; k < nk; ++k) {
+    const int n = layout->kinds[k].n;
+    if (n < 1 || n > kMaxSolveN) return X2C_ERR_ARG;
+    for (int q = 0; q < nc; ++q)
+      if (!kind_U[k].UL[q] || !kind_U[k].US[q]) return X2C_ERR_ARG;
+    off[k + 1] = off[k] + 2 * (size_t)nc * n * n;
+  }
+  X2C_TRY(ensure_stage(ctx, off[nk] * sizeof(double)));
+  double *stage = reinterpret_cast<double *>(ctx->stage);
+  std::vector<const double *> ul(nk), us(nk);
+  for (int k = 0; k < nk; ++k) {
+    const size_t n2 = (size_t)layout->kinds[k].n * layout->kinds[k].n;
+    double *dst = stage + off[k];
+    for (int q = 0; q < nc; ++q) {
+      X2C_TRY_CUDA(ctx, cudaMemcpyAsync(dst + q * n2, kind_U[k].UL[q], n2 * sizeof(double),
+                                        cudaMemcpyDeviceToDevice, st));
+      X2C_TRY_CUDA(ctx, cudaMemcpyAsync(dst + (nc + q) * n2, kind_U[k].US[q], n2 * sizeof(double),
+                                        cudaMemcpyDeviceToDevice, st));
+    }
+    ul[k] = dst;
+    us[k] = dst + nc * n2;
+  }
+  KindTransforms ku{ul.data(), us.data()};
+  return dlu_build(ctx, opt, 1, layout, mol, h, &ku, st, nullptr);
 }
 
 x2c_status x2c_atomic_transforms(x2c_ctx *ctx, const x2c_options *opt, int32_t n_problems,
                                  const x2c_mats *inputs, const x2c_uout *U, void *stream) {
-  X2C_TRY(begin_call(ctx));
-  X2C_TRY(check_options(opt));
-  if (n_problems < 1 || !inputs || !U) return X2C_ERR_ARG;
-  BuildPlan plan;
-  plan.nc = opt->two_component ? 4 : 1;
-  for (int i = 0; i < n_problems; ++i) {
-    if (!mats_ok(&inputs[i], plan.nc) || inputs[i].n > kMaxSolveN) return X2C_ERR_ARG;
-    plan.problems.push_back({input_desc(&inputs[i], plan.nc, 0, inputs[i].n), inputs[i].n});
-  }
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  std::vector<double *> ULp, USp;
-  X2C_TRY(run_plan(ctx, opt, plan, st, &ULp, &USp));
-  for (int i = 0; i < n_problems; ++i) {
-    const size_t n2 = (size_t)inputs[i].n * inputs[i].n;
-    for (int q = 0; q < plan.nc; ++q) {
-      if (!U[i].UL[q] || !U[i].US[q]) return X2C_ERR_ARG;
-      X2C_TRY_CUDA(ctx, cudaMemcpyAsync(U[i].UL[q], ULp[i] + q * n2, n2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
-      X2C_TRY_CUDA(ctx, cudaMemcpyAsync(U[i].US[q], USp[i] + q * n2, n2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    }
-  }
-  end_call(ctx, plan);
-  return X2C_OK;
+  return transforms_build(ctx, opt, n_problems, inputs, U, static_cast<cudaStream_t>(stream), nullptr);
 }
 
 x2c_status x2c_quaternion_to_dense(const double *const h[4], int32_t n, double *out, void *stream) {

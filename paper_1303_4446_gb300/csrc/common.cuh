@@ -44,6 +44,9 @@ struct x2c_ctx {
   std::vector<Pending> pending;
   std::map<std::string, KernelTotals> kernel_ms;
   std::string names_buf;
+  // when set, the workspace grows stream-ordered from this pool on the call's stream
+  // (no device-wide synchronisation; used by the server, whose slots run concurrently)
+  cudaMemPool_t pool = nullptr;
 };
 
 namespace x2c {
@@ -147,8 +150,31 @@ struct Arena {
 };
 inline size_t arena_doubles(size_t n) { return ((n * sizeof(double) + 255) / 256) * 256; }
 
-// Grow the context workspace to at least `bytes` (synchronises the device when it grows).
-x2c_status ensure_workspace(x2c_ctx *ctx, size_t bytes, Arena *out);
+// Grow the context workspace to at least `bytes` (synchronises the device when it grows,
+// unless the context has a pool: then the growth is stream-ordered on `st`).
+x2c_status ensure_workspace(x2c_ctx *ctx, size_t bytes, Arena *out, cudaStream_t st);
+// Workspace size the context holds after a call that needs `bytes`.
+size_t workspace_after_growth(const x2c_ctx *ctx, size_t bytes);
+// Grow the staging area of the host-buffer calls (synchronises the device when it grows).
+x2c_status ensure_stage(x2c_ctx *ctx, size_t bytes);
+
+// Argument checks shared by the entry points.
+bool mats_ok(const x2c_mats *m, int nc);
+x2c_status check_options(const x2c_options *o);
+
+// Entry points shared by the C ABI and the server.  With dry_bytes non-NULL nothing is
+// enqueued: *dry_bytes receives the workspace the call needs.
+struct KindTransforms {
+  const double *const *UL;  // host arrays indexed by kind: device U^L, U^S of that kind,
+  const double *const *US;  // nc n^2 doubles each, part-major (NULL entry = solve it)
+};
+x2c_status full_build(x2c_ctx *ctx, const x2c_options *opt, const x2c_mats *mol, const x2c_hout *h,
+                      const x2c_uout *U, cudaStream_t st, size_t *dry_bytes);
+x2c_status dlu_build(x2c_ctx *ctx, const x2c_options *opt, int n_mol, const x2c_layout *layouts,
+                     const x2c_mats *mols, const x2c_hout *h, const KindTransforms *ku, cudaStream_t st,
+                     size_t *dry_bytes);
+x2c_status transforms_build(x2c_ctx *ctx, const x2c_options *opt, int n_problems, const x2c_mats *inputs,
+                            const x2c_uout *U, cudaStream_t st, size_t *dry_bytes);
 
 // Descriptor of one decoupling problem's inputs (device pointers, leading dimension ld).
 struct InputDesc {

@@ -3,23 +3,9 @@
 
 #include "common.cuh"
 
-namespace {
+using x2c::ensure_stage;
 
-x2c_status ensure_stage(x2c_ctx *ctx, size_t bytes) {
-  if (bytes <= ctx->stage_bytes) return X2C_OK;
-  X2C_TRY_CUDA(ctx, cudaDeviceSynchronize());
-  if (ctx->stage) cudaFree(ctx->stage);
-  ctx->stage = nullptr;
-  ctx->stage_bytes = 0;
-  cudaError_t e = cudaMalloc(&ctx->stage, bytes);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    ctx->last_error = std::string("staging allocation: ") + cudaGetErrorString(e);
-    return X2C_ERR_NOMEM;
-  }
-  ctx->stage_bytes = bytes;
-  return X2C_OK;
-}
+namespace {
 
 // Copy the diagonal blocks of an N x N host matrix into the same places of a device matrix.
 x2c_status copy_diag_blocks(x2c_ctx *ctx, double *dst, const double *src, int64_t N,

@@ -14,5 +14,14 @@ int main(void) {
   printf("layout %zu %zu %zu %zu\n", sizeof(x2c_layout), offsetof(x2c_layout, atom_offset),
          offsetof(x2c_layout, n_kinds), offsetof(x2c_layout, kinds));
   printf("counters %zu %zu\n", sizeof(x2c_counters), offsetof(x2c_counters, credited_flops));
+  printf("server_options %zu %zu %zu\n", sizeof(x2c_server_options), offsetof(x2c_server_options, hbm_budget_bytes),
+         offsetof(x2c_server_options, reserved));
+  printf("request %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(x2c_request), offsetof(x2c_request, kind),
+         offsetof(x2c_request, layout), offsetof(x2c_request, kind_key), offsetof(x2c_request, mol),
+         offsetof(x2c_request, ld), offsetof(x2c_request, out), offsetof(x2c_request, t_arrival));
+  printf("result %zu %zu %zu %zu\n", sizeof(x2c_result), offsetof(x2c_result, h), offsetof(x2c_result, t_end),
+         offsetof(x2c_result, slot));
+  printf("server_stats %zu %zu %zu %zu\n", sizeof(x2c_server_stats), offsetof(x2c_server_stats, latency_p50_ms),
+         offsetof(x2c_server_stats, bytes_in_use), offsetof(x2c_server_stats, max_concurrent));
   return 0;
 }

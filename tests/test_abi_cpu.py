@@ -50,6 +50,13 @@ def test_ctypes_structs_match_header(tmp_path):
     L = abi.Layout
     assert out["layout"] == [ctypes.sizeof(L), L.atom_offset.offset, L.n_kinds.offset, L.kinds.offset]
     assert out["counters"] == [ctypes.sizeof(abi.Counters), abi.Counters.credited_flops.offset]
+    SO, R, Re, SS = abi.ServerOptions, abi.Request, abi.Result, abi.ServerStats
+    assert out["server_options"] == [ctypes.sizeof(SO), SO.hbm_budget_bytes.offset, SO.reserved.offset]
+    assert out["request"] == [ctypes.sizeof(R), R.kind.offset, R.layout.offset, R.kind_key.offset, R.mol.offset,
+                              R.ld.offset, R.out.offset, R.t_arrival.offset]
+    assert out["result"] == [ctypes.sizeof(Re), Re.h.offset, Re.t_end.offset, Re.slot.offset]
+    assert out["server_stats"] == [ctypes.sizeof(SS), SS.latency_p50_ms.offset, SS.bytes_in_use.offset,
+                                   SS.max_concurrent.offset]
 
 
 def _spinor(parts):
