@@ -241,7 +241,6 @@ x2c_status add_molecule(BuildPlan &plan, const x2c_options *opt, const x2c_layou
   if (opt->dlu_potential == X2C_DLU_MOLECULAR_BLOCK) {
     for (int a = 0; a < L; ++a) {
       const int n = lay->atom_offset[a + 1] - lay->atom_offset[a];
-      if (n > kMaxSolveN) return X2C_ERR_ARG;
       uidx[a] = (int)plan.problems.size();
       plan.problems.push_back({input_desc(mol, nc, lay->atom_offset[a], mol->n), n});
     }
@@ -270,7 +269,7 @@ x2c_status add_molecule(BuildPlan &plan, const x2c_options *opt, const x2c_layou
         uidx[a] = it->second;
         continue;
       }
-      if (!mats_ok(km, nc) || km->n != n || n > kMaxSolveN) return X2C_ERR_ARG;
+      if (!mats_ok(km, nc) || km->n != n) return X2C_ERR_ARG;
       auto key = std::make_tuple(km->S, km->T, km->V, km->W0, nc == 4 ? km->Wx : nullptr);
       auto it = kind_index.find(key);
       if (it == kind_index.end()) {
@@ -355,7 +354,6 @@ x2c_status full_build(x2c_ctx *ctx, const x2c_options *opt, const x2c_mats *mol,
   X2C_TRY(check_options(opt));
   const int nc = opt->two_component ? 4 : 1;
   if (!mats_ok(mol, nc) || !h) return X2C_ERR_ARG;
-  if (mol->n > kMaxSolveN) return X2C_ERR_ARG;
   x2c_options o = *opt;
   o.dlu_potential = X2C_DLU_MOLECULAR_BLOCK;
   o.precision = X2C_PREC_FP64;
@@ -404,7 +402,7 @@ x2c_status transforms_build(x2c_ctx *ctx, const x2c_options *opt, int n_problems
   BuildPlan plan;
   plan.nc = opt->two_component ? 4 : 1;
   for (int i = 0; i < n_problems; ++i) {
-    if (!mats_ok(&inputs[i], plan.nc) || inputs[i].n > kMaxSolveN) return X2C_ERR_ARG;
+    if (!mats_ok(&inputs[i], plan.nc)) return X2C_ERR_ARG;
     for (int q = 0; q < plan.nc; ++q)
       if (!U[i].UL[q] || !U[i].US[q]) return X2C_ERR_ARG;
     plan.problems.push_back({input_desc(&inputs[i], plan.nc, 0, inputs[i].n), inputs[i].n});
@@ -573,7 +571,7 @@ x2c_status x2c_build_dlu_with_transforms(x2c_ctx *ctx, const x2c_options *opt, c
   std::vector<size_t> off(nk + 1, 0);
   for (int k = 0; k < nk; ++k) {
     const int n = layout->kinds[k].n;
-    if (n < 1 || n > kMaxSolveN) return X2C_ERR_ARG;
+    if (n < 1) return X2C_ERR_ARG;
     for (int q = 0; q < nc; ++q)
       if (!kind_U[k].UL[q] || !kind_U[k].US[q]) return X2C_ERR_ARG;
     off[k + 1] = off[k] + 2 * (size_t)nc * n * n;

@@ -187,7 +187,7 @@ struct InputDesc {
 // size n with nc = 1 (scalar) or 4 (two-component) parts.  d_in: device array of nb
 // descriptors.  UL, US: device, nb * nc * n * n doubles each (problem-major, then part).
 // Scratch comes from `ar` (passed by value: the caller's arena is not advanced).
-constexpr int kMaxSolveN = 168;
+constexpr int kMaxSolveN = 168;  // largest n factorised in one CTA (bigger: blocked)
 x2c_status solve_transforms(x2c_ctx *ctx, cudaStream_t st, double c, int nb, int n, int nc,
                             const InputDesc *d_in, double *UL, double *US, Arena ar);
 size_t solve_workspace_bytes(int nb, int n, int nc);

@@ -102,7 +102,8 @@ __global__ void __launch_bounds__(Cfg::NT) gemm_f64_kernel(AOp A, BOp B, COp C, 
   constexpr int NTX = Cfg::NTX, NTY = Cfg::NTY, NT = Cfg::NT;
   const int b = blockIdx.x;
   const int M = D.M(b), N = D.N(b), K = D.K(b);
-  const int tm = blockIdx.y / tiles_n, tn = blockIdx.y - (blockIdx.y / tiles_n) * tiles_n;
+  const int tile = blockIdx.y + blockIdx.z * gridDim.y;  // grid.z only when tiles > 65535
+  const int tm = tile / tiles_n, tn = tile - (tile / tiles_n) * tiles_n;
   const int m0 = tm * BM, n0 = tn * BN;
   if (m0 >= M || n0 >= N) return;
 
@@ -165,7 +166,7 @@ inline double dims_flops(const UniformDims &d, int batch) { return 2.0 * d.m * d
 struct SplitDims;
 inline double dims_flops(const SplitDims &d, int);
 
-// Launch helper: grid.x = batch entries, grid.y = tiles of the largest M x N.
+// Launch helper: grid.x = batch entries, grid.y (and z) = tiles of the largest M x N.
 template <class Cfg, class AOp, class BOp, class COp, class Dims>
 inline x2c_status gemm_f64(x2c_ctx *ctx, cudaStream_t st, int batch, int max_m, int max_n,
                            const AOp &A, const BOp &B, const COp &C, const Dims &D,
@@ -173,7 +174,8 @@ inline x2c_status gemm_f64(x2c_ctx *ctx, cudaStream_t st, int batch, int max_m, 
   if (batch <= 0 || max_m <= 0 || max_n <= 0) return X2C_OK;
   const int tiles_m = (max_m + Cfg::BM - 1) / Cfg::BM;
   const int tiles_n = (max_n + Cfg::BN - 1) / Cfg::BN;
-  dim3 grid(batch, tiles_m * tiles_n);
+  const int tiles = tiles_m * tiles_n;
+  dim3 grid(batch, std::min(tiles, 65535), (tiles + 65534) / 65535);
   tbegin(ctx, st);
   gemm_f64_kernel<Cfg><<<grid, Cfg::NT, 0, st>>>(A, B, C, D, tiles_n);
   return launched(ctx, name, st, dims_flops(D, batch));
@@ -255,5 +257,7 @@ inline int choose_splits(int batch, int m, int n, int k) {
 // Default tile for the dense (square-ish) products of the decoupling solve.
 using TileSolve = TileCfg<64, 64, 16, 4, 4>;
 using TileSmall = TileCfg<32, 32, 16, 2, 2>;
+// Large dense products (full X2C of a whole molecule): 96 x 64 tiles, 24 accumulators.
+using TileLarge = TileCfg<96, 64, 16, 6, 4>;
 
 }  // namespace x2c

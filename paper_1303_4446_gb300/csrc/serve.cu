@@ -162,16 +162,14 @@ x2c_status prepare(x2c_server *s, const x2c_request *in, Request &r) {
   r.ld = in->ld ? in->ld : r.n;
   if (r.ld < r.n) return X2C_ERR_ARG;
   const bool free_atom = in->kind == X2C_REQ_DLU && in->opt.dlu_potential == X2C_DLU_FREE_ATOM;
-  if (in->kind == X2C_REQ_FULL) {
-    if (r.n > x2c::kMaxSolveN) return X2C_ERR_ARG;
-  } else {
+  if (in->kind != X2C_REQ_FULL) {
     const x2c_layout &L = in->layout;
     if (L.n_atoms < 1 || !L.atom_offset) return X2C_ERR_ARG;
     r.offsets.assign(L.atom_offset, L.atom_offset + L.n_atoms + 1);
     if (r.offsets[0] != 0 || r.offsets[L.n_atoms] != r.n) return X2C_ERR_ARG;
     for (int a = 0; a < L.n_atoms; ++a) {
       const int na = r.offsets[a + 1] - r.offsets[a];
-      if (na < 1 || na > x2c::kMaxSolveN) return X2C_ERR_ARG;
+      if (na < 1) return X2C_ERR_ARG;
     }
     if (free_atom) {
       if (!L.atom_kind || L.n_kinds < 1 || !L.kinds) return X2C_ERR_ARG;
@@ -395,41 +393,58 @@ void x2c_server::launch(int si, std::vector<ReqPtr> &batch) {
       }
       char *p = r.in_slab;
       const cudaMemcpyKind kind = r.rq.memory == X2C_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
-      auto put = [&](const double *src, int64_t n, int64_t ld) -> const double * {
+      // Blocks a build reads: everything (full X2C), the upper block triangle A <= B (pair
+      // blocks of DLU), or the same-atom blocks only (DLU: S in molecular-block mode, and
+      // Wx, Wy, Wz when they vanish across atoms).  The copy keeps the n x n layout.
+      enum Blocks { kAll, kUpper, kDiag };
+      auto put = [&](const double *src, int64_t n, int64_t ld, Blocks which) -> const double * {
         double *dst = reinterpret_cast<double *>(p);
         p += round256(mat_bytes(n));
-        if (cudaMemcpy2DAsync(dst, n * sizeof(double), src, ld * sizeof(double), n * sizeof(double), n, kind, s) !=
-            cudaSuccess) {
-          cudaGetLastError();
-          fail(X2C_ERR_CUDA);
+        auto copy = [&](int64_t r0, int64_t c0, int64_t rows, int64_t cols) {
+          if (cudaMemcpy2DAsync(dst + r0 * n + c0, n * sizeof(double), src + r0 * ld + c0, ld * sizeof(double),
+                                cols * sizeof(double), rows, kind, s) != cudaSuccess) {
+            cudaGetLastError();
+            fail(X2C_ERR_CUDA);
+          }
+        };
+        if (which == kAll || r.offsets.empty()) {
+          copy(0, 0, n, n);
+        } else {
+          for (size_t a = 0; a + 1 < r.offsets.size(); ++a) {
+            const int64_t o = r.offsets[a], na = r.offsets[a + 1] - o;
+            copy(o, o, na, which == kUpper ? n - o : na);
+          }
         }
         return dst;
       };
       const bool free_atom = r.rq.kind == X2C_REQ_DLU && opt.dlu_potential == X2C_DLU_FREE_ATOM;
+      const Blocks pair = r.rq.kind == X2C_REQ_FULL ? kAll : kUpper;
+      const Blocks same = r.rq.kind == X2C_REQ_FULL ? kAll : kDiag;
+      const Blocks so = (r.rq.kind == X2C_REQ_FULL || !opt.so_same_atom_only) ? pair : kDiag;
       if (r.copy_in) {
-        r.dmol.T = put(r.rq.mol.T, r.n, r.ld);
-        r.dmol.V = put(r.rq.mol.V, r.n, r.ld);
-        r.dmol.W0 = put(r.rq.mol.W0, r.n, r.ld);
+        r.dmol.T = put(r.rq.mol.T, r.n, r.ld, pair);
+        r.dmol.V = put(r.rq.mol.V, r.n, r.ld, pair);
+        r.dmol.W0 = put(r.rq.mol.W0, r.n, r.ld, pair);
         // free-atom DLU never reads the molecular S: any valid device address will do
-        r.dmol.S = free_atom ? r.dmol.T : put(r.rq.mol.S, r.n, r.ld);
+        r.dmol.S = free_atom ? r.dmol.T : put(r.rq.mol.S, r.n, r.ld, same);
         if (nc == 4) {
-          r.dmol.Wx = put(r.rq.mol.Wx, r.n, r.ld);
-          r.dmol.Wy = put(r.rq.mol.Wy, r.n, r.ld);
-          r.dmol.Wz = put(r.rq.mol.Wz, r.n, r.ld);
+          r.dmol.Wx = put(r.rq.mol.Wx, r.n, r.ld, so);
+          r.dmol.Wy = put(r.rq.mol.Wy, r.n, r.ld, so);
+          r.dmol.Wz = put(r.rq.mol.Wz, r.n, r.ld, so);
         }
       }
       if (r.rq.memory == X2C_MEM_HOST && free_atom) {
         for (size_t ki = 0; ki < r.dkinds.size(); ++ki) {
           if (!r.used[ki]) continue;
           x2c_mats &k = r.dkinds[ki];
-          k.S = put(k.S, k.n, k.n);
-          k.T = put(k.T, k.n, k.n);
-          k.V = put(k.V, k.n, k.n);
-          k.W0 = put(k.W0, k.n, k.n);
+          k.S = put(k.S, k.n, k.n, kAll);
+          k.T = put(k.T, k.n, k.n, kAll);
+          k.V = put(k.V, k.n, k.n, kAll);
+          k.W0 = put(k.W0, k.n, k.n, kAll);
           if (nc == 4) {
-            k.Wx = put(k.Wx, k.n, k.n);
-            k.Wy = put(k.Wy, k.n, k.n);
-            k.Wz = put(k.Wz, k.n, k.n);
+            k.Wx = put(k.Wx, k.n, k.n, kAll);
+            k.Wy = put(k.Wy, k.n, k.n, kAll);
+            k.Wz = put(k.Wz, k.n, k.n, kAll);
           }
         }
       }

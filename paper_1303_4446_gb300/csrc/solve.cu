@@ -22,6 +22,7 @@
 // Two-component matrices are handled in the quaternion form (four real parts), so every
 // product is a real GEMM with the quaternion left-multiplication matrix read in place.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 
 #include "common.cuh"
@@ -104,6 +105,69 @@ __global__ void chol_inv_kernel(const InputDesc *in, int n, double *fac, double 
   }
 }
 
+// Leaf of the blocked factorisation of large matrices: Cholesky factor F (lower, zeros
+// above the diagonal) and its inverse X of the n x n block at A (leading dimension lda),
+// n <= kLeaf, one CTA, factorisation in shared memory as in chol_inv_kernel.
+constexpr int kLeaf = 128;
+__global__ void chol_leaf_kernel(const double *Ain, int64_t lda, int n, double *F, double *X, int64_t ld,
+                                 int *status) {
+  extern __shared__ double A[];
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int i = idx / n, j = idx - i * n;
+    A[idx] = Ain[(int64_t)i * lda + j];
+  }
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    if (threadIdx.x == 0) {
+      double p = A[j * n + j];
+      if (!(p > 0.0)) {
+        bad = 1;
+        p = 1.0;
+      }
+      A[j * n + j] = sqrt(p);
+    }
+    __syncthreads();
+    const double piv = A[j * n + j];
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[i * n + j] /= piv;
+    __syncthreads();
+    const int w = n - j - 1;
+    for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
+      const int i = j + 1 + idx / w, k = j + 1 + idx % w;
+      if (k <= i) A[i * n + k] -= A[i * n + j] * A[k * n + j];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && bad) flag_error(status, X2C_DEV_NOT_POSDEF);
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int i = idx / n, k = idx - i * n;
+    F[(int64_t)i * ld + k] = (k <= i) ? A[idx] : 0.0;
+    X[(int64_t)i * ld + k] = 0.0;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    X[(int64_t)j * ld + j] = 1.0 / A[j * n + j];
+    for (int i = j + 1; i < n; ++i) {
+      double s = 0.0;
+      for (int k = j; k < i; ++k) s = fma(A[i * n + k], X[(int64_t)k * ld + j], s);
+      X[(int64_t)i * ld + j] = -s / A[i * n + i];
+    }
+  }
+}
+
+// Copy S (which = 0) or T (which = 1) of problem `prob` into a dense n x n matrix.
+__global__ void copy_input_kernel(const InputDesc *in, int prob, int which, int n, double *dst) {
+  const InputDesc d = in[prob];
+  const double *src = which ? d.T : d.S;
+  const int64_t total = (int64_t)n * n;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx / n, j = idx - i * n;
+    dst[idx] = src[i * d.ld + j];
+  }
+}
+
 // B operand reading an input matrix of problem bb / div (part bb % div for W).
 struct InputOp {
   const InputDesc *d;
@@ -133,17 +197,19 @@ struct MatDiv {
 };
 
 // Z = H^p + c^2 (Eq. 14 in the Cholesky-orthonormal basis), parts of size 2n x 2n.
+// grid.x = problem x part, grid.y strides over the elements.
 __global__ void assemble_hp_kernel(int n, int nc, double c, const double *Vt, const double *LSm,
                                    const double *Wt, double *Z) {
   const int prob = blockIdx.x / nc, q = blockIdx.x % nc;
-  const int d = 2 * n;
+  const int64_t d = 2 * n;
   const double c2 = c * c;
   const double *vt = Vt + (int64_t)prob * n * n;
   const double *ls = LSm + (int64_t)prob * n * n;
   const double *wt = Wt + ((int64_t)prob * nc + q) * n * n;
   double *z = Z + ((int64_t)prob * nc + q) * d * d;
-  for (int idx = threadIdx.x; idx < d * d; idx += blockDim.x) {
-    const int r = idx / d, col = idx - r * d;
+  for (int64_t idx = blockIdx.y * (int64_t)blockDim.x + threadIdx.x; idx < d * d;
+       idx += (int64_t)gridDim.y * blockDim.x) {
+    const int64_t r = idx / d, col = idx - r * d;
     double v = 0.0;
     if (r < n && col < n) {
       if (q == 0) v = vt[r * n + col] + (r == col ? c2 : 0.0);
@@ -190,15 +256,23 @@ __device__ double block_sum(double v, double *red) {
   return v;
 }
 
-// Scale every problem's Z by an upper bound of its spectral radius: the largest row sum of
-// quaternion moduli (a Gershgorin bound of the equivalent complex matrix).
-__global__ void normalise_kernel(int d, int nc, double *Z, int *status) {
+// Maximum of non-negative doubles across CTAs: their bit patterns order like the values
+// (a NaN compares above every finite value and is caught by the consumer).
+__device__ void atomic_max_nonneg(unsigned long long *slot, double v) {
+  atomicMax(slot, static_cast<unsigned long long>(__double_as_longlong(v)));
+}
+
+// Gershgorin bound of every problem's Z: the largest row sum of quaternion moduli (a bound
+// of the spectral radius of the equivalent complex matrix).  One warp per row, grid.x =
+// problem, grid.y strides over rows; the maximum goes to mx[problem] (zeroed before).
+__global__ void gershgorin_kernel(int d, int nc, const double *Z, unsigned long long *mx) {
   __shared__ double red[32];
-  double *z = Z + (int64_t)blockIdx.x * nc * d * d;
-  double mx = 0.0;
-  for (int r = threadIdx.x; r < d; r += blockDim.x) {
+  const double *z = Z + (int64_t)blockIdx.x * nc * d * d;
+  const int warps = blockDim.x >> 5, w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  double best = 0.0;
+  for (int r = blockIdx.y * warps + w; r < d; r += gridDim.y * warps) {
     double s = 0.0;
-    for (int col = 0; col < d; ++col) {
+    for (int col = l; col < d; col += 32) {
       double q2 = 0.0;
       for (int q = 0; q < nc; ++q) {
         const double v = z[(int64_t)q * d * d + (int64_t)r * d + col];
@@ -206,53 +280,75 @@ __global__ void normalise_kernel(int d, int nc, double *Z, int *status) {
       }
       s += sqrt(q2);
     }
-    mx = fmax(mx, s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    best = fmax(best, s);
   }
-  mx = block_max(mx, red);
-  if (!(mx > 0.0) || !isfinite(mx)) {
-    if (threadIdx.x == 0) flag_error(status, X2C_DEV_NONFINITE);
-    mx = 1.0;
-  }
-  const double inv = 1.0 / mx;
-  for (int64_t idx = threadIdx.x; idx < (int64_t)nc * d * d; idx += blockDim.x) z[idx] *= inv;
+  best = block_max(best, red);
+  if (threadIdx.x == 0) atomic_max_nonneg(&mx[blockIdx.x], best);
 }
 
-// Convergence checks: ||Y - 1||_max of the last squared iterate and, for the sign
-// function, |trace Z_0| < 1/2 (equal numbers of positive- and negative-energy states).
-__global__ void check_kernel(int d, int nc, const double *Y, const double *Z, double tol,
-                             int trace_check, int *status) {
+// Z /= its Gershgorin bound (a bad bound is flagged and the scale left at 1).
+__global__ void scale_kernel(int64_t per, double *Z, const unsigned long long *mx, int *status) {
+  double m = __longlong_as_double(static_cast<long long>(mx[blockIdx.x]));
+  if (!(m > 0.0) || !isfinite(m)) {
+    if (blockIdx.y == 0 && threadIdx.x == 0) flag_error(status, X2C_DEV_NONFINITE);
+    m = 1.0;
+  }
+  const double inv = 1.0 / m;
+  double *z = Z + (int64_t)blockIdx.x * per;
+  for (int64_t idx = blockIdx.y * (int64_t)blockDim.x + threadIdx.x; idx < per;
+       idx += (int64_t)gridDim.y * blockDim.x)
+    z[idx] *= inv;
+}
+
+// Convergence checks: ||Y - 1||_max of the last squared iterate (into dev[problem]) and,
+// for the sign function, trace Z_0 (into tr[problem]); both zeroed before.
+__global__ void deviation_kernel(int d, int nc, const double *Y, unsigned long long *dev) {
   __shared__ double red[32];
   const double *y = Y + (int64_t)blockIdx.x * nc * d * d;
+  const int64_t total = (int64_t)nc * d * d;
   double mx = 0.0;
-  for (int64_t idx = threadIdx.x; idx < (int64_t)nc * d * d; idx += blockDim.x) {
+  for (int64_t idx = blockIdx.y * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.y * blockDim.x) {
     const int64_t rr = idx / d, col = idx % d;
     double v = y[idx] - ((rr == col) ? 1.0 : 0.0);  // part 0 rows are rr < d
     if (!isfinite(v)) v = 1e300;
     mx = fmax(mx, fabs(v));
   }
   mx = block_max(mx, red);
-  double tr = 0.0;
-  if (trace_check) {
-    const double *z = Z + (int64_t)blockIdx.x * nc * d * d;
-    for (int r = threadIdx.x; r < d; r += blockDim.x) tr += z[(int64_t)r * d + r];
-    tr = block_sum(tr, red);
-  }
-  if (threadIdx.x == 0) {
-    if (!(mx <= tol)) flag_error(status, mx >= 1e299 ? X2C_DEV_NONFINITE : X2C_DEV_NOCONV);
-    if (trace_check && !(fabs(tr) < 0.5)) flag_error(status, X2C_DEV_DECOUPLING);
+  if (threadIdx.x == 0) atomic_max_nonneg(&dev[blockIdx.x], mx);
+}
+
+__global__ void trace_kernel(int d, int nc, const double *Z, double *tr) {
+  __shared__ double red[32];
+  const double *z = Z + (int64_t)blockIdx.x * nc * d * d;
+  double t = 0.0;
+  for (int r = threadIdx.x; r < d; r += blockDim.x) t += z[(int64_t)r * d + r];
+  t = block_sum(t, red);
+  if (threadIdx.x == 0) tr[blockIdx.x] = t;
+}
+
+__global__ void check_final_kernel(int nb, const unsigned long long *dev, const double *tr, double tol,
+                                   int *status) {
+  for (int p = threadIdx.x; p < nb; p += blockDim.x) {
+    const double m = __longlong_as_double(static_cast<long long>(dev[p]));
+    if (!(m <= tol)) flag_error(status, m >= 1e299 ? X2C_DEV_NONFINITE : X2C_DEV_NOCONV);
+    if (tr && !(fabs(tr[p]) < 0.5)) flag_error(status, X2C_DEV_DECOUPLING);
   }
 }
 
 // P = (1 + Z)/2 blocks: P_LL (Hermitian part of the LL block) and P_SL.
 __global__ void projector_kernel(int n, int nc, const double *Z, double *PLL, double *PSL) {
   const int prob = blockIdx.x / nc, q = blockIdx.x % nc;
-  const int d = 2 * n;
+  const int64_t d = 2 * n;
   const double *z = Z + ((int64_t)prob * nc + q) * d * d;
   double *pll = PLL + ((int64_t)prob * nc + q) * n * n;
   double *psl = PSL + ((int64_t)prob * nc + q) * n * n;
   const double sgn = (q == 0) ? 1.0 : -1.0;  // part 0 symmetric, parts 1-3 antisymmetric
-  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-    const int i = idx / n, j = idx - i * n;
+  const int64_t total = (int64_t)n * n;
+  for (int64_t idx = blockIdx.y * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.y * blockDim.x) {
+    const int64_t i = idx / n, j = idx - i * n;
     const double h = 0.5 * (z[i * d + j] + sgn * z[j * d + i]);
     pll[idx] = 0.5 * h + ((q == 0 && i == j) ? 0.5 : 0.0);
     psl[idx] = 0.5 * z[(n + i) * d + j];
@@ -263,10 +359,20 @@ __global__ void projector_kernel(int n, int nc, const double *Z, double *PLL, do
 __global__ void identity_kernel(int n, int nc, double *X) {
   const int prob = blockIdx.x;
   double *x = X + (int64_t)prob * nc * n * n;
-  for (int64_t idx = threadIdx.x; idx < (int64_t)nc * n * n; idx += blockDim.x) {
+  const int64_t total = (int64_t)nc * n * n;
+  for (int64_t idx = blockIdx.y * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.y * blockDim.x) {
     const int64_t r = idx / n, col = idx % n;
     x[idx] = (r == col) ? 1.0 : 0.0;
   }
+}
+
+// Grid of an element-wise kernel: x = `rows` independent blocks of `elems` elements each,
+// y = enough CTAs of 256 threads to cover them, about two waves in total.
+dim3 aux_grid(int rows, int64_t elems) {
+  int64_t y = (elems + 256 * 8 - 1) / (256 * 8);
+  y = std::min<int64_t>(y, std::max<int64_t>(1, 152 * 16 / std::max(1, rows)));
+  return dim3(rows, (unsigned)std::max<int64_t>(1, std::min<int64_t>(y, 65535)));
 }
 
 // Quaternion product C = A B for nb problems (parts m x m): C_stack = Lq(A) B_stack.
@@ -279,7 +385,15 @@ x2c_status quat_gemm(x2c_ctx *ctx, cudaStream_t st, int nb, int m, int nc, const
   const int M = nc * m, K = nc * m;
   const int splits = part ? choose_splits<TileSmall>(nb, M, m, K) : 1;
   if (splits > 1) return gemm_f64_splitk<TileSmall>(ctx, st, nb, M, m, K, splits, part, a, b, C, "solve_quat_gemm");
+  if (m >= 512) return gemm_f64<TileLarge>(ctx, st, nb, M, m, a, b, C, UniformDims{M, m, K}, "solve_quat_gemm");
   return gemm_f64<TileSolve>(ctx, st, nb, M, m, a, b, C, UniformDims{M, m, K}, "solve_quat_gemm");
+}
+
+// Square-ish products of the solve: the larger tile once the matrices are large.
+template <class AOp, class BOp, class COp>
+x2c_status gemm_sq(x2c_ctx *ctx, cudaStream_t st, int batch, int n, const AOp &A, const BOp &B, const COp &C) {
+  if (n >= 512) return gemm_f64<TileLarge>(ctx, st, batch, n, n, A, B, C, UniformDims{n, n, n});
+  return gemm_f64<TileSolve>(ctx, st, batch, n, n, A, B, C, UniformDims{n, n, n});
 }
 
 // Size of the split-K partial buffer for quat_gemm on nb problems of part size m.
@@ -293,19 +407,70 @@ inline StoreAxpby store_plain(double *out, int m, int nc) {
   return StoreAxpby{out, nullptr, m, (int64_t)nc * m * m, 1.0, 0.0};
 }
 
+// Blocked Cholesky factor F and inverse X = F^-1 of the n x n matrix A (leading dimension
+// lda; its lower part is overwritten by the trailing updates), by halves:
+//   F11 X11 from A11;  F21 = A21 X11^T;  A22 -= F21 F21^T;  F22 X22 from A22;
+//   X21 = -X22 (F21 X11).
+// F and X (leading dimension ld) must be zero above the diagonal blocks beforehand; tmp
+// holds n^2/4 + 32 n doubles (the largest F21 X11 product).
+x2c_status chol_inv_blocked(x2c_ctx *ctx, cudaStream_t st, double *A, int64_t lda, int n, double *F,
+                            double *X, int64_t ld, double *tmp, int *status) {
+  if (n <= kLeaf) {
+    const size_t smem = (size_t)n * n * sizeof(double);
+    X2C_TRY_CUDA(ctx, cudaFuncSetAttribute(chol_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)(kLeaf * kLeaf * sizeof(double))));
+    tbegin(ctx, st);
+    chol_leaf_kernel<<<1, 256, smem, st>>>(A, lda, n, F, X, ld, status);
+    return launched(ctx, "chol_leaf_kernel", st);
+  }
+  const int n1 = ((n / 2 + 31) / 32) * 32, n2 = n - n1;
+  X2C_TRY(chol_inv_blocked(ctx, st, A, lda, n1, F, X, ld, tmp, status));
+  double *F21 = F + (int64_t)n1 * ld, *X21 = X + (int64_t)n1 * ld;
+  X2C_TRY((gemm_f64<TileLarge>(ctx, st, 1, n2, n1, Mat<false>{A + (int64_t)n1 * lda, lda, 0, 1.0},
+                               Mat<true>{X, ld, 0, 1.0}, StoreAxpby{F21, nullptr, ld, 0, 1.0, 0.0},
+                               UniformDims{n2, n1, n1}, "chol_gemm")));
+  double *A22 = A + (int64_t)n1 * lda + n1;
+  X2C_TRY((gemm_f64<TileLarge>(ctx, st, 1, n2, n2, Mat<false>{F21, ld, 0, 1.0}, Mat<true>{F21, ld, 0, 1.0},
+                               StoreAxpby{A22, A22, lda, 0, -1.0, 1.0}, UniformDims{n2, n2, n1}, "chol_gemm")));
+  X2C_TRY(chol_inv_blocked(ctx, st, A22, lda, n2, F21 + n1, X21 + n1, ld, tmp, status));
+  X2C_TRY((gemm_f64<TileLarge>(ctx, st, 1, n2, n1, Mat<false>{F21, ld, 0, 1.0}, Mat<false>{X, ld, 0, 1.0},
+                               StoreAxpby{tmp, nullptr, n1, 0, 1.0, 0.0}, UniformDims{n2, n1, n1}, "chol_gemm")));
+  return gemm_f64<TileLarge>(ctx, st, 1, n2, n1, Mat<false>{X21 + n1, ld, 0, 1.0}, Mat<false>{tmp, n1, 0, 1.0},
+                             StoreAxpby{X21, nullptr, ld, 0, -1.0, 0.0}, UniformDims{n2, n1, n2}, "chol_gemm");
+}
+
+// ||Y - 1||_max <= tol for every problem and, with Z, |trace Z_0| < 1/2 (equal numbers of
+// positive- and negative-energy states); failures are latched in the status word.
+x2c_status check(x2c_ctx *ctx, cudaStream_t st, int nb, int d, int nc, const double *Y, const double *Z,
+                 double tol, unsigned long long *slot, double *trace, int *status) {
+  X2C_TRY_CUDA(ctx, cudaMemsetAsync(slot, 0, sizeof(unsigned long long) * nb, st));
+  tbegin(ctx, st);
+  deviation_kernel<<<aux_grid(nb, (int64_t)nc * d * d), 256, 0, st>>>(d, nc, Y, slot);
+  X2C_TRY(launched(ctx, "check_kernel", st));
+  if (Z) {
+    tbegin(ctx, st);
+    trace_kernel<<<nb, 256, 0, st>>>(d, nc, Z, trace);
+    X2C_TRY(launched(ctx, "check_kernel", st));
+  }
+  tbegin(ctx, st);
+  check_final_kernel<<<1, 256, 0, st>>>(nb, slot, Z ? trace : nullptr, tol, status);
+  return launched(ctx, "check_kernel", st);
+}
+
 }  // namespace
 
 size_t solve_workspace_bytes(int nb, int n, int nc) {
   const size_t n2 = (size_t)n * n;
   const size_t per = (6 + 23 * (size_t)nc) * n2;
   const size_t part = std::max(quat_part_doubles(nb, 2 * n, nc), quat_part_doubles(nb, n, nc));
-  return arena_doubles(per * nb) + arena_doubles(part) + 16 * 256;
+  const size_t big = n > kMaxSolveN ? arena_doubles(n2) + arena_doubles(n2 / 4 + 32 * (size_t)n) : 0;
+  return arena_doubles(per * nb) + arena_doubles(part) + big + 2 * arena_doubles(nb) + 20 * 256;
 }
 
 x2c_status solve_transforms(x2c_ctx *ctx, cudaStream_t st, double c, int nb, int n, int nc,
                             const InputDesc *d_in, double *UL, double *US, Arena ar) {
   if (nb <= 0) return X2C_OK;
-  if (n < 1 || n > kMaxSolveN) return X2C_ERR_ARG;
+  if (n < 1 || 2 * (int64_t)n * 2 * n > INT32_MAX) return X2C_ERR_ARG;
   const int64_t n2 = (int64_t)n * n;
   const int d = 2 * n;
   const int64_t d2 = (int64_t)d * d;
@@ -317,43 +482,64 @@ x2c_status solve_transforms(x2c_ctx *ctx, cudaStream_t st, double c, int nb, int
   double *Yk = ar.take(nb * nc * n2), *Zk = ar.take(nb * nc * n2), *Tm = ar.take(nb * nc * n2);
   double *Yk2 = ar.take(nb * nc * n2), *Zk2 = ar.take(nb * nc * n2);
   double *XR = ar.take(nb * nc * n2), *tmp2 = ar.take(nb * nc * n2);
-  if (!tmp2) return X2C_ERR_NOMEM;
+  auto *slot = reinterpret_cast<unsigned long long *>(ar.take(nb));
+  double *trace = ar.take(nb);
+  if (!tmp2 || !slot || !trace) return X2C_ERR_NOMEM;
   const size_t part_n = std::max(quat_part_doubles(nb, d, nc), quat_part_doubles(nb, n, nc));
   double *part = part_n ? ar.take(part_n) : nullptr;
   if (part_n && !part) return X2C_ERR_NOMEM;
   int *status = ctx->d_status;
 
   // 1. Cholesky factors and inverses of S and T.
-  const size_t smem = (size_t)n2 * sizeof(double);
-  X2C_TRY_CUDA(ctx, cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  tbegin(ctx, st);
-  chol_inv_kernel<<<2 * nb, 256, smem, st>>>(d_in, n, fac, inv, status);
-  X2C_TRY(launched(ctx, "chol_inv_kernel", st));
+  if (n <= kMaxSolveN) {
+    const size_t smem = (size_t)n2 * sizeof(double);
+    X2C_TRY_CUDA(ctx, cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    tbegin(ctx, st);
+    chol_inv_kernel<<<2 * nb, 256, smem, st>>>(d_in, n, fac, inv, status);
+    X2C_TRY(launched(ctx, "chol_inv_kernel", st));
+  } else {
+    // large matrices: blocked factorisation of a dense copy, one matrix at a time
+    double *Acopy = ar.take(n2), *ctmp = ar.take(n2 / 4 + 32 * n);
+    if (!ctmp) return X2C_ERR_NOMEM;
+    X2C_TRY_CUDA(ctx, cudaMemsetAsync(fac, 0, sizeof(double) * 2 * nb * n2, st));
+    X2C_TRY_CUDA(ctx, cudaMemsetAsync(inv, 0, sizeof(double) * 2 * nb * n2, st));
+    for (int b = 0; b < nb; ++b)
+      for (int which = 0; which < 2; ++which) {
+        tbegin(ctx, st);
+        copy_input_kernel<<<152 * 4, 256, 0, st>>>(d_in, b, which, n, Acopy);
+        X2C_TRY(launched(ctx, "copy_input_kernel", st));
+        X2C_TRY(chol_inv_blocked(ctx, st, Acopy, n, n, fac + (2 * b + which) * n2, inv + (2 * b + which) * n2, n,
+                                 ctmp, status));
+      }
+  }
   // L_S at fac + 2b n2, L_T at fac + (2b+1) n2; inverses likewise in inv.
   const double rt2c = std::sqrt(2.0) * c;
   {
-    UniformDims dims{n, n, n};
     // tmp = L^-1 V ;  Vt = tmp L^-T
-    X2C_TRY((gemm_f64<TileSolve>(ctx, st, nb, n, n, Mat<false>{inv, n, 2 * n2, 1.0},
-                                 InputOp{d_in, 2, 1}, StoreAxpby{tmp, nullptr, n, n2, 1.0, 0.0}, dims)));
-    X2C_TRY((gemm_f64<TileSolve>(ctx, st, nb, n, n, Mat<false>{tmp, n, n2, 1.0},
-                                 Mat<true>{inv, n, 2 * n2, 1.0}, StoreAxpby{Vt, nullptr, n, n2, 1.0, 0.0}, dims)));
+    X2C_TRY((gemm_sq(ctx, st, nb, n, Mat<false>{inv, n, 2 * n2, 1.0},
+                                 InputOp{d_in, 2, 1}, StoreAxpby{tmp, nullptr, n, n2, 1.0, 0.0})));
+    X2C_TRY((gemm_sq(ctx, st, nb, n, Mat<false>{tmp, n, n2, 1.0},
+                                 Mat<true>{inv, n, 2 * n2, 1.0}, StoreAxpby{Vt, nullptr, n, n2, 1.0, 0.0})));
     // LSm = sqrt2 c L^-1 M
-    X2C_TRY((gemm_f64<TileSolve>(ctx, st, nb, n, n, Mat<false>{inv, n, 2 * n2, 1.0},
-                                 Mat<false>{fac + n2, n, 2 * n2, 1.0}, StoreAxpby{LSm, nullptr, n, n2, rt2c, 0.0}, dims)));
+    X2C_TRY((gemm_sq(ctx, st, nb, n, Mat<false>{inv, n, 2 * n2, 1.0},
+                                 Mat<false>{fac + n2, n, 2 * n2, 1.0}, StoreAxpby{LSm, nullptr, n, n2, rt2c, 0.0})));
     // tmp_q = M^-1 W_q ;  Wt_q = (1/2) tmp_q M^-T      (batch over problem x part)
-    X2C_TRY((gemm_f64<TileSolve>(ctx, st, nb * nc, n, n, MatDiv<false>{inv + n2, n, 2 * n2, nc, 1.0},
-                                 InputOp{d_in, 3, nc}, StoreAxpby{tmp, nullptr, n, n2, 1.0, 0.0}, dims)));
-    X2C_TRY((gemm_f64<TileSolve>(ctx, st, nb * nc, n, n, Mat<false>{tmp, n, n2, 1.0},
-                                 MatDiv<true>{inv + n2, n, 2 * n2, nc, 1.0}, StoreAxpby{Wt, nullptr, n, n2, 0.5, 0.0}, dims)));
+    X2C_TRY((gemm_sq(ctx, st, nb * nc, n, MatDiv<false>{inv + n2, n, 2 * n2, nc, 1.0},
+                                 InputOp{d_in, 3, nc}, StoreAxpby{tmp, nullptr, n, n2, 1.0, 0.0})));
+    X2C_TRY((gemm_sq(ctx, st, nb * nc, n, Mat<false>{tmp, n, n2, 1.0},
+                                 MatDiv<true>{inv + n2, n, 2 * n2, nc, 1.0}, StoreAxpby{Wt, nullptr, n, n2, 0.5, 0.0})));
   }
   // 2. Z = H^p + c^2, scaled into [-1, 1].
   tbegin(ctx, st);
-  assemble_hp_kernel<<<nb * nc, 256, 0, st>>>(n, nc, c, Vt, LSm, Wt, Z);
+  assemble_hp_kernel<<<aux_grid(nb * nc, d2), 256, 0, st>>>(n, nc, c, Vt, LSm, Wt, Z);
   X2C_TRY(launched(ctx, "assemble_hp_kernel", st));
+  X2C_TRY_CUDA(ctx, cudaMemsetAsync(slot, 0, sizeof(unsigned long long) * nb, st));
   tbegin(ctx, st);
-  normalise_kernel<<<nb, 256, 0, st>>>(d, nc, Z, status);
-  X2C_TRY(launched(ctx, "normalise_kernel", st));
+  gershgorin_kernel<<<aux_grid(nb, (int64_t)d * 32 * nc), 256, 0, st>>>(d, nc, Z, slot);
+  X2C_TRY(launched(ctx, "gershgorin_kernel", st));
+  tbegin(ctx, st);
+  scale_kernel<<<aux_grid(nb, nc * d2), 256, 0, st>>>(nc * d2, Z, slot, status);
+  X2C_TRY(launched(ctx, "scale_kernel", st));
   // 3. Sign function by the scaled Newton-Schulz schedule.
   const std::vector<double> sched = sign_schedule(kSignLowerBound);
   for (double a : sched) {
@@ -363,16 +549,14 @@ x2c_status solve_transforms(x2c_ctx *ctx, cudaStream_t st, double c, int nb, int
     X2C_TRY(quat_gemm(ctx, st, nb, d, nc, Z, Y, 1.0, upd, part));
     std::swap(Z, Zn);
   }
+  X2C_TRY(check(ctx, st, nb, d, nc, Y, Z, kSignTol, slot, trace, status));
   tbegin(ctx, st);
-  check_kernel<<<nb, 256, 0, st>>>(d, nc, Y, Z, kSignTol, 1, status);
-  X2C_TRY(launched(ctx, "check_kernel", st));
-  tbegin(ctx, st);
-  projector_kernel<<<nb * nc, 256, 0, st>>>(n, nc, Z, PLL, PSL);
+  projector_kernel<<<aux_grid(nb * nc, n2), 256, 0, st>>>(n, nc, Z, PLL, PSL);
   X2C_TRY(launched(ctx, "projector_kernel", st));
   // 4. Coupled Newton-Schulz: Yk -> P_LL^1/2, Zk -> P_LL^-1/2.
   X2C_TRY_CUDA(ctx, cudaMemcpyAsync(Yk, PLL, sizeof(double) * nb * nc * n2, cudaMemcpyDeviceToDevice, st));
   tbegin(ctx, st);
-  identity_kernel<<<nb, 256, 0, st>>>(n, nc, Zk);
+  identity_kernel<<<aux_grid(nb, nc * n2), 256, 0, st>>>(n, nc, Zk);
   X2C_TRY(launched(ctx, "identity_kernel", st));
   for (int it = 0; it < kSqrtIters; ++it) {
     StoreShiftIdentity tm{Tm, n, (int64_t)nc * n2, n, -0.5, 1.5};
@@ -382,22 +566,19 @@ x2c_status solve_transforms(x2c_ctx *ctx, cudaStream_t st, double c, int nb, int
     std::swap(Yk, Yk2);
     std::swap(Zk, Zk2);
   }
-  tbegin(ctx, st);
-  check_kernel<<<nb, 256, 0, st>>>(n, nc, Tm, nullptr, kSqrtTol, 0, status);
-  X2C_TRY(launched(ctx, "check_kernel", st));
+  X2C_TRY(check(ctx, st, nb, n, nc, Tm, nullptr, kSqrtTol, slot, nullptr, status));
   // 5. X'R' = P_SL P_LL^-1/2
   X2C_TRY(quat_gemm(ctx, st, nb, n, nc, PSL, Zk, 1.0, store_plain(XR, n, nc), part));
   // 6. U^L_q = L^-T (R'_q L^T),  U^S_q = sqrt2 c M^-T (X'R'_q L^T)   (batch over problem x part)
   {
-    UniformDims dims{n, n, n};
-    X2C_TRY((gemm_f64<TileSolve>(ctx, st, nb * nc, n, n, Mat<false>{Yk, n, n2, 1.0},
-                                 MatDiv<true>{fac, n, 2 * n2, nc, 1.0}, StoreAxpby{tmp, nullptr, n, n2, 1.0, 0.0}, dims)));
-    X2C_TRY((gemm_f64<TileSolve>(ctx, st, nb * nc, n, n, MatDiv<true>{inv, n, 2 * n2, nc, 1.0},
-                                 Mat<false>{tmp, n, n2, 1.0}, StoreAxpby{UL, nullptr, n, n2, 1.0, 0.0}, dims)));
-    X2C_TRY((gemm_f64<TileSolve>(ctx, st, nb * nc, n, n, Mat<false>{XR, n, n2, 1.0},
-                                 MatDiv<true>{fac, n, 2 * n2, nc, 1.0}, StoreAxpby{tmp2, nullptr, n, n2, 1.0, 0.0}, dims)));
-    X2C_TRY((gemm_f64<TileSolve>(ctx, st, nb * nc, n, n, MatDiv<true>{inv + n2, n, 2 * n2, nc, 1.0},
-                                 Mat<false>{tmp2, n, n2, 1.0}, StoreAxpby{US, nullptr, n, n2, rt2c, 0.0}, dims)));
+    X2C_TRY((gemm_sq(ctx, st, nb * nc, n, Mat<false>{Yk, n, n2, 1.0},
+                                 MatDiv<true>{fac, n, 2 * n2, nc, 1.0}, StoreAxpby{tmp, nullptr, n, n2, 1.0, 0.0})));
+    X2C_TRY((gemm_sq(ctx, st, nb * nc, n, MatDiv<true>{inv, n, 2 * n2, nc, 1.0},
+                                 Mat<false>{tmp, n, n2, 1.0}, StoreAxpby{UL, nullptr, n, n2, 1.0, 0.0})));
+    X2C_TRY((gemm_sq(ctx, st, nb * nc, n, Mat<false>{XR, n, n2, 1.0},
+                                 MatDiv<true>{fac, n, 2 * n2, nc, 1.0}, StoreAxpby{tmp2, nullptr, n, n2, 1.0, 0.0})));
+    X2C_TRY((gemm_sq(ctx, st, nb * nc, n, MatDiv<true>{inv + n2, n, 2 * n2, nc, 1.0},
+                                 Mat<false>{tmp2, n, n2, 1.0}, StoreAxpby{US, nullptr, n, n2, rt2c, 0.0})));
   }
   return X2C_OK;
 }
