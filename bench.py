@@ -36,6 +36,11 @@ METRIC = "X2C h builds/s & FP64-equiv TFLOP/s (Ag309 2c DLU) vs plain FP64; p99 
 # i.e. 2 DFMA per clock per SM; at the 2070 MHz maximum SM clock that is
 # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz = 1.2586 TFLOP/s.  (mma.sync f64 measured 1.046.)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# DRAM bytes (read + write) per two-component 48 x 48 pair block of the split kernels, from
+# one ncu capture of the Ag55 two-component build (1540 pairs, the same per-pair shapes as
+# Ag309); a launch's traffic is this times its pairs.  Set an entry to None when its kernel
+# changes.
+PROFILED_DRAM_BYTES_PER_PAIR = {"split_stage1": 251.6e3, "split_stage2": 310.3e3}
 WORKLOADS = {
     "ag309_2c": dict(L=309, basis="s48", two_c=True),
     # 64 uneven spin-free clusters, n ~ U[2, 43], basis s30/s48 50/50, one batched launch
@@ -486,6 +491,8 @@ def main():
     ap.add_argument("--requests", type=int, default=0, help="serving: requests in the stream (0 = 2000)")
     ap.add_argument("--rate", type=float, default=50.0, help="serving: mean arrivals per second")
     ap.add_argument("--slots", type=int, default=4, help="serving: concurrent builds")
+    ap.add_argument("--serving-requests", type=int, default=500,
+                    help="default workload: requests of the short serving run reported as 'serving' (0 = none)")
     args = ap.parse_args()
     cfg = WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -587,7 +594,11 @@ def main():
                 "fp64_equiv_achieved": dom_flops / (dom_ms * 1e-3) / 1e12,
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained, of measured"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    per_pair = PROFILED_DRAM_BYTES_PER_PAIR.get(dom_name) if two_c and cfg["basis"] == "s48" else None
+    # per launch, like `achieved`: the pairs of all timed launches over their count
+    roof["traffic"] = per_pair * len(pairs) * args.steps / dom_launches if per_pair else None
+    if per_pair:
+        roof["traffic_source"] = "ncu dram__bytes_read+write of the Ag55 2c capture, per pair x pairs per launch"
     roof["launches"] = int(dom_launches)
     roof["avg_launch_ms"] = dom_ms / max(1, dom_launches)
 
@@ -664,6 +675,27 @@ def main():
                                 "sample": f"atomic solve + {n} seeded pair blocks ({secs:.1f} s), "
                                           f"extrapolated to {len(pairs)} pair blocks"}
     ctx.close()
+    if args.serving_requests > 0:
+        # p99 latency of the metric: a shorter run of the serving stream on the same GPU
+        # (the full 2000-request stream is `--workload serving`)
+        del g, out
+        torch.cuda.empty_cache()
+        big, kinds_s = serving_inputs()
+        reqs = w.serving_requests(count=args.serving_requests, rate=args.rate, seed=w.DEFAULT_SEED + rank)
+        srv = x.Server(local, max_inflight=args.slots, max_batch=16, hbm_budget_bytes=150 * 10 ** 9)
+        combos = [(n, b, tc) for n in (147, 24, 5) for b in ("s30", "s48") for tc in (False, True)]
+        serve_stream(srv, [dict(t_arrive=0.002 * i, natoms=n, basis=b, two_component=tc)
+                           for i, (n, b, tc) in enumerate(combos)], big, kinds_s, prec, args.slices)
+        srv.reset_stats()
+        serve_stream(srv, reqs, big, kinds_s, prec, args.slices)
+        st = srv.stats()
+        srv.close()
+        line["serving"] = {"requests": len(reqs), "rate_per_s": args.rate, "p50_ms": st["latency_p50_ms"],
+                           "p99_ms": st["latency_p99_ms"], "max_ms": st["latency_max_ms"],
+                           "builds_per_s": st["builds_per_s"], "completed": st["completed"], "failed": st["failed"],
+                           "precision": args.precision,
+                           "workload": "Ag_n DLU, n log-uniform in [2,147], s30/s48, 30% two-component, "
+                                       "pinned host inputs; latency = completion - scheduled arrival"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -43,6 +43,19 @@ size_t workspace_after_growth(const x2c_ctx *ctx, size_t bytes) {
   return bytes > ctx->ws_bytes ? bytes + bytes / 8 : ctx->ws_bytes;
 }
 
+x2c_status ensure_aux_streams(x2c_ctx *ctx, int count) {
+  if (!ctx->aux_fork) X2C_TRY_CUDA(ctx, cudaEventCreateWithFlags(&ctx->aux_fork, cudaEventDisableTiming));
+  while ((int)ctx->aux.size() < count) {
+    cudaStream_t s;
+    cudaEvent_t e;
+    X2C_TRY_CUDA(ctx, cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    X2C_TRY_CUDA(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    ctx->aux.push_back(s);
+    ctx->aux_join.push_back(e);
+  }
+  return X2C_OK;
+}
+
 bool mats_ok(const x2c_mats *m, int nc) {
   if (!m || m->n < 1 || !m->S || !m->T || !m->V || !m->W0) return false;
   if (nc == 4 && (!m->Wx || !m->Wy || !m->Wz)) return false;
@@ -109,7 +122,7 @@ x2c_status run_plan(x2c_ctx *ctx, const x2c_options *opt, BuildPlan &plan, cudaS
   for (auto &g : groups) {
     const size_t n2 = (size_t)g.first * g.first;
     u_doubles += 2 * g.second.size() * nc * n2;
-    solve_ws = std::max(solve_ws, solve_workspace_bytes((int)g.second.size(), g.first, nc));
+    solve_ws += solve_workspace_bytes((int)g.second.size(), g.first, nc) + 256;  // groups run concurrently
     desc_bytes += ((g.second.size() * sizeof(InputDesc) + 255) / 256) * 256;
   }
   const size_t np = plan.problems.size();
@@ -156,17 +169,39 @@ x2c_status run_plan(x2c_ctx *ctx, const x2c_options *opt, BuildPlan &plan, cudaS
     ddescs.push_back(dd);
     plan.credited += nb * credited_solve_flops(n, nc);
   }
-  // solves share the scratch region that follows (assembly reuses it afterwards)
+  // Size groups are independent: each runs on its own stream (the first on the caller's)
+  // with its own part of the scratch region that follows; the caller's stream then waits
+  // for all of them (the assembly reuses the region afterwards).
   {
+    const int ng = (int)groups.size();
+    std::vector<cudaStream_t> gs(ng, st);
+    if (ng > 1) {
+      X2C_TRY(ensure_aux_streams(ctx, std::min(ng - 1, kMaxAuxStreams)));
+      X2C_TRY_CUDA(ctx, cudaEventRecord(ctx->aux_fork, st));
+      for (int i = 1; i < ng; ++i) {
+        gs[i] = ctx->aux[(i - 1) % kMaxAuxStreams];
+        if (i <= kMaxAuxStreams) X2C_TRY_CUDA(ctx, cudaStreamWaitEvent(gs[i], ctx->aux_fork, 0));
+      }
+    }
     size_t gi = 0, uo = 0;
+    Arena scratch = ar;
     for (auto &g : groups) {
       const int n = g.first, nb = (int)g.second.size();
       const size_t n2 = (size_t)n * n;
       double *UL = Ustore + uo;
       double *US = UL + (size_t)nb * nc * n2;
       uo += 2 * (size_t)nb * nc * n2;
-      Arena scratch = ar;
-      X2C_TRY(solve_transforms(ctx, st, c, nb, n, nc, ddescs[gi++], UL, US, scratch));
+      const size_t need = solve_workspace_bytes(nb, n, nc);
+      Arena mine;
+      mine.base = static_cast<char *>(scratch.take_bytes(need));
+      mine.cap = need;
+      if (!mine.base) return X2C_ERR_NOMEM;
+      X2C_TRY(solve_transforms(ctx, gs[gi], c, nb, n, nc, ddescs[gi], UL, US, mine));
+      ++gi;
+    }
+    for (int i = 1; i < ng && i <= kMaxAuxStreams; ++i) {
+      X2C_TRY_CUDA(ctx, cudaEventRecord(ctx->aux_join[i - 1], ctx->aux[i - 1]));
+      X2C_TRY_CUDA(ctx, cudaStreamWaitEvent(st, ctx->aux_join[i - 1], 0));
     }
   }
   size_t solved = 0;
@@ -472,6 +507,9 @@ x2c_status x2c_ctx_destroy(x2c_ctx *ctx) {
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->stage) cudaFree(ctx->stage);
   for (auto e : ctx->ev_pool) cudaEventDestroy(e);
+  for (auto s : ctx->aux) cudaStreamDestroy(s);
+  for (auto e : ctx->aux_join) cudaEventDestroy(e);
+  if (ctx->aux_fork) cudaEventDestroy(ctx->aux_fork);
   if (ctx->d_status) cudaFree(ctx->d_status);
   delete ctx;
   return X2C_OK;

@@ -47,6 +47,10 @@ struct x2c_ctx {
   // when set, the workspace grows stream-ordered from this pool on the call's stream
   // (no device-wide synchronisation; used by the server, whose slots run concurrently)
   cudaMemPool_t pool = nullptr;
+  // streams on which independent size groups of a batched solve run concurrently
+  std::vector<cudaStream_t> aux;
+  std::vector<cudaEvent_t> aux_join;
+  cudaEvent_t aux_fork = nullptr;
 };
 
 namespace x2c {
@@ -153,6 +157,9 @@ inline size_t arena_doubles(size_t n) { return ((n * sizeof(double) + 255) / 256
 // Grow the context workspace to at least `bytes` (synchronises the device when it grows,
 // unless the context has a pool: then the growth is stream-ordered on `st`).
 x2c_status ensure_workspace(x2c_ctx *ctx, size_t bytes, Arena *out, cudaStream_t st);
+// Auxiliary streams of the context (created on first use, at most kMaxAuxStreams).
+constexpr int kMaxAuxStreams = 4;
+x2c_status ensure_aux_streams(x2c_ctx *ctx, int count);
 // Workspace size the context holds after a call that needs `bytes`.
 size_t workspace_after_growth(const x2c_ctx *ctx, size_t bytes);
 // Grow the staging area of the host-buffer calls (synchronises the device when it grows).

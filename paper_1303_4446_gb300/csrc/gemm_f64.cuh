@@ -245,18 +245,22 @@ inline x2c_status gemm_f64_splitk(x2c_ctx *ctx, cudaStream_t st, int batch, int 
   return launched(ctx, "splitk_reduce", st);
 }
 
-// Split count that gives about two waves of CTAs on 152 SMs.
+// Split count that gives about two waves of CTAs on 152 SMs, with at least `min_chunks`
+// K steps per split.
 template <class Cfg>
-inline int choose_splits(int batch, int m, int n, int k) {
+inline int choose_splits(int batch, int m, int n, int k, int min_chunks = 2) {
   const int tiles = ((m + Cfg::BM - 1) / Cfg::BM) * ((n + Cfg::BN - 1) / Cfg::BN) * batch;
   int s = (2 * 152 + tiles - 1) / tiles;
-  s = std::max(1, std::min(s, k / (2 * Cfg::KC)));
+  s = std::max(1, std::min(s, k / (min_chunks * Cfg::KC)));
   return s;
 }
 
 // Default tile for the dense (square-ish) products of the decoupling solve.
 using TileSolve = TileCfg<64, 64, 16, 4, 4>;
 using TileSmall = TileCfg<32, 32, 16, 2, 2>;
+// Tiny products (the decoupling solve of one small atom kind): one output per thread, so
+// that a 60 x 60 product still spreads over dozens of CTAs.
+using TileTiny = TileCfg<16, 16, 16, 1, 1>;
 // Large dense products (full X2C of a whole molecule): 96 x 64 tiles, 24 accumulators.
 using TileLarge = TileCfg<96, 64, 16, 6, 4>;
 

@@ -375,6 +375,23 @@ dim3 aux_grid(int rows, int64_t elems) {
   return dim3(rows, (unsigned)std::max<int64_t>(1, std::min<int64_t>(y, 65535)));
 }
 
+// Tile and split-K choice of the solve's products: products of a few million FMAs (one small
+// atom kind) are latency-bound and get the smallest tile split along K down to single K
+// steps; larger ones the 32 x 32 tile with split-K or the 64 x 64 / 96 x 64 tiles.
+enum class SolveTile { Tiny, Small, Mid, Large };
+struct SolvePlan {
+  SolveTile tile;
+  int splits;
+};
+constexpr double kTinyWork = 4.0 * 1024 * 1024;  // FMAs of one launch
+SolvePlan plan_product(int nb, int M, int m, int K, bool can_split) {
+  if ((double)nb * M * m * K <= kTinyWork)
+    return {SolveTile::Tiny, can_split ? choose_splits<TileTiny>(nb, M, m, K, 1) : 1};
+  if (m >= 512) return {SolveTile::Large, 1};
+  const int s = can_split ? choose_splits<TileSmall>(nb, M, m, K) : 1;
+  return {s > 1 ? SolveTile::Small : SolveTile::Mid, s};
+}
+
 // Quaternion product C = A B for nb problems (parts m x m): C_stack = Lq(A) B_stack.
 // Small problems are split along K into a partial buffer (`part`, see quat_part_doubles).
 template <class COp>
@@ -383,24 +400,35 @@ x2c_status quat_gemm(x2c_ctx *ctx, cudaStream_t st, int nb, int m, int nc, const
   QuatLeft<false> a{A, m, (int64_t)nc * m * m, (int64_t)m * m, m, nc, scale};
   Mat<false> b{B, m, (int64_t)nc * m * m, 1.0};
   const int M = nc * m, K = nc * m;
-  const int splits = part ? choose_splits<TileSmall>(nb, M, m, K) : 1;
-  if (splits > 1) return gemm_f64_splitk<TileSmall>(ctx, st, nb, M, m, K, splits, part, a, b, C, "solve_quat_gemm");
-  if (m >= 512) return gemm_f64<TileLarge>(ctx, st, nb, M, m, a, b, C, UniformDims{M, m, K}, "solve_quat_gemm");
-  return gemm_f64<TileSolve>(ctx, st, nb, M, m, a, b, C, UniformDims{M, m, K}, "solve_quat_gemm");
+  const SolvePlan p = plan_product(nb, M, m, K, part != nullptr);
+  const char *name = "solve_quat_gemm";
+  switch (p.tile) {
+    case SolveTile::Tiny:
+      if (p.splits > 1) return gemm_f64_splitk<TileTiny>(ctx, st, nb, M, m, K, p.splits, part, a, b, C, name);
+      return gemm_f64<TileTiny>(ctx, st, nb, M, m, a, b, C, UniformDims{M, m, K}, name);
+    case SolveTile::Small:
+      return gemm_f64_splitk<TileSmall>(ctx, st, nb, M, m, K, p.splits, part, a, b, C, name);
+    case SolveTile::Large:
+      return gemm_f64<TileLarge>(ctx, st, nb, M, m, a, b, C, UniformDims{M, m, K}, name);
+    default:
+      return gemm_f64<TileSolve>(ctx, st, nb, M, m, a, b, C, UniformDims{M, m, K}, name);
+  }
 }
 
-// Square-ish products of the solve: the larger tile once the matrices are large.
+// Square-ish products of the solve (no split-K): tile by size.
 template <class AOp, class BOp, class COp>
 x2c_status gemm_sq(x2c_ctx *ctx, cudaStream_t st, int batch, int n, const AOp &A, const BOp &B, const COp &C) {
-  if (n >= 512) return gemm_f64<TileLarge>(ctx, st, batch, n, n, A, B, C, UniformDims{n, n, n});
+  const SolvePlan p = plan_product(batch, n, n, n, false);
+  if (p.tile == SolveTile::Tiny) return gemm_f64<TileTiny>(ctx, st, batch, n, n, A, B, C, UniformDims{n, n, n});
+  if (p.tile == SolveTile::Large) return gemm_f64<TileLarge>(ctx, st, batch, n, n, A, B, C, UniformDims{n, n, n});
   return gemm_f64<TileSolve>(ctx, st, batch, n, n, A, B, C, UniformDims{n, n, n});
 }
 
 // Size of the split-K partial buffer for quat_gemm on nb problems of part size m.
 size_t quat_part_doubles(int nb, int m, int nc) {
   const int M = nc * m, K = nc * m;
-  const int splits = choose_splits<TileSmall>(nb, M, m, K);
-  return splits > 1 ? (size_t)(splits + 1) * nb * M * m : 0;
+  const SolvePlan p = plan_product(nb, M, m, K, true);
+  return p.splits > 1 ? (size_t)(p.splits + 1) * nb * M * m : 0;
 }
 
 inline StoreAxpby store_plain(double *out, int m, int nc) {
