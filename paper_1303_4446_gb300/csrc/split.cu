@@ -55,11 +55,8 @@ __device__ __forceinline__ __nv_bfloat16 int_to_bf16(int d) {
   return __ushort_as_bfloat16(static_cast<unsigned short>(__float_as_uint(static_cast<float>(d)) >> 16));
 }
 
-__device__ __forceinline__ int warp_max(int v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
+// Maximum over the warp (one redux.sync instruction).
+__device__ __forceinline__ int warp_max(int v) { return __reduce_max_sync(0xffffffffu, v); }
 
 // ------------------------------------------------------------------ slicers
 // Class description: pairs share nA, nB and the transforms U_A, U_B.
@@ -347,11 +344,30 @@ struct Stage2Store {
         const int il = (c0 >> 2) + g;  // i' slot within the tile
         const int ip = nt * IT + il;
         const bool colv = ip < nA;
+        // t[l] = sign+(l, pq) I[4g + (l xor pq)]: the xor permutation as two conditional
+        // swaps, so that I stays in registers (no dynamically indexed local array)
         long long t[4];
-#pragma unroll
-        for (int l = 0; l < 4; ++l) {
-          const long long v = (valid && colv) ? I[4 * g + (l ^ pq)] : 0;
-          t[l] = quat_sign_adj(l, pq) < 0 ? -v : v;
+        {
+          long long u0 = I[4 * g], u1 = I[4 * g + 1], u2 = I[4 * g + 2], u3 = I[4 * g + 3];
+          if (pq & 1) {
+            const long long a = u0, b = u2;
+            u0 = u1;
+            u1 = a;
+            u2 = u3;
+            u3 = b;
+          }
+          if (pq & 2) {
+            const long long a = u0, b = u1;
+            u0 = u2;
+            u1 = u3;
+            u2 = a;
+            u3 = b;
+          }
+          const bool ok = valid && colv;
+          t[0] = ok ? (quat_sign_adj(0, pq) < 0 ? -u0 : u0) : 0;
+          t[1] = ok ? (quat_sign_adj(1, pq) < 0 ? -u1 : u1) : 0;
+          t[2] = ok ? (quat_sign_adj(2, pq) < 0 ? -u2 : u2) : 0;
+          t[3] = ok ? (quat_sign_adj(3, pq) < 0 ? -u3 : u3) : 0;
         }
         // reduce-scatter over the quad: lane with pq = l ends up with sum_p t[l]
         const int b0 = pq & 1, b1 = (pq >> 1) & 1;
@@ -538,17 +554,18 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       for (int j = 0; j < CW; ++j) I[j] = 0;
 #pragma unroll
       for (int g = 0; g < S; ++g) {
+        // all of this warp's columns of accumulator g in flight at once, then one wait
+        uint32_t v[CW];
 #pragma unroll
-        for (int c = 0; c < CW; c += 8) {
-          uint32_t v[8];
+        for (int c = 0; c < CW; c += 8)
           asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                       : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                       : "=r"(v[c]), "=r"(v[c + 1]), "=r"(v[c + 2]), "=r"(v[c + 3]), "=r"(v[c + 4]), "=r"(v[c + 5]),
+                         "=r"(v[c + 6]), "=r"(v[c + 7])
                        : "r"(lane_addr + static_cast<uint32_t>(g * NT + sub * CW + c))
                        : "memory");
-          umma::tmem_ld_wait();
+        umma::tmem_ld_wait();
 #pragma unroll
-          for (int j = 0; j < 8; ++j) I[c + j] = I[c + j] * 256 + __float2int_rn(__uint_as_float(v[j]));
-        }
+        for (int j = 0; j < CW; ++j) I[j] = I[j] * 256 + __float2int_rn(__uint_as_float(v[j]));
       }
       umma::fence_before_sync();
       __syncwarp();
