@@ -40,7 +40,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # one ncu capture of the Ag55 two-component build (1540 pairs, the same per-pair shapes as
 # Ag309); a launch's traffic is this times its pairs.  Set an entry to None when its kernel
 # changes.
-PROFILED_DRAM_BYTES_PER_PAIR = {"split_stage1": 251.6e3, "split_stage2": 310.3e3}
+PROFILED_DRAM_BYTES_PER_PAIR = {"split_stage1": 242.6e3, "split_stage2": 300.4e3}  # with the 96-column N tile
 WORKLOADS = {
     "ag309_2c": dict(L=309, basis="s48", two_c=True),
     # 64 uneven spin-free clusters, n ~ U[2, 43], basis s30/s48 50/50, one batched launch
@@ -52,6 +52,13 @@ WORKLOADS = {
     "ag55_2c": dict(L=55, basis="s48", two_c=True),
     "ag55_sf": dict(L=55, basis="s48", two_c=False),
     "ag4_sf": dict(L=4, basis="s30", two_c=False),
+    # DLU with the paper-literal atomic potential (molecular diagonal blocks): one decoupling
+    # solve per atom, batched over all 309 atoms
+    "ag309_2c_mb": dict(L=309, basis="s48", two_c=True, mb=True),
+    # full X2C of the whole cluster (blocked factorisation, Newton-Schulz sign function)
+    "ag55_sf_full": dict(L=55, basis="s48", two_c=False, full=True),
+    "ag55_2c_full": dict(L=55, basis="s48", two_c=True, full=True),
+    "ag13_2c_full": dict(L=13, basis="s48", two_c=True, full=True),
 }
 
 
@@ -139,14 +146,15 @@ def make_inputs(cfg, seed=w.DEFAULT_SEED):
     return mol, m, kind
 
 
-def cpu_oracle_rate(mol, m, kind, two_c, budget_s, seed=1):
-    """Oracle builds/s from the atomic solve plus a timed seeded sample of pair blocks,
-    extrapolated to all pair blocks.  Returns (builds/s, n_sampled_pairs, seconds)."""
+def cpu_oracle_rate(mol, m, kind, two_c, budget_s, seed=1, solves=1):
+    """Oracle builds/s from the atomic solve (times `solves` per build) plus a timed seeded
+    sample of pair blocks, extrapolated to all pair blocks.  Returns (builds/s,
+    n_sampled_pairs, seconds)."""
     import oracle
 
     t0 = time.perf_counter()
     r = oracle.x2c_full(kind)
-    t_atom = time.perf_counter() - t0
+    t_atom = (time.perf_counter() - t0) * solves
     UL, US = r["UL"], r["US"]
     pairs = pair_list(mol.natoms)
     rng = np.random.default_rng(seed)
@@ -329,6 +337,31 @@ def run_batched(args, cfg):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(value, dist=None, device="cpu"):
+    """The maximum of a per-rank value over all ranks (each step is timed on every rank and
+    the slowest rank counts); the value itself on one process."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, seconds_per_step):
+    """Whole-job builds/s: every rank completes one independent build per step."""
+    return world / seconds_per_step
+
+
+def pct(v, p):
+    """Nearest-rank percentile (None for no samples)."""
+    if not v:
+        return None
+    v = sorted(v)
+    k = max(0, min(len(v) - 1, int(np.ceil(p / 100.0 * len(v))) - 1))
+    return v[k]
+
+
 def serving_inputs(seed=w.DEFAULT_SEED):
     """Pinned host matrices of Ag147 per basis (two-component set; spin-free requests use S,
     T, V, W0) and the free-atom kinds, host and device."""
@@ -352,7 +385,7 @@ def serve_stream(srv, reqs, big, kinds, precision, n_slices, t_lead=0.05):
     keys = {(b, tc): 1 + 2 * ("s30", "s48").index(b) + int(tc) for b in ("s30", "s48") for tc in (False, True)}
     pending = []
     lock = threading.Condition()
-    done = {"n": 0, "failed": 0}
+    done = {"n": 0, "failed": 0, "wait_ms": [], "service_ms": []}
     h2d = [0]
 
     def reaper():
@@ -367,6 +400,9 @@ def serve_stream(srv, reqs, big, kinds, precision, n_slices, t_lead=0.05):
             r = srv.wait(t, timeout_ms=600000)
             if r["status"] != 0:
                 done["failed"] += 1
+            else:
+                done["wait_ms"].append((r["t_start"] - r["t_arrival"]) * 1e3)
+                done["service_ms"].append((r["t_end"] - r["t_start"]) * 1e3)
             srv.release(t)
             done["n"] += 1
 
@@ -398,6 +434,73 @@ def serve_stream(srv, reqs, big, kinds, precision, n_slices, t_lead=0.05):
         lock.notify()
     th.join()
     return done, h2d[0]
+
+
+def run_full(args, cfg):
+    """Full X2C of a whole cluster (x2c_build_full), with the oracle's full build timed beside it."""
+    import torch
+    import paper_1303_4446_gb300 as x
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    t_gen = time.perf_counter()
+    mol = w.silver_cluster(cfg["L"], cfg["basis"])
+    two_c = cfg["two_c"]
+    m = w.molecule_inputs(mol, two_c)
+    t_gen = time.perf_counter() - t_gen
+    g = {k: torch.from_numpy(v).to(dev) for k, v in m.items()}
+    ctx = x.Context(local)
+    stream = torch.cuda.current_stream(dev)
+    warm, steps = max(1, args.warmup), max(1, args.steps)
+    for _ in range(warm):
+        out = x.x2c_build_full(ctx, g, two_component=two_c, stream=stream)
+    ctx.status(stream)
+    counters = ctx.counters()
+    ctx.set_timing(True)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(steps):
+            out = x.x2c_build_full(ctx, g, two_component=two_c, stream=stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ctx.status(stream)
+    ms = ev0.elapsed_time(ev1) / steps
+    kt = ctx.kernel_times(with_flops=True)
+    ctx.set_timing(False)
+    dom_name, (dom_ms, dom_l, dom_fl) = max(kt.items(), key=lambda kv: kv[1][0])
+    roof = {"bound": "alu", "achieved": dom_fl / (dom_ms * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "kernel": dom_name, "frac": dom_fl / (dom_ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS, "traffic": None,
+            "launches": int(dom_l), "peak_source": "152 SMs x 2 DFMA/clk x 2.07 GHz",
+            "flops": "2 m n k per real product the kernel computes (upper triangles of Hermitian products)"}
+    line = {"metric": METRIC, "value": world * 1e3 / ms, "unit": "builds/s", "n_gpus": world, "steps": steps,
+            "warmup": warm, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"full X2C of Ag{cfg['L']} {'two-component' if two_c else 'spin-free'}, "
+                                   f"{cfg['basis']} primitives per atom, N={mol.nbf}",
+                       "inputs": "resident", "parallelism": f"independent replicas x{world}"},
+            "fp64_equiv_tflops": world * counters["credited_flops"] / (ms * 1e-3) / 1e12,
+            "credited_flops_per_build": counters["credited_flops"],
+            "gpu_launches": int(counters["kernel_launches"]) * steps, "roofline": roof, "clocks": clk.summary(),
+            "kernel_ms_per_step": {k: v[0] / steps for k, v in sorted(kt.items(), key=lambda kv: -kv[1][0])[:10]},
+            "input_generation_s": t_gen}
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        t0 = time.perf_counter()
+        r = oracle.x2c_full(m)
+        dt = time.perf_counter() - t0
+        ref = list(oracle.quaternion_parts(r["h"])) if two_c else [r["h"]]
+        err = max(float(np.abs(a.cpu().numpy() - b).max()) for a, b in zip(out["h"], ref)) / float(np.abs(r["h"]).max())
+        line["cpu_baseline"] = {"value": 1.0 / dt, "unit": "builds/s", "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": f"one whole oracle build ({dt:.1f} s)"}
+        line["max_abs_err_rel_to_max_h"] = err
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 def run_serving(args, cfg):
@@ -442,7 +545,11 @@ def run_serving(args, cfg):
                         "completed": n_ok, "failed": st["failed"], "builds_launched": st["builds_launched"],
                         "cache_hits": st["cache_hits"], "cache_misses": st["cache_misses"],
                         "peak_bytes": st["peak_bytes"], "max_concurrent": st["max_concurrent"],
-                        "latency": "completion (device event) - scheduled arrival"},
+                        "latency": "completion (device event) - scheduled arrival",
+                        "wait_p50_ms": pct(done["wait_ms"], 50), "wait_p99_ms": pct(done["wait_ms"], 99),
+                        "service_p50_ms": pct(done["service_ms"], 50), "service_p99_ms": pct(done["service_ms"], 99),
+                        "split": "wait = device start - scheduled arrival (submission, admission, queueing); "
+                                 "service = device start to completion (input copies + build)"},
             "gpu_launches": int(st["kernel_launches"]), "roofline": None,
             "roofline_note": "latency-bound request stream; kernel rooflines are on the Ag309 line",
             "clocks": clk.summary(), "input_generation_s": t_gen,
@@ -501,6 +608,12 @@ def main():
         return run_batched(args, cfg)
     if cfg.get("serving"):
         return run_serving(args, cfg)
+    if cfg.get("full"):
+        return run_full(args, cfg)
+    if cfg.get("mb"):
+        # one transform per atom: the split assembly shares operands per atom kind, so the
+        # molecular-block mode runs on the FP64 path
+        args.precision, args.fp64_steps = "fp64", 0
 
     import torch
     import paper_1303_4446_gb300 as x
@@ -532,9 +645,10 @@ def main():
     prec = x.PREC_SPLIT_BF16 if args.precision == "split" else x.PREC_FP64
     stream = torch.cuda.current_stream(dev)
     kinds = [0] * mol.natoms
+    dlu_pot = x.DLU_MOLECULAR_BLOCK if cfg.get("mb") else x.DLU_FREE_ATOM
 
     def build():
-        x.x2c_build_dlu(ctx, g, mol.offsets, kinds, [gk], two_component=two_c, precision=prec,
+        x.x2c_build_dlu(ctx, g, mol.offsets, kinds, [gk], two_component=two_c, precision=prec, dlu_potential=dlu_pot,
                         n_slices=args.slices, out=out, stream=stream)
 
     for _ in range(args.warmup):
@@ -554,17 +668,14 @@ def main():
     barrier()
     ctx.status(stream)
     ms = ev0.elapsed_time(ev1) / args.steps
-    ktimes = ctx.kernel_times()
+    ktimes = ctx.kernel_times(with_flops=True)
     ctx.set_timing(False)
-    ms_t = torch.tensor([ms], device=dev)
-    if dist is not None:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
+    ms_max = max_over_ranks(ms, dist, dev)
     clocks = clk.summary()
     credited = counters["credited_flops"]
     # roofline of the dominant kernel (largest total time in the timed region)
     dom = max(ktimes.items(), key=lambda kv: kv[1][0])
-    dom_name, (dom_ms, dom_launches) = dom
+    dom_name, (dom_ms, dom_launches, dom_lib_flops) = dom
     pairs = pair_list(mol.natoms)
     sizes = np.diff(mol.offsets)
     dom_flops = sum(kernel_flops(dom_name, sizes[a], sizes[b], nc, a == b) for a, b in pairs) * args.steps
@@ -581,8 +692,11 @@ def main():
         hbm = peaks.get("hbm_gbs", 6684.8)
         roof = {"bound": "hbm", "achieved": byt / (dom_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
                 "kernel": dom_name, "peak_source": "MEASURED_PEAKS.json hbm_gbs, of measured"}
-    elif dom_name.startswith("dlu_") and args.precision == "fp64":
-        roof = {"bound": "alu", "achieved": dom_flops / (dom_ms * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS,
+    elif args.precision == "fp64" or not dom_name.startswith("split_"):
+        # FP64 kernels: the pair-assembly flop model, or the flops the library counts for
+        # each FP64 GEMM launch (the decoupling solves)
+        fl = dom_flops if dom_flops > 0 else dom_lib_flops
+        roof = {"bound": "alu", "achieved": fl / (dom_ms * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "kernel": dom_name,
                 "peak_source": "152 SMs x 2 DFMA/clk (measured by peak_probe.cu) x 2.07 GHz max clock"}
     else:
@@ -594,7 +708,8 @@ def main():
                 "fp64_equiv_achieved": dom_flops / (dom_ms * 1e-3) / 1e12,
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained, of measured"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    per_pair = PROFILED_DRAM_BYTES_PER_PAIR.get(dom_name) if two_c and cfg["basis"] == "s48" else None
+    nt96 = any("-> NT 96" in l for l in ctx.tuning_log().splitlines())
+    per_pair = PROFILED_DRAM_BYTES_PER_PAIR.get(dom_name) if two_c and cfg["basis"] == "s48" and nt96 else None
     # per launch, like `achieved`: the pairs of all timed launches over their count
     roof["traffic"] = per_pair * len(pairs) * args.steps / dom_launches if per_pair else None
     if per_pair:
@@ -602,12 +717,13 @@ def main():
     roof["launches"] = int(dom_launches)
     roof["avg_launch_ms"] = dom_ms / max(1, dom_launches)
 
-    line = {"metric": METRIC, "value": world * 1e3 / ms_max, "unit": "builds/s", "n_gpus": world,
+    line = {"metric": METRIC, "value": job_rate(world, ms_max * 1e-3), "unit": "builds/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "bf16x-split",
             "data": "synthetic",
             "config": {"workload": f"Ag{cfg['L']} {'two-component' if two_c else 'spin-free'} DLU "
-                                   f"(free-atom U per kind), {cfg['basis']} primitives per atom, N={N}",
+                                   f"({'molecular-block U per atom' if cfg.get('mb') else 'free-atom U per kind'}), "
+                                   f"{cfg['basis']} primitives per atom, N={N}",
                        "pairs": len(pairs), "precision": args.precision, "inputs": "larger than L2 (no flush)",
                        "parallelism": f"independent replicas x{world}"},
             "fp64_equiv_tflops": world * credited / (ms_max * 1e-3) / 1e12,
@@ -615,6 +731,7 @@ def main():
             "gpu_launches": int(counters["kernel_launches"]) * args.steps,
             "roofline": roof, "clocks": clocks,
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in sorted(ktimes.items(), key=lambda kv: -kv[1][0])},
+            "autotune": ctx.tuning_log().strip().splitlines(),
             "input_generation_s": t_gen}
 
     if args.precision == "split" and args.fp64_steps > 0:
@@ -624,7 +741,7 @@ def main():
         prec64 = x.PREC_FP64
 
         def build64():
-            x.x2c_build_dlu(ctx, g, mol.offsets, kinds, [gk], two_component=two_c, precision=prec64,
+            x.x2c_build_dlu(ctx, g, mol.offsets, kinds, [gk], two_component=two_c, precision=prec64, dlu_potential=dlu_pot,
                             out=out, stream=stream)
 
         build64()
@@ -652,7 +769,8 @@ def main():
         pin = {k: torch.from_numpy(v).pin_memory() for k, v in m.items()}
         pink = {k: torch.from_numpy(v).pin_memory() for k, v in kind.items()}
         hout = [torch.empty((N, N), dtype=torch.float64).pin_memory() for _ in range(nc)]
-        e2e_args = dict(two_component=two_c, precision=prec, n_slices=args.slices, out=hout, stream=stream)
+        e2e_args = dict(two_component=two_c, precision=prec, n_slices=args.slices, out=hout, stream=stream,
+                        dlu_potential=dlu_pot)
         x.x2c_build_dlu_host(ctx, pin, mol.offsets, kinds, [pink], **e2e_args)
         torch.cuda.synchronize()
         barrier()
@@ -660,17 +778,15 @@ def main():
         for _ in range(args.e2e_steps):
             x.x2c_build_dlu_host(ctx, pin, mol.offsets, kinds, [pink], **e2e_args)
         t_e2e = (time.perf_counter() - t0) / args.e2e_steps
-        t_t = torch.tensor([t_e2e], device=dev)
-        if dist is not None:
-            dist.all_reduce(t_t, op=dist.ReduceOp.MAX)
+        t_e2e_max = max_over_ranks(t_e2e, dist, dev)
         sz = np.diff(mol.offsets)
         h2d = 8 * (3 * N * N + (3 * int((sz * sz).sum()) if two_c else 0) + (3 + (4 if two_c else 1)) * len(kind["S"]) ** 2)
-        line["e2e"] = {"value": world / float(t_t.item()), "unit": "builds/s", "h2d_bytes_per_step": int(h2d),
+        line["e2e"] = {"value": job_rate(world, t_e2e_max), "unit": "builds/s", "h2d_bytes_per_step": int(h2d),
                        "d2h_bytes_per_step": int(8 * nc * N * N), "steps": args.e2e_steps}
         del pin, hout
 
     if rank == 0 and not args.no_cpu_baseline:
-        v, n, secs = cpu_oracle_rate(mol, m, kind, two_c, args.cpu_budget)
+        v, n, secs = cpu_oracle_rate(mol, m, kind, two_c, args.cpu_budget, solves=mol.natoms if cfg.get("mb") else 1)
         line["cpu_baseline"] = {"value": v, "unit": "builds/s", "cores": os.cpu_count(), "kind": "oracle",
                                 "sample": f"atomic solve + {n} seeded pair blocks ({secs:.1f} s), "
                                           f"extrapolated to {len(pairs)} pair blocks"}
@@ -687,11 +803,12 @@ def main():
         serve_stream(srv, [dict(t_arrive=0.002 * i, natoms=n, basis=b, two_component=tc)
                            for i, (n, b, tc) in enumerate(combos)], big, kinds_s, prec, args.slices)
         srv.reset_stats()
-        serve_stream(srv, reqs, big, kinds_s, prec, args.slices)
+        done_s, _ = serve_stream(srv, reqs, big, kinds_s, prec, args.slices)
         st = srv.stats()
         srv.close()
         line["serving"] = {"requests": len(reqs), "rate_per_s": args.rate, "p50_ms": st["latency_p50_ms"],
                            "p99_ms": st["latency_p99_ms"], "max_ms": st["latency_max_ms"],
+                           "service_p99_ms": pct(done_s["service_ms"], 99), "wait_p99_ms": pct(done_s["wait_ms"], 99),
                            "builds_per_s": st["builds_per_s"], "completed": st["completed"], "failed": st["failed"],
                            "precision": args.precision,
                            "workload": "Ag_n DLU, n log-uniform in [2,147], s30/s48, 30% two-component, "

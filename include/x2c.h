@@ -216,6 +216,16 @@ x2c_status x2c_ctx_counters(x2c_ctx *ctx, x2c_counters *out);
  * be NULL.  At most max_entries entries are written and *n_entries receives the number
  * written. */
 x2c_status x2c_ctx_set_timing(x2c_ctx *ctx, int32_t enable);
+
+/* Autotuner (on by default): the first split-precision build of a workload shape (slices,
+ * spin, atom sizes, order of magnitude of the pair count) on a context runs every candidate
+ * N tile of the tensor-core kernels twice (a warm pass, then one timed with CUDA events on
+ * the call's stream; that call synchronises the stream) and keeps the fastest for later
+ * builds of the same shape.  All
+ * candidates give bit-identical h.  x2c_ctx_tuning_log() returns one line per decision
+ * (candidates with their times, and the choice); valid until the next call on the context. */
+x2c_status x2c_ctx_set_autotune(x2c_ctx *ctx, int32_t enable);
+const char *x2c_ctx_tuning_log(x2c_ctx *ctx);
 x2c_status x2c_ctx_kernel_times(x2c_ctx *ctx, int32_t max_entries, char *names, double *ms,
                                 int64_t *launches, double *flops, int32_t *n_entries);
 

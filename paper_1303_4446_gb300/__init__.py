@@ -50,6 +50,14 @@ class Context:
         """x2c_ctx_set_timing: bracket every kernel launch with CUDA events (clears totals)."""
         abi.check(self.lib.x2c_ctx_set_timing(self.handle, int(bool(enable))), "x2c_ctx_set_timing")
 
+    def set_autotune(self, enable: bool):
+        """x2c_ctx_set_autotune: time the candidate tensor-core tiles once per workload shape."""
+        abi.check(self.lib.x2c_ctx_set_autotune(self.handle, int(bool(enable))), "x2c_ctx_set_autotune")
+
+    def tuning_log(self) -> str:
+        """x2c_ctx_tuning_log: the autotuner's decisions, one line each."""
+        return self.lib.x2c_ctx_tuning_log(self.handle).decode()
+
     def kernel_times(self, max_entries: int = 64, with_flops: bool = False):
         """x2c_ctx_kernel_times: {kernel name: (total ms, launches)} since timing was enabled,
         or (total ms, launches, algorithmic flops) with with_flops=True."""

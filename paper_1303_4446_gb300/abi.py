@@ -110,6 +110,8 @@ _SIGS = {
                                                ctypes.c_void_p]),
     "x2c_ctx_counters": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Counters)]),
     "x2c_ctx_set_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "x2c_ctx_set_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "x2c_ctx_tuning_log": (ctypes.c_char_p, [ctypes.c_void_p]),
     "x2c_ctx_kernel_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_char_p,
                                             ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
                                             ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]),

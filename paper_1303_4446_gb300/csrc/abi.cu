@@ -507,6 +507,8 @@ x2c_status x2c_ctx_destroy(x2c_ctx *ctx) {
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->stage) cudaFree(ctx->stage);
   for (auto e : ctx->ev_pool) cudaEventDestroy(e);
+  for (auto e : ctx->tune_ev)
+    if (e) cudaEventDestroy(e);
   for (auto s : ctx->aux) cudaStreamDestroy(s);
   for (auto e : ctx->aux_join) cudaEventDestroy(e);
   if (ctx->aux_fork) cudaEventDestroy(ctx->aux_fork);
@@ -544,6 +546,14 @@ x2c_status x2c_ctx_set_timing(x2c_ctx *ctx, int32_t enable) {
   ctx->kernel_ms.clear();
   return X2C_OK;
 }
+
+x2c_status x2c_ctx_set_autotune(x2c_ctx *ctx, int32_t enable) {
+  if (!ctx || (enable != 0 && enable != 1)) return X2C_ERR_ARG;
+  ctx->autotune = enable != 0;
+  return X2C_OK;
+}
+
+const char *x2c_ctx_tuning_log(x2c_ctx *ctx) { return ctx ? ctx->tune_log.c_str() : ""; }
 
 x2c_status x2c_ctx_kernel_times(x2c_ctx *ctx, int32_t max_entries, char *names, double *ms,
                                 int64_t *launches, double *flops, int32_t *n_entries) {

@@ -51,6 +51,11 @@ struct x2c_ctx {
   std::vector<cudaStream_t> aux;
   std::vector<cudaEvent_t> aux_join;
   cudaEvent_t aux_fork = nullptr;
+  // autotuner: tile choice per workload shape, chosen by timing the candidates once
+  bool autotune = true;
+  std::map<uint64_t, int> tuned;
+  std::string tune_log;
+  cudaEvent_t tune_ev[2] = {nullptr, nullptr};
 };
 
 namespace x2c {

@@ -31,6 +31,24 @@ struct UniformDims {
   __device__ int K0(int) const { return 0; }
 };
 
+// Shape of a product whose result is Hermitian in the quaternion sense (stacked parts of
+// `part` rows; part 0 symmetric, parts 1-3 antisymmetric): tiles strictly below the diagonal
+// of their part are skipped and the epilogue writes the mirror.
+struct HermDims {
+  int m, n, k, part;
+  __device__ int M(int) const { return m; }
+  __device__ int N(int) const { return n; }
+  __device__ int K(int) const { return k; }
+  __device__ int K0(int) const { return 0; }
+};
+template <class Dims>
+__device__ __forceinline__ bool tile_skip(const Dims &, int, int, int, int) { return false; }
+__device__ __forceinline__ bool tile_skip(const HermDims &d, int m0, int n0, int BM, int BN) {
+  const int p = m0 / d.part;
+  if (m0 + BM - 1 >= (p + 1) * d.part) return false;  // the tile spans two parts
+  return m0 - p * d.part > n0 + BN - 1;
+}
+
 // A plain strided matrix operand: element (r, k) (or (k, n) for B) of batch b.
 //   trans = false: p[b*bs + r*ld + k];  trans = true: p[b*bs + k*ld + r]
 template <bool TRANS>
@@ -96,6 +114,39 @@ struct StoreShiftIdentity {
   }
 };
 
+// Hermitian-product epilogues: write element (i, c) of part p for i <= c and its mirror
+// (c, i) = +-value (part 0 symmetric, parts 1-3 antisymmetric); i > c is left to the mirror.
+struct StoreAxpbyHerm {
+  double *out;
+  const double *cin;
+  int64_t ld, bs;
+  double alpha, beta;
+  int m;
+  __device__ __forceinline__ void operator()(int b, int r, int c, double acc) const {
+    const int p = r / m, i = r - p * m;
+    if (i > c) return;
+    const int64_t o = b * bs + (int64_t)r * ld + c;
+    double v = alpha * acc;
+    if (cin) v += beta * cin[o];
+    out[o] = v;
+    if (i < c) out[b * bs + (int64_t)(p * m + c) * ld + i] = p == 0 ? v : -v;
+  }
+};
+struct StoreShiftIdentityHerm {
+  double *out;
+  int64_t ld, bs;
+  int m;
+  double alpha, shift;
+  __device__ __forceinline__ void operator()(int b, int r, int c, double acc) const {
+    const int p = r / m, i = r - p * m;
+    if (i > c) return;
+    double v = alpha * acc;
+    if (r == c && r < m) v += shift;
+    out[b * bs + (int64_t)r * ld + c] = v;
+    if (i < c) out[b * bs + (int64_t)(p * m + c) * ld + i] = p == 0 ? v : -v;
+  }
+};
+
 template <class Cfg, class AOp, class BOp, class COp, class Dims>
 __global__ void __launch_bounds__(Cfg::NT) gemm_f64_kernel(AOp A, BOp B, COp C, Dims D, int tiles_n) {
   constexpr int BM = Cfg::BM, BN = Cfg::BN, KC = Cfg::KC, TM = Cfg::TM, TN = Cfg::TN;
@@ -105,7 +156,7 @@ __global__ void __launch_bounds__(Cfg::NT) gemm_f64_kernel(AOp A, BOp B, COp C, 
   const int tile = blockIdx.y + blockIdx.z * gridDim.y;  // grid.z only when tiles > 65535
   const int tm = tile / tiles_n, tn = tile - (tile / tiles_n) * tiles_n;
   const int m0 = tm * BM, n0 = tn * BN;
-  if (m0 >= M || n0 >= N) return;
+  if (m0 >= M || n0 >= N || tile_skip(D, m0, n0, BM, BN)) return;
 
   __shared__ double As[KC][BM + 1];
   __shared__ double Bs[KC][BN + 1];
@@ -163,6 +214,10 @@ __global__ void __launch_bounds__(Cfg::NT) gemm_f64_kernel(AOp A, BOp B, COp C, 
 template <class Dims>
 inline double dims_flops(const Dims &, int) { return 0.0; }
 inline double dims_flops(const UniformDims &d, int batch) { return 2.0 * d.m * d.n * d.k * batch; }
+// Hermitian products: the upper triangle of every part (about half of the full product).
+inline double dims_flops(const HermDims &d, int batch) {
+  return (double)d.m / d.part * d.part * (d.part + 1.0) * d.k * batch;
+}
 struct SplitDims;
 inline double dims_flops(const SplitDims &d, int);
 

@@ -415,6 +415,19 @@ x2c_status quat_gemm(x2c_ctx *ctx, cudaStream_t st, int nb, int m, int nc, const
   }
 }
 
+// Quaternion product whose result is Hermitian (products of commuting Hermitian matrices:
+// every Newton-Schulz product here): only the upper triangle of each part is computed, the
+// epilogue mirrors.  Worth it for large parts (no split-K there).
+constexpr int kHermMin = 256;
+template <class COp>
+x2c_status quat_gemm_herm(x2c_ctx *ctx, cudaStream_t st, int nb, int m, int nc, const double *A,
+                          const double *B, const COp &C) {
+  QuatLeft<false> a{A, m, (int64_t)nc * m * m, (int64_t)m * m, m, nc, 1.0};
+  Mat<false> b{B, m, (int64_t)nc * m * m, 1.0};
+  const int M = nc * m, K = nc * m;
+  return gemm_f64<TileLarge>(ctx, st, nb, M, m, a, b, C, HermDims{M, m, K, m}, "solve_quat_gemm");
+}
+
 // Square-ish products of the solve (no split-K): tile by size.
 template <class AOp, class BOp, class COp>
 x2c_status gemm_sq(x2c_ctx *ctx, cudaStream_t st, int batch, int n, const AOp &A, const BOp &B, const COp &C) {
@@ -570,11 +583,18 @@ x2c_status solve_transforms(x2c_ctx *ctx, cudaStream_t st, double c, int nb, int
   X2C_TRY(launched(ctx, "scale_kernel", st));
   // 3. Sign function by the scaled Newton-Schulz schedule.
   const std::vector<double> sched = sign_schedule(kSignLowerBound);
+  const bool herm_d = d >= kHermMin, herm_n = n >= kHermMin;
   for (double a : sched) {
-    X2C_TRY(quat_gemm(ctx, st, nb, d, nc, Z, Z, 1.0, store_plain(Y, d, nc), part));
-    // Zn = (3a/2) Z - (a^3/2) Z Y
-    StoreAxpby upd{Zn, Z, d, (int64_t)nc * d2, -0.5 * a * a * a, 1.5 * a};
-    X2C_TRY(quat_gemm(ctx, st, nb, d, nc, Z, Y, 1.0, upd, part));
+    // Y = Z Z;  Zn = (3a/2) Z - (a^3/2) Z Y   (Z, Y commute and are Hermitian)
+    if (herm_d) {
+      X2C_TRY(quat_gemm_herm(ctx, st, nb, d, nc, Z, Z, StoreAxpbyHerm{Y, nullptr, d, (int64_t)nc * d2, 1.0, 0.0, d}));
+      X2C_TRY(quat_gemm_herm(ctx, st, nb, d, nc, Z, Y,
+                             StoreAxpbyHerm{Zn, Z, d, (int64_t)nc * d2, -0.5 * a * a * a, 1.5 * a, d}));
+    } else {
+      X2C_TRY(quat_gemm(ctx, st, nb, d, nc, Z, Z, 1.0, store_plain(Y, d, nc), part));
+      StoreAxpby upd{Zn, Z, d, (int64_t)nc * d2, -0.5 * a * a * a, 1.5 * a};
+      X2C_TRY(quat_gemm(ctx, st, nb, d, nc, Z, Y, 1.0, upd, part));
+    }
     std::swap(Z, Zn);
   }
   X2C_TRY(check(ctx, st, nb, d, nc, Y, Z, kSignTol, slot, trace, status));
@@ -587,10 +607,17 @@ x2c_status solve_transforms(x2c_ctx *ctx, cudaStream_t st, double c, int nb, int
   identity_kernel<<<aux_grid(nb, nc * n2), 256, 0, st>>>(n, nc, Zk);
   X2C_TRY(launched(ctx, "identity_kernel", st));
   for (int it = 0; it < kSqrtIters; ++it) {
-    StoreShiftIdentity tm{Tm, n, (int64_t)nc * n2, n, -0.5, 1.5};
-    X2C_TRY(quat_gemm(ctx, st, nb, n, nc, Zk, Yk, 1.0, tm, part));
-    X2C_TRY(quat_gemm(ctx, st, nb, n, nc, Yk, Tm, 1.0, store_plain(Yk2, n, nc), part));
-    X2C_TRY(quat_gemm(ctx, st, nb, n, nc, Tm, Zk, 1.0, store_plain(Zk2, n, nc), part));
+    // Tm = 3/2 - Zk Yk / 2;  Yk <- Yk Tm;  Zk <- Tm Zk   (all functions of P_LL: Hermitian)
+    if (herm_n) {
+      X2C_TRY(quat_gemm_herm(ctx, st, nb, n, nc, Zk, Yk, StoreShiftIdentityHerm{Tm, n, (int64_t)nc * n2, n, -0.5, 1.5}));
+      X2C_TRY(quat_gemm_herm(ctx, st, nb, n, nc, Yk, Tm, StoreAxpbyHerm{Yk2, nullptr, n, (int64_t)nc * n2, 1.0, 0.0, n}));
+      X2C_TRY(quat_gemm_herm(ctx, st, nb, n, nc, Tm, Zk, StoreAxpbyHerm{Zk2, nullptr, n, (int64_t)nc * n2, 1.0, 0.0, n}));
+    } else {
+      StoreShiftIdentity tm{Tm, n, (int64_t)nc * n2, n, -0.5, 1.5};
+      X2C_TRY(quat_gemm(ctx, st, nb, n, nc, Zk, Yk, 1.0, tm, part));
+      X2C_TRY(quat_gemm(ctx, st, nb, n, nc, Yk, Tm, 1.0, store_plain(Yk2, n, nc), part));
+      X2C_TRY(quat_gemm(ctx, st, nb, n, nc, Tm, Zk, 1.0, store_plain(Zk2, n, nc), part));
+    }
     std::swap(Yk, Yk2);
     std::swap(Zk, Zk2);
   }

@@ -693,24 +693,22 @@ struct Runner {
     return X2C_ERR_ARG;
   }
 
-  // N tile: two-component products have 4 n columns (96 per tile, 64 when S = 6 to keep the
-  // S accumulators within 512 TMEM columns); spin-free ones n columns (64, or 32 when S = 6).
-  // stage_kind: 1 = fused stage-1 epilogue, 2 = stage-2 epilogue (sizes of their smem staging)
-  template <class Epi>
+  // N tile NT4 (two-component, 4 n columns) or NT1 (spin-free, n columns); the S
+  // accumulators of a tile take S x NT <= 512 TMEM columns.  The pair (NT4, NT1) is chosen by
+  // the autotuner (assemble_pairs_split).  stage_kind: 1 = fused stage-1 epilogue, 2 =
+  // stage-2 epilogue (sizes of their smem staging).
+  template <int NT4, int NT1, class Epi>
   static x2c_status gemm_any(x2c_ctx *ctx, cudaStream_t st, int nc, int KP, const __nv_bfloat16 *A,
                              const __nv_bfloat16 *B, int m_tiles, int cols, const Epi &epi, int stage_kind,
                              int a_rows, const char *name) {
+    static_assert(S * NT4 <= 512 && S * NT1 <= 512, "TMEM columns");
     if (nc == 4) {
-      constexpr int NT = (S <= 5) ? 96 : 64;
-      const int stage = stage_kind == 2 ? Stage2Store<4>::stage_bytes(NT) : Stage1Fused<S, 4>::stage_bytes(NT);
-      return gemm_kp<NT>(ctx, st, KP, A, B, m_tiles, (cols + NT - 1) / NT, epi, stage, a_rows, name);
+      const int stage = stage_kind == 2 ? Stage2Store<4>::stage_bytes(NT4) : Stage1Fused<S, 4>::stage_bytes(NT4);
+      return gemm_kp<NT4>(ctx, st, KP, A, B, m_tiles, (cols + NT4 - 1) / NT4, epi, stage, a_rows, name);
     }
-    constexpr int NT = (S <= 5) ? 64 : 32;
-    const int stage = stage_kind == 2 ? Stage2Store<1>::stage_bytes(NT) : Stage1Fused<S, 1>::stage_bytes(NT);
-    return gemm_kp<NT>(ctx, st, KP, A, B, m_tiles, (cols + NT - 1) / NT, epi, stage, a_rows, name);
+    const int stage = stage_kind == 2 ? Stage2Store<1>::stage_bytes(NT1) : Stage1Fused<S, 1>::stage_bytes(NT1);
+    return gemm_kp<NT1>(ctx, st, KP, A, B, m_tiles, (cols + NT1 - 1) / NT1, epi, stage, a_rows, name);
   }
-
-  static int ntile(int nc) { return nc == 4 ? ((S <= 5) ? 96 : 64) : ((S <= 5) ? 64 : 32); }
 
   template <class Src>
   static x2c_status slice(x2c_ctx *ctx, cudaStream_t st, const Src &src, int rows, int rows_pad, int K, int KP,
@@ -730,12 +728,13 @@ struct Runner {
     return launched(ctx, "split_kexp", st);
   }
 
+  template <int NT4, int NT1>
   static x2c_status run(x2c_ctx *ctx, cudaStream_t st, double c, int nc, int so_all,
                         const std::vector<PairDesc> &pairs_in, const MolDesc *d_mols, UTable ut,
                         const std::vector<const double *> &hUL, const std::vector<const double *> &hUS,
-                        Arena &ar) {
+                        const Arena &ar) {
     const double inv4c2 = 1.0 / (4.0 * c * c);
-    const int NT = ntile(nc);
+    const int NT = nc == 4 ? NT4 : NT1;
     // classes: pairs sharing (uA, uB) (and so nA, nB)
     std::map<std::pair<int, int>, std::vector<PairDesc>> classes;
     for (const auto &P : pairs_in) classes[{P.uA, P.uB}].push_back(P);
@@ -793,17 +792,17 @@ struct Runner {
         X2C_TRY(slice(ctx, st, MidRowsPadded{ci, TRA}, rows1, rows1, 2 * nB, KP1, TRA, 1, k1p, A1, e1,
                       "split_slice_mid"));
         if (nc == 4)
-          X2C_TRY(gemm_any(ctx, st, nc, KP1, A1, Fs, np, cols1,
-                           Stage1Fused<S, 4>{e1, k2p, eF, A2, e2, np, nA, cols1, KP2, TRA}, 1, TRA, "split_stage1"));
+          X2C_TRY((gemm_any<NT4, NT1>(ctx, st, nc, KP1, A1, Fs, np, cols1,
+                           Stage1Fused<S, 4>{e1, k2p, eF, A2, e2, np, nA, cols1, KP2, TRA}, 1, TRA, "split_stage1")));
         else
-          X2C_TRY(gemm_any(ctx, st, nc, KP1, A1, Fs, np, cols1,
-                           Stage1Fused<S, 1>{e1, k2p, eF, A2, e2, np, nA, cols1, KP2, TRA}, 1, TRA, "split_stage1"));
+          X2C_TRY((gemm_any<NT4, NT1>(ctx, st, nc, KP1, A1, Fs, np, cols1,
+                           Stage1Fused<S, 1>{e1, k2p, eF, A2, e2, np, nA, cols1, KP2, TRA}, 1, TRA, "split_stage1")));
         if (nc == 4)
-          X2C_TRY(gemm_any(ctx, st, nc, KP2, A2, Gs, rows2p / kTileM, cols2,
-                           Stage2Store<4>{dp, d_mols, e2, eG, rows2, nA, nB, S}, 2, kTileM, "split_stage2"));
+          X2C_TRY((gemm_any<NT4, NT1>(ctx, st, nc, KP2, A2, Gs, rows2p / kTileM, cols2,
+                           Stage2Store<4>{dp, d_mols, e2, eG, rows2, nA, nB, S}, 2, kTileM, "split_stage2")));
         else
-          X2C_TRY(gemm_any(ctx, st, nc, KP2, A2, Gs, rows2p / kTileM, cols2,
-                           Stage2Store<1>{dp, d_mols, e2, eG, rows2, nA, nB, S}, 2, kTileM, "split_stage2"));
+          X2C_TRY((gemm_any<NT4, NT1>(ctx, st, nc, KP2, A2, Gs, rows2p / kTileM, cols2,
+                           Stage2Store<1>{dp, d_mols, e2, eG, rows2, nA, nB, S}, 2, kTileM, "split_stage2")));
         // spin-orbit middle term (FP64): diagonal pairs, or all pairs in the general case
         if (nc == 4) {
           std::vector<PairDesc> so;
@@ -830,16 +829,84 @@ struct Runner {
 
 }  // namespace
 
+namespace {
+
+// Autotuner: the N tile pairs each slice count may use, tried once per workload shape on the
+// first build of a context; every candidate computes bit-identical h (exact integer digit
+// products, the same per-element epilogue), so the tuning runs are real builds.
+template <int S>
+x2c_status run_choice(int choice, x2c_ctx *ctx, cudaStream_t st, double c, int nc, int so_all,
+                      const std::vector<PairDesc> &pairs, const MolDesc *d_mols, UTable ut,
+                      const std::vector<const double *> &hUL, const std::vector<const double *> &hUS,
+                      const Arena &ar) {
+  if constexpr (S <= 5) {
+    if (choice == 0) return Runner<S>::template run<96, 64>(ctx, st, c, nc, so_all, pairs, d_mols, ut, hUL, hUS, ar);
+  }
+  return Runner<S>::template run<64, 32>(ctx, st, c, nc, so_all, pairs, d_mols, ut, hUL, hUS, ar);
+}
+constexpr const char *kChoiceName[2] = {"NT 96 (2c) / 64 (sf)", "NT 64 (2c) / 32 (sf)"};
+
+template <int S>
+x2c_status run_tuned(x2c_ctx *ctx, cudaStream_t st, double c, int nc, int so_all, const std::vector<PairDesc> &pairs,
+                     const MolDesc *d_mols, UTable ut, const std::vector<const double *> &hUL,
+                     const std::vector<const double *> &hUS, const Arena &ar) {
+  const int n_choices = S <= 5 ? 2 : 1;
+  // shape key: slices, spin, the (nA, nB) classes and the order of magnitude of the pair count
+  uint64_t key = 1469598103934665603ull;
+  auto mix = [&](uint64_t v) { key = (key ^ v) * 1099511628211ull; };
+  mix(S);
+  mix(nc);
+  mix(63 - __builtin_clzll((unsigned long long)pairs.size()));
+  std::map<std::pair<int, int>, int> shapes;
+  for (const auto &P : pairs) shapes[{P.nA, P.nB}] = 1;
+  for (auto &kv : shapes) mix(((uint64_t)kv.first.first << 20) | (uint64_t)kv.first.second);
+  auto it = ctx->tuned.find(key);
+  if (it != ctx->tuned.end())
+    return run_choice<S>(it->second, ctx, st, c, nc, so_all, pairs, d_mols, ut, hUL, hUS, ar);
+  if (!ctx->autotune || n_choices == 1) {
+    ctx->tuned[key] = 0;
+    return run_choice<S>(S <= 5 ? 0 : 1, ctx, st, c, nc, so_all, pairs, d_mols, ut, hUL, hUS, ar);
+  }
+  for (int i = 0; i < 2; ++i)
+    if (!ctx->tune_ev[i]) X2C_TRY_CUDA(ctx, cudaEventCreate(&ctx->tune_ev[i]));
+  int best = 0;
+  float best_ms = 0.f;
+  std::string log = "split S=" + std::to_string(S) + " nc=" + std::to_string(nc) + " pairs=" +
+                    std::to_string(pairs.size()) + ":";
+  // one untimed pass over the candidates first (module load, shared-memory configuration,
+  // cold caches), then the timed pass
+  for (int i = 0; i < n_choices; ++i)
+    X2C_TRY(run_choice<S>(i, ctx, st, c, nc, so_all, pairs, d_mols, ut, hUL, hUS, ar));
+  for (int i = 0; i < n_choices; ++i) {
+    X2C_TRY_CUDA(ctx, cudaEventRecord(ctx->tune_ev[0], st));
+    X2C_TRY(run_choice<S>(i, ctx, st, c, nc, so_all, pairs, d_mols, ut, hUL, hUS, ar));
+    X2C_TRY_CUDA(ctx, cudaEventRecord(ctx->tune_ev[1], st));
+    X2C_TRY_CUDA(ctx, cudaEventSynchronize(ctx->tune_ev[1]));
+    float ms = 0.f;
+    X2C_TRY_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->tune_ev[0], ctx->tune_ev[1]));
+    log += std::string(" [") + kChoiceName[i] + " " + std::to_string(ms) + " ms]";
+    if (i == 0 || ms < best_ms) {
+      best = i;
+      best_ms = ms;
+    }
+  }
+  ctx->tuned[key] = best;
+  ctx->tune_log += log + " -> " + kChoiceName[best] + "\n";
+  return X2C_OK;  // h holds the last candidate's (identical) result
+}
+
+}  // namespace
+
 x2c_status assemble_pairs_split(x2c_ctx *ctx, cudaStream_t st, double c, int nc, int so_all_pairs,
                                 const std::vector<PairDesc> &pairs, const MolDesc *d_mols, UTable ut,
                                 const std::vector<const double *> &hUL, const std::vector<const double *> &hUS,
                                 int n_slices, Arena &ar) {
   if (pairs.empty()) return X2C_OK;
   switch (n_slices) {
-    case 3: return Runner<3>::run(ctx, st, c, nc, so_all_pairs, pairs, d_mols, ut, hUL, hUS, ar);
-    case 4: return Runner<4>::run(ctx, st, c, nc, so_all_pairs, pairs, d_mols, ut, hUL, hUS, ar);
-    case 5: return Runner<5>::run(ctx, st, c, nc, so_all_pairs, pairs, d_mols, ut, hUL, hUS, ar);
-    case 6: return Runner<6>::run(ctx, st, c, nc, so_all_pairs, pairs, d_mols, ut, hUL, hUS, ar);
+    case 3: return run_tuned<3>(ctx, st, c, nc, so_all_pairs, pairs, d_mols, ut, hUL, hUS, ar);
+    case 4: return run_tuned<4>(ctx, st, c, nc, so_all_pairs, pairs, d_mols, ut, hUL, hUS, ar);
+    case 5: return run_tuned<5>(ctx, st, c, nc, so_all_pairs, pairs, d_mols, ut, hUL, hUS, ar);
+    case 6: return run_tuned<6>(ctx, st, c, nc, so_all_pairs, pairs, d_mols, ut, hUL, hUS, ar);
   }
   return X2C_ERR_ARG;
 }

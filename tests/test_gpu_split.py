@@ -113,3 +113,26 @@ def test_batched_uneven_molecules_split_and_fp64(ctx):
             assert (hb[0] - hs[0]).abs().max().item() <= 1e-13 * hs[0].abs().max().item()
             ref = O.x2c_dlu(m, mol.offsets, [kinds[b] for b in mol.basis])["h"]
             assert np.abs(hb[0].cpu().numpy() - ref).max() <= tol * np.abs(ref).max()
+
+
+def test_autotuner_choices_give_identical_h():
+    """The tile autotuner times every candidate on the first build of a shape; all candidates
+    must give bit-identical h (exact digit products), equal to a context without tuning."""
+    mol = w.silver_cluster(6, "s48")
+    for two_c in (False, True):
+        g = dev(w.molecule_inputs(mol, two_c))
+        gk = dev(w.atomic_inputs(47.0, "s48", two_c))
+        tuned, plain = x.Context(0), x.Context(0)
+        plain.set_autotune(False)
+        h1 = x.x2c_build_dlu(tuned, g, mol.offsets, [0] * 6, [gk], two_component=two_c, precision=x.PREC_SPLIT_BF16)
+        h2 = x.x2c_build_dlu(tuned, g, mol.offsets, [0] * 6, [gk], two_component=two_c, precision=x.PREC_SPLIT_BF16)
+        h3 = x.x2c_build_dlu(plain, g, mol.offsets, [0] * 6, [gk], two_component=two_c, precision=x.PREC_SPLIT_BF16)
+        tuned.status()
+        plain.status()
+        log = tuned.tuning_log()
+        assert "split S=5" in log and "->" in log, log
+        assert plain.tuning_log() == ""
+        for a, b, c in zip(h1, h2, h3):
+            assert torch.equal(a, b) and torch.equal(a, c)
+        tuned.close()
+        plain.close()
