@@ -102,6 +102,21 @@ struct MidRowsPadded {
   }
 };
 
+// Stage-1 A rows of the same-atom spin-orbit term, one quaternion part k = 1..3 of the middle
+// matrix i sigma.W / 4c^2 at a time: only the small-small block (Y = X = 1) is non-zero.
+struct SoMidRowsPadded {
+  ClassInfo ci;
+  int TRA, k;
+  __device__ __forceinline__ double operator()(int r, int kk2) const {
+    const int p = r / TRA, rr = r - p * TRA;
+    if (rr < ci.nA || rr >= 2 * ci.nA || kk2 < ci.nB) return 0.0;
+    const PairDesc &P = ci.pairs[p];
+    const MolDesc &m = ci.mols[P.mol];
+    const int64_t o = static_cast<int64_t>(P.offA + rr - ci.nA) * m.ld + (P.offB + kk2 - ci.nB);
+    return m.W[k - 1][o] * ci.inv4c2;
+  }
+};
+
 // B operand of stage 1: rows (j, q), K = (X, k): U^X_q[k][j] of atom kind B.
 struct FtRows {
   const double *UL, *US;
@@ -238,12 +253,16 @@ struct GemmShape {
 // NCQ columns (one j) the stage-2 row exponent is the maximum over the pair's rows of
 // bitlen(I) + e1[row] + kexp2[row]; the digits of I 2^(e1 + kexp2 - bl + 8S) go straight to
 // the stage-2 A slices (row r2 = pair * cols1 + c, k = (Y, i)) with e2[r2] = bl + eF[c] - 8(S+1).
-template <int S, int NCQ>
+// perm = k (1..3, two-component): the spin-orbit pass of quaternion part k; the product with
+// the middle part k maps column (j, q) of M_k F to column (j, q xor k) of the stage-2 operand
+// with the sign of the quaternion product table (C_l = sign(l, l xor k) M_k F_(l xor k)).
+template <int S, int NCQ, bool SOP = false>
 struct Stage1Fused {
   const int *e1, *k2p, *eF;
   __nv_bfloat16 *A2;
   int *e2;
   int n_pairs, nA, cols1, KP2, tra;
+  int perm;
   static int stage_bytes(int NT) { return 4 * NT * 4 + 64; }  // per (quarter, column) maxima
   template <int NC>
   __device__ __forceinline__ void operator()(int mt, int nt, int NT, int rloc, int c0, const long long (&I)[NC],
@@ -288,9 +307,16 @@ struct Stage1Fused {
     for (int j = 0; j < NC; ++j) {
       const int c = cbase + j;
       if (c >= cols1 || !kvalid) continue;
-      const int r2 = p * cols1 + c;
+      int cd = c;
+      long long v = I[j];
+      if (SOP && NCQ == 4) {
+        const int q = c & 3;
+        cd = (c & ~3) | (q ^ perm);
+        if (quat_sign(q ^ perm, q) < 0) v = -v;
+      }
+      const int r2 = p * cols1 + cd;
       int d[S];
-      digits<S>(rowv ? shift_round(I[j], ek - bl[j] + 8 * S) : 0, d);
+      digits<S>(rowv ? shift_round(v, ek - bl[j] + 8 * S) : 0, d);
       const size_t o0 = core_off(r2, rloc, kTileM, KP2, S, 0);
       const size_t slice_stride = static_cast<size_t>(kTileM) * KP2;
 #pragma unroll
@@ -298,6 +324,84 @@ struct Stage1Fused {
       if (rloc == 0) e2[r2] = bl[j] + eF[c] - 8 * (S + 1);
     }
     epi_sync();
+  }
+};
+
+// Stage 1 with transposed roles (TRM kernel): the tile is R_AB^T, rows c = (j, q) of the
+// resident F^T tile nt (lanes), columns r = (Y, i) of the streamed pair mt.  Each thread holds
+// its row c: the stage-2 row exponent (max over r of bitlen(I) + e1 + kexp2, shared by the 4
+// quaternion rows of one j) needs only the 4 warps of its lane quarter (shared memory and a
+// 128-thread named barrier) and two shuffles, and the digits of 8 consecutive r form one
+// 16-byte chunk of the stage-2 operand's core-matrix layout, written with one vector store
+// per slice.
+template <int S, bool SOP = false>
+struct Stage1T {
+  const int *e1, *k2p, *eF;
+  __nv_bfloat16 *A2;
+  int *e2;
+  int n_pairs, nA, cols1, KP2, tra;  // tra = rows of the streamed operand per pair (NT)
+  int perm;                           // spin-orbit pass k (SOP): row (j, q) -> (j, q xor k), signed
+  static int stage_bytes(int) { return 2 * 4 * 4 * 32 * 4 + 64; }  // [parity][quarter][sub][lane]
+  template <int NC>
+  __device__ __forceinline__ void operator()(int mt, int nt, int NT, int rloc, int c0, const long long (&I)[NC],
+                                             int lane, uint8_t *stage) const {
+    static_assert(NC % 8 == 0, "columns per warp");
+    const int p = mt;
+    const int quarter = rloc >> 5, sub = c0 / NC;
+    const int par = ((mt - static_cast<int>(blockIdx.y)) / static_cast<int>(gridDim.y)) & 1;
+    int *red = reinterpret_cast<int *>(stage) + par * (4 * 4 * 32);
+    const int c = nt * kTileM + rloc;
+    const bool cv = c < cols1;
+    const int rows_p = 2 * nA;
+    int ek[NC];
+    int m = kNoExp;
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+      const int r = c0 + j;
+      ek[j] = r < rows_p ? e1[p * tra + r] + k2p[r] : 0;
+      if (r < rows_p && I[j] != 0) {
+        const unsigned long long a = I[j] < 0 ? static_cast<unsigned long long>(-I[j]) : static_cast<unsigned long long>(I[j]);
+        m = max(m, 64 - __clzll(static_cast<long long>(a)) + ek[j]);
+      }
+    }
+    red[(quarter * 4 + sub) * 32 + lane] = m;
+    asm volatile("bar.sync %0, 128;" ::"r"(2 + quarter) : "memory");
+    m = max(max(red[(quarter * 4) * 32 + lane], red[(quarter * 4 + 1) * 32 + lane]),
+            max(red[(quarter * 4 + 2) * 32 + lane], red[(quarter * 4 + 3) * 32 + lane]));
+    m = max(m, __shfl_xor_sync(0xffffffffu, m, 1));  // the 4 quaternion rows of one j
+    m = max(m, __shfl_xor_sync(0xffffffffu, m, 2));
+    if (m == kNoExp) m = 0;
+    int cd = c;
+    bool neg = false;
+    if (SOP) {
+      const int q = c & 3;
+      cd = (c & ~3) | (q ^ perm);
+      neg = quat_sign(q ^ perm, q) < 0;
+    }
+    const int r2 = p * cols1 + cd;
+    if (cv && sub == 0) e2[r2] = m + eF[c] - 8 * (S + 1);
+    if (!cv) return;
+    const size_t slice_stride = static_cast<size_t>(kTileM) * KP2;
+#pragma unroll
+    for (int g = 0; g < NC; g += 8) {
+      uint32_t w[S][4];
+#pragma unroll
+      for (int jj = 0; jj < 8; jj += 2) {
+        int d0[S], d1[S];
+        const int j = g + jj;
+        const long long v0 = neg ? -I[j] : I[j], v1 = neg ? -I[j + 1] : I[j + 1];
+        digits<S>((c0 + j) < rows_p ? shift_round(v0, ek[j] - m + 8 * S) : 0, d0);
+        digits<S>((c0 + j + 1) < rows_p ? shift_round(v1, ek[j + 1] - m + 8 * S) : 0, d1);
+#pragma unroll
+        for (int s2 = 0; s2 < S; ++s2)
+          w[s2][jj >> 1] = static_cast<uint32_t>(__bfloat16_as_ushort(int_to_bf16(d0[s2]))) |
+                           (static_cast<uint32_t>(__bfloat16_as_ushort(int_to_bf16(d1[s2]))) << 16);
+      }
+      const size_t o0 = core_off(r2, c0 + g, kTileM, KP2, S, 0);
+#pragma unroll
+      for (int s2 = 0; s2 < S; ++s2)
+        *reinterpret_cast<uint4 *>(A2 + o0 + s2 * slice_stride) = make_uint4(w[s2][0], w[s2][1], w[s2][2], w[s2][3]);
+    }
   }
 };
 
@@ -312,6 +416,7 @@ struct Stage2Store {
   const MolDesc *mols;
   const int *e2, *eG;
   int rows, nA, nB, S;
+  int accumulate;  // add to h instead of writing it (the spin-orbit passes of diagonal pairs)
   // staging: [part][i' (NT/NCQ)][j (128/NCQ)] doubles, then per-j-slot pair info
   static int stage_bytes(int NT) { return NT * kTileM * 8 / NCQ + (kTileM / NCQ) * 16; }
   template <int NC>
@@ -400,14 +505,17 @@ struct Stage2Store {
       const int4 info = slot[jl2];
       if (info.x < 0 || il2 >= iv) continue;
       const MolDesc &m = mols[info.w];
-      m.h[part][static_cast<int64_t>(info.x + ip0 + il2) * m.ld + info.y] = sv[(part * IT + il2) * JT + jl2];
+      double *dst = m.h[part] + static_cast<int64_t>(info.x + ip0 + il2) * m.ld + info.y;
+      const double val = sv[(part * IT + il2) * JT + jl2];
+      if (accumulate) *dst += val;
+      else *dst = val;
     }
     // mirror h_BA = h_AB+: rows offB + j, contiguous along i'
     for (int idx = tid; idx < NCQ * IT * JT; idx += nthr) {
       const int il2 = idx % IT, rest = idx / IT;
       const int jl2 = rest % JT, part = rest / JT;
       const int4 info = slot[jl2];
-      if (info.x < 0 || info.z || il2 >= iv) continue;
+      if (info.x < 0 || info.z || il2 >= iv || accumulate) continue;
       const MolDesc &m = mols[info.w];
       const double v = sv[(part * IT + il2) * JT + jl2];
       m.h[part][static_cast<int64_t>(info.y) * m.ld + (info.x + ip0 + il2)] = (part == 0) ? v : -v;
@@ -416,15 +524,21 @@ struct Stage2Store {
   }
 };
 
-template <int S, int NT, int KP, class Epi>
+// TRM = false: the B operand (NT rows, S slices) stays resident per CTA (N tile blockIdx.x)
+// and 128-row A tiles stream through the ring.  TRM = true (transposed roles): the A operand
+// (128 rows) stays resident per CTA (M tile blockIdx.x) and NT-row B tiles stream; the
+// pointer A is always the streamed operand and B the resident one.
+template <int S, int NT, int KP, class Epi, bool TRM = false>
 __global__ void __launch_bounds__(kGemmThreads, 1)
     ozaki_gemm_kernel(const __nv_bfloat16 *__restrict__ A, const __nv_bfloat16 *__restrict__ B, int m_tiles,
                       int a_rows, Epi epi, int stage_bytes, int *status) {
   using G = GemmShape<S, NT, KP>;
+  constexpr uint32_t RES_TILE = TRM ? G::A_TILE : G::B_TILE;   // resident slice bytes
+  constexpr uint32_t STR_TILE = TRM ? G::B_TILE : G::A_TILE;   // streamed slice bytes
   extern __shared__ __align__(128) uint8_t smem[];
-  uint8_t *sB = smem;
-  uint8_t *sA = sB + S * G::B_TILE;
-  uint8_t *sStage = sA + kStages * G::A_TILE;
+  uint8_t *sB = smem;                          // resident slices
+  uint8_t *sA = sB + S * RES_TILE;             // ring of streamed slices
+  uint8_t *sStage = sA + kStages * STR_TILE;
   uint64_t *bars = reinterpret_cast<uint64_t *>(sStage + ((stage_bytes + 127) / 128) * 128);
   uint64_t *bar_b = bars, *full = bars + 1, *empty = bars + 1 + kStages;
   uint64_t *acc_full = bars + 1 + 2 * kStages, *acc_empty = acc_full + 1;
@@ -448,12 +562,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     umma::tmem_alloc(tmem_slot, G::TMEM_COLS);
     umma::tmem_relinquish();
   }
-  // A tiles of a_rows < 128 rows leave rows a_rows..127 of every ring slot at zero for good
-  if (a_rows < kTileM) {
+  // streamed A tiles of a_rows < 128 rows leave rows a_rows..127 of every ring slot at zero
+  if (!TRM && a_rows < kTileM) {
     const uint32_t row_bytes = KP * 2;  // one row spread over core matrices: zero whole 8-row groups
     const uint32_t first = static_cast<uint32_t>(a_rows / 8) * 8 * row_bytes;
-    for (uint32_t o = first + threadIdx.x * 16; o < G::A_TILE; o += blockDim.x * 16)
-      for (int st = 0; st < kStages; ++st) *reinterpret_cast<uint4 *>(sA + st * G::A_TILE + o) = make_uint4(0, 0, 0, 0);
+    for (uint32_t o = first + threadIdx.x * 16; o < STR_TILE; o += blockDim.x * 16)
+      for (int st = 0; st < kStages; ++st) *reinterpret_cast<uint4 *>(sA + st * STR_TILE + o) = make_uint4(0, 0, 0, 0);
   }
   __syncthreads();
   umma::fence_after_sync();
@@ -465,9 +579,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
 
   if (warp == 0) {
     if (lane == 0) {  // ---------------- producer
-      umma::mbar_expect_tx(bar_b, S * G::B_TILE);
+      umma::mbar_expect_tx(bar_b, S * RES_TILE);
       for (int t = 0; t < S; ++t)
-        umma::bulk_g2s(sB + t * G::B_TILE, B + (static_cast<size_t>(nt) * S + t) * (G::B_TILE / 2), G::B_TILE, bar_b);
+        umma::bulk_g2s(sB + t * RES_TILE, B + (static_cast<size_t>(nt) * S + t) * (RES_TILE / 2), RES_TILE, bar_b);
       long long it = 0;
       for (int ti = 0; ti < n_my && !abort_flag; ++ti) {
         const int mt = blockIdx.y + ti * gridDim.y;
@@ -480,7 +594,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             break;
           }
           umma::mbar_expect_tx(&full[slot], a_bytes);
-          umma::bulk_g2s(sA + slot * G::A_TILE, At + static_cast<size_t>(s2) * (a_bytes / 2), a_bytes, &full[slot]);
+          umma::bulk_g2s(sA + slot * STR_TILE, At + static_cast<size_t>(s2) * (a_bytes / 2), a_bytes, &full[slot]);
         }
       }
       // before the CTA may exit, every issued copy must have landed
@@ -507,9 +621,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             break;
           }
           umma::fence_after_sync();
-          const uint32_t a0 = umma::smem_u32(sA + slot * G::A_TILE);
+          const uint32_t str0 = umma::smem_u32(sA + slot * STR_TILE);
           for (int t = 0; t + s2 < S; ++t) {
-            const uint32_t b0 = umma::smem_u32(sB + t * G::B_TILE);
+            const uint32_t res0 = umma::smem_u32(sB + t * RES_TILE);
+            const uint32_t a0 = TRM ? res0 : str0, b0 = TRM ? str0 : res0;
             const uint32_t d = tmem + static_cast<uint32_t>((s2 + t) * NT);
 #pragma unroll
             for (int kk = 0; kk < KP / 16; ++kk) {
@@ -693,6 +808,41 @@ struct Runner {
     return X2C_ERR_ARG;
   }
 
+  // Transposed-role stage 1 (TRM kernel): resident 128-row F^T tiles, streamed pair tiles
+  // of NTs = KP2 rows; instantiated for S = 5 and KP2, KP1 in {64, 96}.
+  template <int NTs, int KP, class Epi>
+  static x2c_status gemm_t(x2c_ctx *ctx, cudaStream_t st, const __nv_bfloat16 *Astream, const __nv_bfloat16 *Bres,
+                           int m_tiles, int n_tiles, const Epi &epi, const char *name) {
+    using Gs = GemmShape<S, NTs, KP>;
+    auto kern = ozaki_gemm_kernel<S, NTs, KP, Epi, true>;
+    const int stage_bytes = Epi::stage_bytes(NTs);
+    const int smem = static_cast<int>(S * Gs::A_TILE + kStages * Gs::B_TILE + (stage_bytes + 127) / 128 * 128 + 256);
+    if (smem > 232448) return X2C_ERR_ARG;
+    X2C_TRY_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int per_n = std::max(1, std::min(m_tiles, std::max(1, sms / n_tiles)));
+    dim3 grid(n_tiles, per_n);
+    tbegin(ctx, st);
+    kern<<<grid, kGemmThreads, smem, st>>>(Astream, Bres, m_tiles, NTs, epi, stage_bytes, ctx->d_status);
+    return launched(ctx, name, st);
+  }
+  static bool trm_ok(int nc, int KP1, int KP2) {
+    return S == 5 && nc == 4 && (KP2 == 64 || KP2 == 96) && (KP1 == 64 || KP1 == 96);
+  }
+  template <class Epi>
+  static x2c_status gemm_t_any(x2c_ctx *ctx, cudaStream_t st, int KP2, int KP1, const __nv_bfloat16 *Astream,
+                               const __nv_bfloat16 *Bres, int m_tiles, int n_tiles, const Epi &epi, const char *name) {
+    if constexpr (S == 5) {
+      if (KP2 == 96 && KP1 == 96) return gemm_t<96, 96>(ctx, st, Astream, Bres, m_tiles, n_tiles, epi, name);
+      if (KP2 == 96 && KP1 == 64) return gemm_t<96, 64>(ctx, st, Astream, Bres, m_tiles, n_tiles, epi, name);
+      if (KP2 == 64 && KP1 == 96) return gemm_t<64, 96>(ctx, st, Astream, Bres, m_tiles, n_tiles, epi, name);
+      if (KP2 == 64 && KP1 == 64) return gemm_t<64, 64>(ctx, st, Astream, Bres, m_tiles, n_tiles, epi, name);
+    }
+    return X2C_ERR_ARG;
+  }
+
   // N tile NT4 (two-component, 4 n columns) or NT1 (spin-free, n columns); the S
   // accumulators of a tile take S x NT <= 512 TMEM columns.  The pair (NT4, NT1) is chosen by
   // the autotuner (assemble_pairs_split).  stage_kind: 1 = fused stage-1 epilogue, 2 =
@@ -732,7 +882,7 @@ struct Runner {
   static x2c_status run(x2c_ctx *ctx, cudaStream_t st, double c, int nc, int so_all,
                         const std::vector<PairDesc> &pairs_in, const MolDesc *d_mols, UTable ut,
                         const std::vector<const double *> &hUL, const std::vector<const double *> &hUS,
-                        const Arena &ar) {
+                        const Arena &ar, bool trm_req = false) {
     const double inv4c2 = 1.0 / (4.0 * c * c);
     const int NT = nc == 4 ? NT4 : NT1;
     // classes: pairs sharing (uA, uB) (and so nA, nB)
@@ -745,12 +895,16 @@ struct Runner {
       if (2 * nA > 128 || 2 * nB > 128) return X2C_ERR_ARG;
       const int KP1 = (2 * nB + 31) / 32 * 32, KP2 = (2 * nA + 31) / 32 * 32;
       const int cols1 = nc * nB, cols2 = nc * nA;
-      const int ntile1 = (cols1 + NT - 1) / NT, ntile2 = (cols2 + NT - 1) / NT;
-      // per-kind B operands: F (stage 1) of U_B, G' (stage 2) of U_A
+      const int ntile2 = (cols2 + NT - 1) / NT;
+      // stage 1 with transposed roles (resident F^T tiles of 128 rows) where instantiated
+      const bool trm = trm_req && trm_ok(nc, KP1, KP2);
+      const int TRF = trm ? kTileM : NT;                      // F rows per tile
+      const int ntile1 = (cols1 + TRF - 1) / TRF;
+      // per-kind operands: F (stage 1) of U_B, G' (stage 2) of U_A
       Arena a0 = ar;
-      __nv_bfloat16 *Fs = reinterpret_cast<__nv_bfloat16 *>(a0.take_bytes((size_t)ntile1 * NT * KP1 * S * 2));
+      __nv_bfloat16 *Fs = reinterpret_cast<__nv_bfloat16 *>(a0.take_bytes((size_t)ntile1 * TRF * KP1 * S * 2));
       __nv_bfloat16 *Gs = reinterpret_cast<__nv_bfloat16 *>(a0.take_bytes((size_t)ntile2 * NT * KP2 * S * 2));
-      int *eF = reinterpret_cast<int *>(a0.take_bytes((size_t)ntile1 * NT * 4));
+      int *eF = reinterpret_cast<int *>(a0.take_bytes((size_t)ntile1 * TRF * 4));
       int *eG = reinterpret_cast<int *>(a0.take_bytes((size_t)ntile2 * NT * 4));
       // K-equilibration exponents (+ on the A operand's columns, - on the B operand's rows)
       int *k1p = reinterpret_cast<int *>(a0.take_bytes(128 * 4)), *k1n = reinterpret_cast<int *>(a0.take_bytes(128 * 4));
@@ -760,10 +914,10 @@ struct Runner {
       const GtRows gt{hUL[kv.first.first], hUS[kv.first.first], nA, nc};
       X2C_TRY(kexp(ctx, st, ft, cols1, 2 * nB, k1p, k1n));
       X2C_TRY(kexp(ctx, st, gt, cols2, 2 * nA, k2p, k2n));
-      X2C_TRY(slice(ctx, st, ft, cols1, ntile1 * NT, 2 * nB, KP1, NT, nc, k1n, Fs, eF, "split_slice_u"));
+      X2C_TRY(slice(ctx, st, ft, cols1, ntile1 * TRF, 2 * nB, KP1, TRF, nc, k1n, Fs, eF, "split_slice_u"));
       X2C_TRY(slice(ctx, st, gt, cols2, ntile2 * NT, 2 * nA, KP2, NT, nc, k2n, Gs, eG, "split_slice_u"));
       // chunk the pairs so the per-chunk buffers fit the arena
-      const int TRA = (2 * nA + 7) / 8 * 8;  // stage-1 A rows per pair tile
+      const int TRA = trm ? KP2 : (2 * nA + 7) / 8 * 8;  // stage-1 Mid rows per pair tile
       const size_t per_pair = (size_t)TRA * KP1 * S * 2 + (size_t)TRA * 4 + (size_t)cols1 * KP2 * S * 2 +
                               (size_t)cols1 * 4 + (size_t)4 * nA * nB * 8 + 2 * sizeof(PairDesc);
       const size_t avail = a0.cap - a0.off;
@@ -791,23 +945,60 @@ struct Runner {
         ClassInfo ci{dp, d_mols, nA, nB, nc, inv4c2};
         X2C_TRY(slice(ctx, st, MidRowsPadded{ci, TRA}, rows1, rows1, 2 * nB, KP1, TRA, 1, k1p, A1, e1,
                       "split_slice_mid"));
-        if (nc == 4)
+        if (trm)
+          X2C_TRY(gemm_t_any(ctx, st, KP2, KP1, A1, Fs, np, ntile1,
+                             Stage1T<S>{e1, k2p, eF, A2, e2, np, nA, cols1, KP2, TRA, 0}, "split_stage1"));
+        else if (nc == 4)
           X2C_TRY((gemm_any<NT4, NT1>(ctx, st, nc, KP1, A1, Fs, np, cols1,
-                           Stage1Fused<S, 4>{e1, k2p, eF, A2, e2, np, nA, cols1, KP2, TRA}, 1, TRA, "split_stage1")));
+                           Stage1Fused<S, 4>{e1, k2p, eF, A2, e2, np, nA, cols1, KP2, TRA, 0}, 1, TRA, "split_stage1")));
         else
           X2C_TRY((gemm_any<NT4, NT1>(ctx, st, nc, KP1, A1, Fs, np, cols1,
-                           Stage1Fused<S, 1>{e1, k2p, eF, A2, e2, np, nA, cols1, KP2, TRA}, 1, TRA, "split_stage1")));
+                           Stage1Fused<S, 1>{e1, k2p, eF, A2, e2, np, nA, cols1, KP2, TRA, 0}, 1, TRA, "split_stage1")));
         if (nc == 4)
           X2C_TRY((gemm_any<NT4, NT1>(ctx, st, nc, KP2, A2, Gs, rows2p / kTileM, cols2,
-                           Stage2Store<4>{dp, d_mols, e2, eG, rows2, nA, nB, S}, 2, kTileM, "split_stage2")));
+                           Stage2Store<4>{dp, d_mols, e2, eG, rows2, nA, nB, S, 0}, 2, kTileM, "split_stage2")));
         else
           X2C_TRY((gemm_any<NT4, NT1>(ctx, st, nc, KP2, A2, Gs, rows2p / kTileM, cols2,
-                           Stage2Store<1>{dp, d_mols, e2, eG, rows2, nA, nB, S}, 2, kTileM, "split_stage2")));
-        // spin-orbit middle term (FP64): diagonal pairs, or all pairs in the general case
-        if (nc == 4) {
+                           Stage2Store<1>{dp, d_mols, e2, eG, rows2, nA, nB, S, 0}, 2, kTileM, "split_stage2")));
+        // spin-orbit middle term.  Same-atom blocks only (the usual case): three more split
+        // passes over the diagonal pairs, one per quaternion part k of i sigma.W / 4c^2, whose
+        // stage 2 adds U_A+ (E_k R) to h.  All pairs (general case): FP64 products.
+        if (nc == 4 && !so_all) {
           std::vector<PairDesc> so;
           for (int i = 0; i < np; ++i)
-            if (so_all || cls[c0 + i].diag) so.push_back(cls[c0 + i]);
+            if (cls[c0 + i].diag) so.push_back(cls[c0 + i]);
+          if (!so.empty()) {
+            const int ns = (int)so.size();
+            Arena a2 = a1;
+            PairDesc *ds = reinterpret_cast<PairDesc *>(a2.take_bytes(ns * sizeof(PairDesc)));
+            if (!ds) return X2C_ERR_NOMEM;
+            X2C_TRY_CUDA(ctx, cudaMemcpyAsync(ds, so.data(), ns * sizeof(PairDesc), cudaMemcpyHostToDevice, st));
+            const int srows1 = ns * TRA, srows2 = ns * cols1;
+            const int srows2p = (srows2 + kTileM - 1) / kTileM * kTileM;
+            if (srows2p > srows2) {
+              const size_t tail0 = (size_t)(srows2p - kTileM) * KP2 * S * 2;
+              X2C_TRY_CUDA(ctx, cudaMemsetAsync(reinterpret_cast<char *>(A2) + tail0, 0, (size_t)kTileM * KP2 * S * 2, st));
+            }
+            ClassInfo cs{ds, d_mols, nA, nB, nc, inv4c2};
+            for (int k = 1; k <= 3; ++k) {
+              X2C_TRY(slice(ctx, st, SoMidRowsPadded{cs, TRA, k}, srows1, srows1, 2 * nB, KP1, TRA, 1, k1p, A1, e1,
+                            "split_slice_so"));
+              if (trm)
+                X2C_TRY(gemm_t_any(ctx, st, KP2, KP1, A1, Fs, ns, ntile1,
+                                   Stage1T<S, true>{e1, k2p, eF, A2, e2, ns, nA, cols1, KP2, TRA, k}, "split_spin_orbit"));
+              else
+                X2C_TRY((gemm_any<NT4, NT1>(ctx, st, nc, KP1, A1, Fs, ns, cols1,
+                                            Stage1Fused<S, 4, true>{e1, k2p, eF, A2, e2, ns, nA, cols1, KP2, TRA, k}, 1,
+                                            TRA, "split_spin_orbit")));
+              X2C_TRY((gemm_any<NT4, NT1>(ctx, st, nc, KP2, A2, Gs, srows2p / kTileM, cols2,
+                                          Stage2Store<4>{ds, d_mols, e2, eG, srows2, nA, nB, S, 1}, 2, kTileM,
+                                          "split_spin_orbit")));
+            }
+          }
+        }
+        if (nc == 4 && so_all) {
+          std::vector<PairDesc> so;
+          for (int i = 0; i < np; ++i) so.push_back(cls[c0 + i]);
           if (!so.empty()) {
             Arena a2 = a1;
             PairDesc *ds = reinterpret_cast<PairDesc *>(a2.take_bytes(so.size() * sizeof(PairDesc)));
@@ -841,16 +1032,19 @@ x2c_status run_choice(int choice, x2c_ctx *ctx, cudaStream_t st, double c, int n
                       const Arena &ar) {
   if constexpr (S <= 5) {
     if (choice == 0) return Runner<S>::template run<96, 64>(ctx, st, c, nc, so_all, pairs, d_mols, ut, hUL, hUS, ar);
+    if (choice == 2)
+      return Runner<S>::template run<96, 64>(ctx, st, c, nc, so_all, pairs, d_mols, ut, hUL, hUS, ar, true);
   }
   return Runner<S>::template run<64, 32>(ctx, st, c, nc, so_all, pairs, d_mols, ut, hUL, hUS, ar);
 }
-constexpr const char *kChoiceName[2] = {"NT 96 (2c) / 64 (sf)", "NT 64 (2c) / 32 (sf)"};
+constexpr const char *kChoiceName[3] = {"NT 96 (2c) / 64 (sf)", "NT 64 (2c) / 32 (sf)",
+                                        "transposed stage 1 + NT 96 stage 2"};
 
 template <int S>
 x2c_status run_tuned(x2c_ctx *ctx, cudaStream_t st, double c, int nc, int so_all, const std::vector<PairDesc> &pairs,
                      const MolDesc *d_mols, UTable ut, const std::vector<const double *> &hUL,
                      const std::vector<const double *> &hUS, const Arena &ar) {
-  const int n_choices = S <= 5 ? 2 : 1;
+  const int n_choices = S == 5 && nc == 4 ? 3 : (S <= 5 ? 2 : 1);
   // shape key: slices, spin, the (nA, nB) classes and the order of magnitude of the pair count
   uint64_t key = 1469598103934665603ull;
   auto mix = [&](uint64_t v) { key = (key ^ v) * 1099511628211ull; };
