@@ -40,7 +40,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # one ncu capture of the Ag55 two-component build (1540 pairs, the same per-pair shapes as
 # Ag309); a launch's traffic is this times its pairs.  Set an entry to None when its kernel
 # changes.
-PROFILED_DRAM_BYTES_PER_PAIR = {"split_stage1": 242.6e3, "split_stage2": 300.4e3}  # with the 96-column N tile
+PROFILED_DRAM_BYTES_PER_PAIR = {}  # (kernel, variant) -> bytes; filled in from the capture below
 WORKLOADS = {
     "ag309_2c": dict(L=309, basis="s48", two_c=True),
     # 64 uneven spin-free clusters, n ~ U[2, 43], basis s30/s48 50/50, one batched launch
@@ -583,7 +583,7 @@ def run_serving(args, cfg):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="ag309_2c", choices=sorted(WORKLOADS))
@@ -708,8 +708,10 @@ def main():
                 "fp64_equiv_achieved": dom_flops / (dom_ms * 1e-3) / 1e12,
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained, of measured"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    nt96 = any("-> NT 96" in l for l in ctx.tuning_log().splitlines())
-    per_pair = PROFILED_DRAM_BYTES_PER_PAIR.get(dom_name) if two_c and cfg["basis"] == "s48" and nt96 else None
+    log = ctx.tuning_log()
+    variant = {"split_stage1": "trm" if "-> transposed" in log else ("nt96" if "-> NT 96" in log else None),
+               "split_stage2": "nt96" if ("-> transposed" in log or "-> NT 96" in log) else None}.get(dom_name)
+    per_pair = PROFILED_DRAM_BYTES_PER_PAIR.get((dom_name, variant)) if two_c and cfg["basis"] == "s48" else None
     # per launch, like `achieved`: the pairs of all timed launches over their count
     roof["traffic"] = per_pair * len(pairs) * args.steps / dom_launches if per_pair else None
     if per_pair:

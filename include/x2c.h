@@ -197,6 +197,14 @@ x2c_status x2c_build_dlu_host(x2c_ctx *ctx, const x2c_options *opt, const x2c_la
 x2c_status x2c_quaternion_to_dense(const double *const h[4], int32_t n, double *out,
                                    void *stream);
 
+/* Device workspace a build would need, without running it (for callers that budget device
+ * memory; a context grows its workspace to this size on that build).  n_mol >= 1: DLU builds
+ * of x2c_build_dlu_batched's arguments (layouts, mols: HOST arrays of n_mol entries; the
+ * matrix pointers are not dereferenced); n_mol = 0: full X2C of mols[0].  The h outputs and
+ * any transforms the caller passes are not included. */
+x2c_status x2c_query_workspace(x2c_ctx *ctx, const x2c_options *opt, int32_t n_mol, const x2c_layout *layouts,
+                               const x2c_mats *mols, size_t *bytes);
+
 /* Counters of the last build on this context (for instrumentation and benchmarks). */
 typedef struct {
   int64_t pair_blocks;       /* pair blocks assembled (A <= B) */
@@ -226,6 +234,13 @@ x2c_status x2c_ctx_set_timing(x2c_ctx *ctx, int32_t enable);
  * (candidates with their times, and the choice); valid until the next call on the context. */
 x2c_status x2c_ctx_set_autotune(x2c_ctx *ctx, int32_t enable);
 const char *x2c_ctx_tuning_log(x2c_ctx *ctx);
+/* Force one candidate of the split-precision kernels instead of the autotuner's choice:
+ * -1 = automatic (default), 0 = 96-column (two-component) / 64-column (spin-free) N tiles,
+ * 1 = 64 / 32-column N tiles, 2 = transposed-role stage 1 with 96-column stage 2 (two-
+ * component, 5 slices, atoms of 17..48 functions; other classes fall back to 0).  With the
+ * autotuner off and no forced variant the default is 2 where it applies, else 0.  All
+ * variants give bit-identical h. */
+x2c_status x2c_ctx_set_split_variant(x2c_ctx *ctx, int32_t variant);
 x2c_status x2c_ctx_kernel_times(x2c_ctx *ctx, int32_t max_entries, char *names, double *ms,
                                 int64_t *launches, double *flops, int32_t *n_entries);
 

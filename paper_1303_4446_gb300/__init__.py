@@ -54,6 +54,10 @@ class Context:
         """x2c_ctx_set_autotune: time the candidate tensor-core tiles once per workload shape."""
         abi.check(self.lib.x2c_ctx_set_autotune(self.handle, int(bool(enable))), "x2c_ctx_set_autotune")
 
+    def set_split_variant(self, variant: int):
+        """x2c_ctx_set_split_variant: force a split-kernel candidate (-1 = automatic)."""
+        abi.check(self.lib.x2c_ctx_set_split_variant(self.handle, int(variant)), "x2c_ctx_set_split_variant")
+
     def tuning_log(self) -> str:
         """x2c_ctx_tuning_log: the autotuner's decisions, one line each."""
         return self.lib.x2c_ctx_tuning_log(self.handle).decode()
@@ -348,6 +352,23 @@ def x2c_build_dlu_with_transforms(ctx: Context, m: dict, offsets, atom_kind, kin
                                                     ctypes.byref(ms), ctypes.byref(ho), _stream(stream)),
               "x2c_build_dlu_with_transforms", ctx.handle)
     return h
+
+
+def x2c_query_workspace(ctx: Context, m: dict, offsets=None, atom_kind=None, kinds=None, two_component=False,
+                        precision=PREC_FP64, dlu_potential=DLU_FREE_ATOM, full=False):
+    """x2c_query_workspace: device workspace bytes a DLU (or, with full=True, a full X2C)
+    build of these inputs would need (nothing runs)."""
+    ms = mats_struct(m, two_component)
+    o = options(two_component, None, precision, dlu_potential)
+    out = ctypes.c_size_t()
+    if full:
+        abi.check(ctx.lib.x2c_query_workspace(ctx.handle, ctypes.byref(o), 0, None, ctypes.byref(ms),
+                                              ctypes.byref(out)), "x2c_query_workspace")
+    else:
+        lay = LayoutHolder(offsets, atom_kind, kinds, two_component)
+        abi.check(ctx.lib.x2c_query_workspace(ctx.handle, ctypes.byref(o), 1, ctypes.byref(lay.s), ctypes.byref(ms),
+                                              ctypes.byref(out)), "x2c_query_workspace")
+    return out.value
 
 
 # ---- serving ------------------------------------------------------------------------------

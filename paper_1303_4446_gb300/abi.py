@@ -112,6 +112,10 @@ _SIGS = {
     "x2c_ctx_set_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "x2c_ctx_set_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "x2c_ctx_tuning_log": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "x2c_ctx_set_split_variant": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "x2c_query_workspace": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Options), ctypes.c_int32,
+                                           ctypes.POINTER(Layout), ctypes.POINTER(Mats),
+                                           ctypes.POINTER(ctypes.c_size_t)]),
     "x2c_ctx_kernel_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_char_p,
                                             ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
                                             ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]),

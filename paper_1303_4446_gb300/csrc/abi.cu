@@ -547,6 +547,31 @@ x2c_status x2c_ctx_set_timing(x2c_ctx *ctx, int32_t enable) {
   return X2C_OK;
 }
 
+x2c_status x2c_query_workspace(x2c_ctx *ctx, const x2c_options *opt, int32_t n_mol, const x2c_layout *layouts,
+                               const x2c_mats *mols, size_t *bytes) {
+  if (!bytes) return X2C_ERR_ARG;
+  *bytes = 0;
+  if (!ctx || !opt || n_mol < 0) return X2C_ERR_ARG;
+  size_t need = 0;
+  if (n_mol == 0) {  // full X2C of mols[0]
+    if (!mols) return X2C_ERR_ARG;
+    const int nc = opt->two_component ? 4 : 1;
+    x2c_hout h{};
+    static double dummy;
+    for (int q = 0; q < nc; ++q) h.h[q] = &dummy;
+    X2C_TRY(full_build(ctx, opt, mols, &h, nullptr, nullptr, &need));
+  } else {
+    if (!layouts || !mols) return X2C_ERR_ARG;
+    std::vector<x2c_hout> h(n_mol);
+    static double dummy;
+    for (auto &o : h)
+      for (int q = 0; q < 4; ++q) o.h[q] = &dummy;
+    X2C_TRY(dlu_build(ctx, opt, n_mol, layouts, mols, h.data(), nullptr, nullptr, &need));
+  }
+  *bytes = need;
+  return X2C_OK;
+}
+
 x2c_status x2c_ctx_set_autotune(x2c_ctx *ctx, int32_t enable) {
   if (!ctx || (enable != 0 && enable != 1)) return X2C_ERR_ARG;
   ctx->autotune = enable != 0;
@@ -554,6 +579,12 @@ x2c_status x2c_ctx_set_autotune(x2c_ctx *ctx, int32_t enable) {
 }
 
 const char *x2c_ctx_tuning_log(x2c_ctx *ctx) { return ctx ? ctx->tune_log.c_str() : ""; }
+
+x2c_status x2c_ctx_set_split_variant(x2c_ctx *ctx, int32_t variant) {
+  if (!ctx || variant < -1 || variant > 2) return X2C_ERR_ARG;
+  ctx->split_variant = variant;
+  return X2C_OK;
+}
 
 x2c_status x2c_ctx_kernel_times(x2c_ctx *ctx, int32_t max_entries, char *names, double *ms,
                                 int64_t *launches, double *flops, int32_t *n_entries) {

@@ -53,6 +53,7 @@ struct x2c_ctx {
   cudaEvent_t aux_fork = nullptr;
   // autotuner: tile choice per workload shape, chosen by timing the candidates once
   bool autotune = true;
+  int split_variant = -1;  // >= 0: always this candidate (x2c_ctx_set_split_variant)
   std::map<uint64_t, int> tuned;
   std::string tune_log;
   cudaEvent_t tune_ev[2] = {nullptr, nullptr};

@@ -737,7 +737,12 @@ x2c_status x2c_server_create(const x2c_server_options *opt, x2c_server **out) {
          x2c_ctx_create(s->device, &sl.ctx) == X2C_OK && cudaEventCreate(&sl.ev_start) == cudaSuccess &&
          cudaEventCreate(&sl.ev_done) == cudaSuccess &&
          cudaHostAlloc(reinterpret_cast<void **>(&sl.h_status), sizeof(int), cudaHostAllocDefault) == cudaSuccess;
-    if (sl.ctx) sl.ctx->pool = s->pool;
+    if (sl.ctx) {
+      sl.ctx->pool = s->pool;
+      // no timing runs inside the request loop: they would synchronise a slot stream while
+      // the scheduler holds its lock; the slots take the untuned default variant
+      sl.ctx->autotune = false;
+    }
     s->slots.push_back(sl);
   }
   if (ok) {

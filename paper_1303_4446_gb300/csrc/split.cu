@@ -353,15 +353,15 @@ struct Stage1T {
     const int c = nt * kTileM + rloc;
     const bool cv = c < cols1;
     const int rows_p = 2 * nA;
-    int ek[NC];
+    // the column exponents e1 + kexp2 are read twice (L1 hits) instead of held in registers
+    const int *e1p = e1 + p * tra;
     int m = kNoExp;
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
       const int r = c0 + j;
-      ek[j] = r < rows_p ? e1[p * tra + r] + k2p[r] : 0;
       if (r < rows_p && I[j] != 0) {
         const unsigned long long a = I[j] < 0 ? static_cast<unsigned long long>(-I[j]) : static_cast<unsigned long long>(I[j]);
-        m = max(m, 64 - __clzll(static_cast<long long>(a)) + ek[j]);
+        m = max(m, 64 - __clzll(static_cast<long long>(a)) + __ldg(e1p + r) + __ldg(k2p + r));
       }
     }
     red[(quarter * 4 + sub) * 32 + lane] = m;
@@ -390,8 +390,9 @@ struct Stage1T {
         int d0[S], d1[S];
         const int j = g + jj;
         const long long v0 = neg ? -I[j] : I[j], v1 = neg ? -I[j + 1] : I[j + 1];
-        digits<S>((c0 + j) < rows_p ? shift_round(v0, ek[j] - m + 8 * S) : 0, d0);
-        digits<S>((c0 + j + 1) < rows_p ? shift_round(v1, ek[j + 1] - m + 8 * S) : 0, d1);
+        const int r0 = c0 + j, r1 = r0 + 1;
+        digits<S>(r0 < rows_p ? shift_round(v0, __ldg(e1p + r0) + __ldg(k2p + r0) - m + 8 * S) : 0, d0);
+        digits<S>(r1 < rows_p ? shift_round(v1, __ldg(e1p + r1) + __ldg(k2p + r1) - m + 8 * S) : 0, d1);
 #pragma unroll
         for (int s2 = 0; s2 < S; ++s2)
           w[s2][jj >> 1] = static_cast<uint32_t>(__bfloat16_as_ushort(int_to_bf16(d0[s2]))) |
@@ -410,6 +411,16 @@ struct Stage1T {
 // sum_p sign+(l,p) O[(j,p),(i', l^p)] is an integer reduce-scatter over the 4 lanes of a j.
 // Values are staged in shared memory and written with coalesced stores (h_AB rows along j,
 // the mirror h_BA rows along i').  NCQ = number of quaternion parts (4, or 1 spin-free).
+// Per j slot of a stage-2 tile: where its outputs go (h_AB row offA, column offB + j, and the
+// mirror h_BA row offB + j, column offA), built once per tile so that the store loops read
+// shared memory only.
+template <int NCQ>
+struct SlotInfo {
+  double *h[NCQ];  // output parts of the pair's molecule
+  long long ld;
+  int offA, offBj, valid, diag;  // h_AB rows start at offA, its column is offB + j
+};
+
 template <int NCQ>
 struct Stage2Store {
   const PairDesc *pairs;
@@ -417,31 +428,40 @@ struct Stage2Store {
   const int *e2, *eG;
   int rows, nA, nB, S;
   int accumulate;  // add to h instead of writing it (the spin-orbit passes of diagonal pairs)
-  // staging: [part][i' (NT/NCQ)][j (128/NCQ)] doubles, then per-j-slot pair info
-  static int stage_bytes(int NT) { return NT * kTileM * 8 / NCQ + (kTileM / NCQ) * 16; }
+  // staging: [part][i' (NT/NCQ)][j (128/NCQ), padded by one against bank conflicts] doubles,
+  // then the per-j-slot output addresses
+  static constexpr int JT = kTileM / NCQ;
+  static constexpr int JTP = NCQ == 4 ? JT + 1 : JT;  // two-component: padded row stride
+  static int stage_bytes(int NT) { return NT * JTP * 8 + JT * static_cast<int>(sizeof(SlotInfo<NCQ>)) + 16; }
   template <int NC>
   __device__ __forceinline__ void operator()(int mt, int nt, int NT, int rloc, int c0, const long long (&I)[NC],
                                              int lane, uint8_t *stage) const {
-    constexpr int JT = kTileM / NCQ;  // j slots per tile
-    const int IT = NT / NCQ;          // i' slots per tile
+    const int IT = NT / NCQ;  // i' slots per tile
     double *sv = reinterpret_cast<double *>(stage);
-    int4 *slot = reinterpret_cast<int4 *>(stage + static_cast<size_t>(NT) * kTileM * 8 / NCQ);
+    SlotInfo<NCQ> *slot = reinterpret_cast<SlotInfo<NCQ> *>(stage + static_cast<size_t>(NT) * JTP * 8);
     const int r = mt * kTileM + rloc;
     const bool valid = r < rows;
     const int pq = rloc % NCQ;
     const int jl = rloc / NCQ;
     const int E = (valid ? e2[r] : 0) - 8 * (S + 1);
     const int tid = threadIdx.x - 64;
-    if (tid < JT) {  // pair of each j slot: (offA, offB + j, diag, mol), or (-1, ...) if padding
+    if (tid < JT) {
       const int r2 = mt * kTileM + tid * NCQ;
-      int4 info = make_int4(-1, 0, 0, 0);
+      SlotInfo<NCQ> si{};
+      si.valid = 0;
       if (r2 < rows) {
         const int per = NCQ * nB;
         const int pi = r2 / per, j = (r2 - pi * per) / NCQ;
         const PairDesc &P = pairs[pi];
-        info = make_int4(P.offA, P.offB + j, P.diag, P.mol);
+        const MolDesc &m = mols[P.mol];
+        si.valid = 1;
+        si.diag = P.diag;
+        si.ld = m.ld;
+        si.offA = P.offA;
+        si.offBj = P.offB + j;
+        for (int q = 0; q < NCQ; ++q) si.h[q] = m.h[q];
       }
-      slot[tid] = info;
+      slot[tid] = si;
     }
     if (NCQ == 4) {
 #pragma unroll
@@ -483,14 +503,14 @@ struct Stage2Store {
         long long keep = b1 ? keep1 : keep0;
         const long long send = b1 ? keep0 : keep1;
         keep += __shfl_xor_sync(0xffffffffu, send, 2);
-        sv[(pq * IT + il) * JT + jl] = (valid && colv) ? scaled_to_double(keep, E + eG[ip * 4]) : 0.0;
+        sv[(pq * IT + il) * JTP + jl] = (valid && colv) ? scaled_to_double(keep, E + eG[ip * 4]) : 0.0;
       }
     } else {
 #pragma unroll
       for (int t = 0; t < NC; ++t) {
         const int il = c0 + t;
         const int ip = nt * IT + il;
-        sv[il * JT + jl] = (valid && ip < nA) ? scaled_to_double(I[t], E + eG[ip]) : 0.0;
+        sv[il * JTP + jl] = (valid && ip < nA) ? scaled_to_double(I[t], E + eG[ip]) : 0.0;
       }
     }
     (void)lane;
@@ -502,23 +522,23 @@ struct Stage2Store {
     for (int idx = tid; idx < NCQ * IT * JT; idx += nthr) {
       const int jl2 = idx % JT, rest = idx / JT;
       const int il2 = rest % IT, part = rest / IT;
-      const int4 info = slot[jl2];
-      if (info.x < 0 || il2 >= iv) continue;
-      const MolDesc &m = mols[info.w];
-      double *dst = m.h[part] + static_cast<int64_t>(info.x + ip0 + il2) * m.ld + info.y;
-      const double val = sv[(part * IT + il2) * JT + jl2];
+      const SlotInfo<NCQ> &si = slot[jl2];
+      if (!si.valid || il2 >= iv) continue;
+      double *dst = si.h[part] + static_cast<int64_t>(si.offA + ip0 + il2) * si.ld + si.offBj;
+      const double val = sv[(part * IT + il2) * JTP + jl2];
       if (accumulate) *dst += val;
       else *dst = val;
     }
     // mirror h_BA = h_AB+: rows offB + j, contiguous along i'
-    for (int idx = tid; idx < NCQ * IT * JT; idx += nthr) {
-      const int il2 = idx % IT, rest = idx / IT;
-      const int jl2 = rest % JT, part = rest / JT;
-      const int4 info = slot[jl2];
-      if (info.x < 0 || info.z || il2 >= iv || accumulate) continue;
-      const MolDesc &m = mols[info.w];
-      const double v = sv[(part * IT + il2) * JT + jl2];
-      m.h[part][static_cast<int64_t>(info.y) * m.ld + (info.x + ip0 + il2)] = (part == 0) ? v : -v;
+    if (!accumulate) {
+      for (int idx = tid; idx < NCQ * IT * JT; idx += nthr) {
+        const int il2 = idx % IT, rest = idx / IT;
+        const int jl2 = rest % JT, part = rest / JT;
+        const SlotInfo<NCQ> &si = slot[jl2];
+        if (!si.valid || si.diag || il2 >= iv) continue;
+        const double v = sv[(part * IT + il2) * JTP + jl2];
+        si.h[part][static_cast<int64_t>(si.offBj) * si.ld + (si.offA + ip0 + il2)] = (part == 0) ? v : -v;
+      }
     }
     epi_sync();
   }
@@ -1054,12 +1074,16 @@ x2c_status run_tuned(x2c_ctx *ctx, cudaStream_t st, double c, int nc, int so_all
   std::map<std::pair<int, int>, int> shapes;
   for (const auto &P : pairs) shapes[{P.nA, P.nB}] = 1;
   for (auto &kv : shapes) mix(((uint64_t)kv.first.first << 20) | (uint64_t)kv.first.second);
+  if (ctx->split_variant >= 0 && ctx->split_variant < n_choices)  // forced (tests, experiments)
+    return run_choice<S>(ctx->split_variant, ctx, st, c, nc, so_all, pairs, d_mols, ut, hUL, hUS, ar);
   auto it = ctx->tuned.find(key);
   if (it != ctx->tuned.end())
     return run_choice<S>(it->second, ctx, st, c, nc, so_all, pairs, d_mols, ut, hUL, hUS, ar);
   if (!ctx->autotune || n_choices == 1) {
-    ctx->tuned[key] = 0;
-    return run_choice<S>(S <= 5 ? 0 : 1, ctx, st, c, nc, so_all, pairs, d_mols, ut, hUL, hUS, ar);
+    // untuned default: the transposed stage 1 where it exists (fastest on every measured shape)
+    const int def = n_choices == 3 ? 2 : (S <= 5 ? 0 : 1);
+    ctx->tuned[key] = def;
+    return run_choice<S>(def, ctx, st, c, nc, so_all, pairs, d_mols, ut, hUL, hUS, ar);
   }
   for (int i = 0; i < 2; ++i)
     if (!ctx->tune_ev[i]) X2C_TRY_CUDA(ctx, cudaEventCreate(&ctx->tune_ev[i]));

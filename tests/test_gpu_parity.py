@@ -247,3 +247,17 @@ def test_invalid_arguments(ctx):
     assert e.value.code == 1
     with pytest.raises(x.X2CError):
         x.x2c_build_dlu(ctx, m, [0, 30], [3], [m])  # kind index out of range
+
+
+def test_query_workspace(ctx):
+    """x2c_query_workspace sizes a build without running it; larger systems need more."""
+    small = w.silver_cluster(4, "s30")
+    big = w.silver_cluster(13, "s30")
+    ws = []
+    for mol in (small, big):
+        g = dev(w.molecule_inputs(mol, True))
+        gk = dev(w.atomic_inputs(47.0, "s30", True))
+        ws.append(x.x2c_query_workspace(ctx, g, mol.offsets, [0] * mol.natoms, [gk], two_component=True))
+        full = x.x2c_query_workspace(ctx, g, two_component=True, full=True)
+        assert full > 0
+    assert 0 < ws[0] < ws[1]

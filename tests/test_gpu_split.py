@@ -115,6 +115,26 @@ def test_batched_uneven_molecules_split_and_fp64(ctx):
             assert np.abs(hb[0].cpu().numpy() - ref).max() <= tol * np.abs(ref).max()
 
 
+def test_split_variants_give_identical_h(ctx):
+    """Every split-kernel variant (N tiles, transposed stage 1) gives bit-identical h, for
+    both spins and for mixed atom sizes."""
+    mol = w.Molecule(w.fcc_sites(5), np.full(5, 47.0), ["s30", "s48", "s30", "s48", "s48"])
+    idx = [0, 1, 0, 1, 1]
+    for two_c in (False, True):
+        g = dev(w.molecule_inputs(mol, two_c))
+        gk = [dev(w.atomic_inputs(47.0, b, two_c)) for b in ("s30", "s48")]
+        hs = []
+        for v in (0, 1, 2):
+            ctx.set_split_variant(v)
+            hs.append(x.x2c_build_dlu(ctx, g, mol.offsets, idx, gk, two_component=two_c,
+                                      precision=x.PREC_SPLIT_BF16))
+            ctx.status()
+        ctx.set_split_variant(-1)
+        for h in hs[1:]:
+            for a, b in zip(hs[0], h):
+                assert torch.equal(a, b)
+
+
 def test_autotuner_choices_give_identical_h():
     """The tile autotuner times every candidate on the first build of a shape; all candidates
     must give bit-identical h (exact digit products), equal to a context without tuning."""
