@@ -40,7 +40,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # one ncu capture of the Ag55 two-component build (1540 pairs, the same per-pair shapes as
 # Ag309); a launch's traffic is this times its pairs.  Set an entry to None when its kernel
 # changes.
-PROFILED_DRAM_BYTES_PER_PAIR = {}  # (kernel, variant) -> bytes; filled in from the capture below
+PROFILED_DRAM_BYTES_PER_PAIR = {("split_stage1", "trm"): 240.1e3, ("split_stage2", "nt96"): 302.1e3}
 WORKLOADS = {
     "ag309_2c": dict(L=309, basis="s48", two_c=True),
     # 64 uneven spin-free clusters, n ~ U[2, 43], basis s30/s48 50/50, one batched launch
@@ -385,7 +385,8 @@ def serve_stream(srv, reqs, big, kinds, precision, n_slices, t_lead=0.05):
     keys = {(b, tc): 1 + 2 * ("s30", "s48").index(b) + int(tc) for b in ("s30", "s48") for tc in (False, True)}
     pending = []
     lock = threading.Condition()
-    done = {"n": 0, "failed": 0, "wait_ms": [], "service_ms": []}
+    done = {"n": 0, "failed": 0, "wait_ms": [], "service_ms": [], "slowest": []}
+    meta = {}
     h2d = [0]
 
     def reaper():
@@ -403,6 +404,7 @@ def serve_stream(srv, reqs, big, kinds, precision, n_slices, t_lead=0.05):
             else:
                 done["wait_ms"].append((r["t_start"] - r["t_arrival"]) * 1e3)
                 done["service_ms"].append((r["t_end"] - r["t_start"]) * 1e3)
+                done["slowest"].append(((r["t_end"] - r["t_start"]) * 1e3, meta.get(t)))
             srv.release(t)
             done["n"] += 1
 
@@ -426,6 +428,7 @@ def serve_stream(srv, reqs, big, kinds, precision, n_slices, t_lead=0.05):
         # what the server copies: the upper block triangle of T, V, W0 (pairs A <= B) and the
         # same-atom blocks of Wx, Wy, Wz
         h2d[0] += 8 * nb * nb * (3 * L * (L + 1) // 2 + (3 * L if tc else 0))
+        meta[t] = f"Ag{L} {b} {'2c' if tc else 'sf'}"
         with lock:
             pending.append(t)
             lock.notify()
@@ -548,6 +551,7 @@ def run_serving(args, cfg):
                         "latency": "completion (device event) - scheduled arrival",
                         "wait_p50_ms": pct(done["wait_ms"], 50), "wait_p99_ms": pct(done["wait_ms"], 99),
                         "service_p50_ms": pct(done["service_ms"], 50), "service_p99_ms": pct(done["service_ms"], 99),
+                        "slowest_service": [[round(v, 2), k] for v, k in sorted(done["slowest"], key=lambda x: -x[0])[:8]],
                         "split": "wait = device start - scheduled arrival (submission, admission, queueing); "
                                  "service = device start to completion (input copies + build)"},
             "gpu_launches": int(st["kernel_launches"]), "roofline": None,

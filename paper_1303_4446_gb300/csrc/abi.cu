@@ -43,6 +43,62 @@ size_t workspace_after_growth(const x2c_ctx *ctx, size_t bytes) {
   return bytes > ctx->ws_bytes ? bytes + bytes / 8 : ctx->ws_bytes;
 }
 
+x2c_status upload(x2c_ctx *ctx, cudaStream_t st, void *dst, const void *src, size_t bytes) {
+  if (bytes == 0) return X2C_OK;
+  const size_t need = (bytes + 255) & ~static_cast<size_t>(255);
+  auto retire = [&](const x2c_ctx::Staged &f) -> x2c_status {
+    X2C_TRY_CUDA(ctx, cudaEventSynchronize(f.done));
+    ctx->ring_events.push_back(f.done);
+    return X2C_OK;
+  };
+  // drop uploads the device has finished
+  while (!ctx->ring_inflight.empty() && cudaEventQuery(ctx->ring_inflight.front().done) == cudaSuccess) {
+    ctx->ring_events.push_back(ctx->ring_inflight.front().done);
+    ctx->ring_inflight.erase(ctx->ring_inflight.begin());
+  }
+  cudaGetLastError();  // cudaErrorNotReady from the query above
+  if (need > ctx->ring_cap) {  // grow: wait for everything staged in the old buffer
+    for (auto &f : ctx->ring_inflight) X2C_TRY(retire(f));
+    ctx->ring_inflight.clear();
+    if (ctx->ring) cudaFreeHost(ctx->ring);
+    ctx->ring = nullptr;
+    ctx->ring_cap = 0;
+    const size_t cap = std::max<size_t>(need, 16u << 20);
+    cudaError_t e = cudaHostAlloc(reinterpret_cast<void **>(&ctx->ring), cap, cudaHostAllocDefault);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      ctx->ring = nullptr;
+      ctx->last_error = std::string("pinned staging allocation: ") + cudaGetErrorString(e);
+      return X2C_ERR_NOMEM;
+    }
+    ctx->ring_cap = cap;
+    ctx->ring_head = 0;
+  }
+  size_t start = ctx->ring_head;
+  if (start + need > ctx->ring_cap) start = 0;  // wrap around
+  const size_t end = start + need;
+  // the region may still be the source of an older upload the device has not performed yet
+  while (!ctx->ring_inflight.empty()) {
+    const auto &f = ctx->ring_inflight.front();
+    if (!(f.start < end && start < f.end)) break;
+    X2C_TRY(retire(f));
+    ctx->ring_inflight.erase(ctx->ring_inflight.begin());
+  }
+  std::memcpy(ctx->ring + start, src, bytes);
+  X2C_TRY_CUDA(ctx, cudaMemcpyAsync(dst, ctx->ring + start, bytes, cudaMemcpyHostToDevice, st));
+  cudaEvent_t ev;
+  if (!ctx->ring_events.empty()) {
+    ev = ctx->ring_events.back();
+    ctx->ring_events.pop_back();
+  } else {
+    X2C_TRY_CUDA(ctx, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  }
+  X2C_TRY_CUDA(ctx, cudaEventRecord(ev, st));
+  ctx->ring_inflight.push_back({start, end, ev});
+  ctx->ring_head = end;
+  return X2C_OK;
+}
+
 x2c_status ensure_aux_streams(x2c_ctx *ctx, int count) {
   if (!ctx->aux_fork) X2C_TRY_CUDA(ctx, cudaEventCreateWithFlags(&ctx->aux_fork, cudaEventDisableTiming));
   while ((int)ctx->aux.size() < count) {
@@ -165,7 +221,7 @@ x2c_status run_plan(x2c_ctx *ctx, const x2c_options *opt, BuildPlan &plan, cudaS
     }
     InputDesc *dd = reinterpret_cast<InputDesc *>(ar.take_bytes(nb * sizeof(InputDesc)));
     if (!dd) return X2C_ERR_NOMEM;
-    X2C_TRY_CUDA(ctx, cudaMemcpyAsync(dd, hd.data(), nb * sizeof(InputDesc), cudaMemcpyHostToDevice, st));
+    X2C_TRY(upload(ctx, st, dd, hd.data(), nb * sizeof(InputDesc)));
     ddescs.push_back(dd);
     plan.credited += nb * credited_solve_flops(n, nc);
   }
@@ -210,10 +266,9 @@ x2c_status run_plan(x2c_ctx *ctx, const x2c_options *opt, BuildPlan &plan, cudaS
   if (UL_out) *UL_out = hUL;
   if (US_out) *US_out = hUS;
   if (plan.pairs.empty()) return X2C_OK;
-  X2C_TRY_CUDA(ctx, cudaMemcpyAsync(dUL, hUL.data(), np * sizeof(double *), cudaMemcpyHostToDevice, st));
-  X2C_TRY_CUDA(ctx, cudaMemcpyAsync(dUS, hUS.data(), np * sizeof(double *), cudaMemcpyHostToDevice, st));
-  X2C_TRY_CUDA(ctx, cudaMemcpyAsync(dmols, plan.mols.data(), plan.mols.size() * sizeof(MolDesc),
-                                    cudaMemcpyHostToDevice, st));
+  X2C_TRY(upload(ctx, st, dUL, hUL.data(), np * sizeof(double *)));
+  X2C_TRY(upload(ctx, st, dUS, hUS.data(), np * sizeof(double *)));
+  X2C_TRY(upload(ctx, st, dmols, plan.mols.data(), plan.mols.size() * sizeof(MolDesc)));
   UTable ut{dUL, dUS};
   const int so_all = (nc == 4 && !opt->so_same_atom_only) ? 1 : 0;
   for (const auto &P : plan.pairs) plan.credited += credited_pair_flops(P.nA, P.nB, nc, P.diag, so_all);
@@ -509,6 +564,9 @@ x2c_status x2c_ctx_destroy(x2c_ctx *ctx) {
   for (auto e : ctx->ev_pool) cudaEventDestroy(e);
   for (auto e : ctx->tune_ev)
     if (e) cudaEventDestroy(e);
+  for (auto &f : ctx->ring_inflight) cudaEventDestroy(f.done);
+  for (auto e : ctx->ring_events) cudaEventDestroy(e);
+  if (ctx->ring) cudaFreeHost(ctx->ring);
   for (auto s : ctx->aux) cudaStreamDestroy(s);
   for (auto e : ctx->aux_join) cudaEventDestroy(e);
   if (ctx->aux_fork) cudaEventDestroy(ctx->aux_fork);

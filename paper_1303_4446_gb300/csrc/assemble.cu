@@ -244,8 +244,7 @@ x2c_status assemble_pairs_fp64(x2c_ctx *ctx, cudaStream_t st, double c, int nc, 
   PairDesc *d_pairs = reinterpret_cast<PairDesc *>(ar.take_bytes(pairs.size() * sizeof(PairDesc)));
   double *R = ar.take(rmax);
   if (!d_pairs || !R) return X2C_ERR_NOMEM;
-  X2C_TRY_CUDA(ctx, cudaMemcpyAsync(d_pairs, pairs.data(), pairs.size() * sizeof(PairDesc),
-                                    cudaMemcpyHostToDevice, st));
+  X2C_TRY(upload(ctx, st, d_pairs, pairs.data(), pairs.size() * sizeof(PairDesc)));
   // Pairs needing the spin-orbit middle term: all pairs, or only A == B.
   std::vector<PairDesc> so_pairs;
   for (auto &ch : chunks) {
@@ -266,8 +265,7 @@ x2c_status assemble_pairs_fp64(x2c_ctx *ctx, cudaStream_t st, double c, int nc, 
         if (!diag.empty()) {
           PairDesc *dd = reinterpret_cast<PairDesc *>(ar.take_bytes(diag.size() * sizeof(PairDesc)));
           if (!dd) return X2C_ERR_NOMEM;
-          X2C_TRY_CUDA(ctx, cudaMemcpyAsync(dd, diag.data(), diag.size() * sizeof(PairDesc),
-                                            cudaMemcpyHostToDevice, st));
+          X2C_TRY(upload(ctx, st, dd, diag.data(), diag.size() * sizeof(PairDesc)));
           X2C_TRY((gemm_f64<TileStage2q>(ctx, st, (int)diag.size(), 4 * max_n, max_n,
                                          SoLeftOp{dd, d_mols, inv4c2}, UStackOp{dd, ut},
                                          AccumulateRS{dd, R}, SoDims{dd}, "dlu_spin_orbit")));

@@ -51,9 +51,19 @@ struct x2c_ctx {
   std::vector<cudaStream_t> aux;
   std::vector<cudaEvent_t> aux_join;
   cudaEvent_t aux_fork = nullptr;
+  // pinned staging ring for the small descriptor uploads (see x2c::upload)
+  struct Staged {
+    size_t start, end;
+    cudaEvent_t done;
+  };
+  char *ring = nullptr;
+  size_t ring_cap = 0, ring_head = 0;
+  std::vector<Staged> ring_inflight;  // oldest first
+  std::vector<cudaEvent_t> ring_events;
   // autotuner: tile choice per workload shape, chosen by timing the candidates once
   bool autotune = true;
   int split_variant = -1;  // >= 0: always this candidate (x2c_ctx_set_split_variant)
+  int cta_cap = 0;         // > 0: the persistent split kernels use at most this many CTAs
   std::map<uint64_t, int> tuned;
   std::string tune_log;
   cudaEvent_t tune_ev[2] = {nullptr, nullptr};
@@ -163,6 +173,11 @@ inline size_t arena_doubles(size_t n) { return ((n * sizeof(double) + 255) / 256
 // Grow the context workspace to at least `bytes` (synchronises the device when it grows,
 // unless the context has a pool: then the growth is stream-ordered on `st`).
 x2c_status ensure_workspace(x2c_ctx *ctx, size_t bytes, Arena *out, cudaStream_t st);
+// Copy `bytes` of host memory to the device on `st` through the context's pinned staging
+// ring, so that the call returns at once: cudaMemcpyAsync from pageable memory would first
+// wait for all work already queued on the stream.  The host data may be reused on return.
+x2c_status upload(x2c_ctx *ctx, cudaStream_t st, void *dst, const void *src, size_t bytes);
+
 // Auxiliary streams of the context (created on first use, at most kMaxAuxStreams).
 constexpr int kMaxAuxStreams = 4;
 x2c_status ensure_aux_streams(x2c_ctx *ctx, int count);

@@ -25,6 +25,8 @@ using x2c::serve::Candidate;
 using Clock = std::chrono::steady_clock;
 
 constexpr uint64_t kDefaultBudget = 150ull * 1000 * 1000 * 1000;
+constexpr size_t kLargePairs = 2000;  // builds above this many pair blocks count as large
+constexpr int kFreeSMs = 32;          // SMs a large build leaves to the other slots
 
 struct CacheEntry {
   std::tuple<uint64_t, int, int, uint64_t> key;  // kind key, n, nc, bits of c
@@ -71,7 +73,9 @@ struct Request {
 using ReqPtr = std::shared_ptr<Request>;
 
 struct Slot {
-  cudaStream_t st = nullptr;
+  cudaStream_t st = nullptr;      // normal priority: large builds
+  cudaStream_t st_hi = nullptr;   // highest priority: small builds
+  cudaStream_t cur = nullptr;     // the stream of the batch in flight
   x2c_ctx *ctx = nullptr;
   cudaEvent_t ev_start = nullptr, ev_done = nullptr;
   int *h_status = nullptr;  // pinned: the context's device status word after the build
@@ -102,6 +106,7 @@ struct x2c_server {
   Clock::time_point t0;
   double t_ref = 0;  // server-clock time of ev_ref
   x2c_ctx *planner = nullptr;  // dry runs only (under the mutex)
+  int sms_ = 152;
   std::vector<Slot> slots;
 
   std::mutex mu;
@@ -345,7 +350,18 @@ void x2c_server::launch(int si, std::vector<ReqPtr> &batch) {
   sl.host_fail = X2C_OK;
   sl.busy = true;
   sl.reserved = 0;
-  cudaStream_t s = sl.st;
+  // Small builds run on the slot's high-priority stream, so that their CTAs are scheduled
+  // ahead of the remaining CTAs of large builds on other slots; large builds leave some SMs
+  // free of their persistent tensor-core kernels.
+  size_t batch_pairs = 0;
+  for (auto &rp : batch) {
+    const size_t L = rp->offsets.empty() ? 1 : rp->offsets.size() - 1;
+    batch_pairs += L * (L + 1) / 2;
+  }
+  const bool large = batch_pairs > kLargePairs;
+  cudaStream_t s = large ? sl.st : sl.st_hi;
+  sl.cur = s;
+  sl.ctx->cta_cap = large ? std::max(1, sms_ - kFreeSMs) : 0;
   const ReqPtr &h = batch[0];
   const x2c_options opt = h->rq.opt;
   const int nc = h->nc;
@@ -594,12 +610,12 @@ void x2c_server::finish(int si, cudaError_t e) {
     r.t_start = t_s;
     r.t_end = t_e;
     if (r.in_slab) {
-      cudaFreeAsync(r.in_slab, sl.st);
+      cudaFreeAsync(r.in_slab, sl.cur);
       r.in_slab = nullptr;
     }
     give(r.in_bytes);
     if (!r.out_kept || r.status != X2C_OK) {
-      if (r.out_dev) cudaFreeAsync(r.out_dev, sl.st);
+      if (r.out_dev) cudaFreeAsync(r.out_dev, sl.cur);
       r.out_dev = nullptr;
       give(r.out_bytes);
       r.out_kept = false;
@@ -607,7 +623,7 @@ void x2c_server::finish(int si, cudaError_t e) {
     for (auto &d : r.deps) {
       d->refs--;
       if (!d->in_map && d->refs == 0 && d->U) {
-        cudaFreeAsync(d->U, sl.st);
+        cudaFreeAsync(d->U, sl.cur);
         cudaEventDestroy(d->ready);
         d->U = nullptr;
         give(d->bytes);
@@ -728,12 +744,20 @@ x2c_status x2c_server_create(const x2c_server_options *opt, x2c_server **out) {
   ok = ok && cudaMemPoolCreate(&s->pool, &props) == cudaSuccess;
   uint64_t keep = UINT64_MAX;
   ok = ok && cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep) == cudaSuccess;
+  // no hidden cross-slot ordering: memory freed on one slot's stream is not handed to another
+  // slot's stream by making that stream wait (the pool grows instead, within the budget)
+  int no = 0;
+  ok = ok && cudaMemPoolSetAttribute(s->pool, cudaMemPoolReuseAllowInternalDependencies, &no) == cudaSuccess;
   ok = ok && cudaStreamCreateWithFlags(&s->misc, cudaStreamNonBlocking) == cudaSuccess;
+  int prio_lo = 0, prio_hi = 0;
+  ok = ok && cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi) == cudaSuccess;
+  ok = ok && cudaDeviceGetAttribute(&s->sms_, cudaDevAttrMultiProcessorCount, s->device) == cudaSuccess;
   ok = ok && cudaEventCreate(&s->ev_ref) == cudaSuccess;
   ok = ok && x2c_ctx_create(s->device, &s->planner) == X2C_OK;
   for (int i = 0; ok && i < slots; ++i) {
     Slot sl;
     ok = cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaStreamCreateWithPriority(&sl.st_hi, cudaStreamNonBlocking, prio_hi) == cudaSuccess &&
          x2c_ctx_create(s->device, &sl.ctx) == X2C_OK && cudaEventCreate(&sl.ev_start) == cudaSuccess &&
          cudaEventCreate(&sl.ev_done) == cudaSuccess &&
          cudaHostAlloc(reinterpret_cast<void **>(&sl.h_status), sizeof(int), cudaHostAllocDefault) == cudaSuccess;
@@ -784,6 +808,7 @@ x2c_status x2c_server_destroy(x2c_server *s) {
     }
   for (auto &sl : s->slots) {
     if (sl.st) cudaStreamSynchronize(sl.st);
+    if (sl.st_hi) cudaStreamSynchronize(sl.st_hi);
     if (sl.ctx && sl.ctx->ws) {
       cudaFreeAsync(sl.ctx->ws, sl.st ? sl.st : s->misc);
       sl.ctx->ws = nullptr;
@@ -797,6 +822,7 @@ x2c_status x2c_server_destroy(x2c_server *s) {
     if (sl.ev_done) cudaEventDestroy(sl.ev_done);
     if (sl.h_status) cudaFreeHost(sl.h_status);
     if (sl.st) cudaStreamDestroy(sl.st);
+    if (sl.st_hi) cudaStreamDestroy(sl.st_hi);
   }
   if (s->planner) x2c_ctx_destroy(s->planner);
   if (s->ev_ref) cudaEventDestroy(s->ev_ref);

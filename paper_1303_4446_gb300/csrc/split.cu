@@ -436,7 +436,8 @@ struct Stage2Store {
   template <int NC>
   __device__ __forceinline__ void operator()(int mt, int nt, int NT, int rloc, int c0, const long long (&I)[NC],
                                              int lane, uint8_t *stage) const {
-    const int IT = NT / NCQ;  // i' slots per tile
+    constexpr int IT = 4 * NC / NCQ;  // i' slots per tile (NT = 4 NC columns: compile-time)
+    (void)NT;
     double *sv = reinterpret_cast<double *>(stage);
     SlotInfo<NCQ> *slot = reinterpret_cast<SlotInfo<NCQ> *>(stage + static_cast<size_t>(NT) * JTP * 8);
     const int r = mt * kTileM + rloc;
@@ -809,6 +810,7 @@ struct Runner {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (ctx->cta_cap > 0) sms = std::min(sms, ctx->cta_cap);
     const int per_n = std::max(1, std::min(m_tiles, std::max(1, sms / n_tiles)));
     dim3 grid(n_tiles, per_n);
     tbegin(ctx, st);
@@ -842,6 +844,7 @@ struct Runner {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (ctx->cta_cap > 0) sms = std::min(sms, ctx->cta_cap);
     const int per_n = std::max(1, std::min(m_tiles, std::max(1, sms / n_tiles)));
     dim3 grid(n_tiles, per_n);
     tbegin(ctx, st);
@@ -957,7 +960,7 @@ struct Runner {
         __nv_bfloat16 *A2 = reinterpret_cast<__nv_bfloat16 *>(a1.take_bytes((size_t)rows2p * KP2 * S * 2));
         int *e2 = reinterpret_cast<int *>(a1.take_bytes((size_t)rows2p * 4));
         if (!dp || !A1 || !e1 || !A2 || !e2) return X2C_ERR_NOMEM;
-        X2C_TRY_CUDA(ctx, cudaMemcpyAsync(dp, cls.data() + c0, np * sizeof(PairDesc), cudaMemcpyHostToDevice, st));
+        X2C_TRY(upload(ctx, st, dp, cls.data() + c0, np * sizeof(PairDesc)));
         if (rows2p > rows2) {  // the stage-2 tail rows are never written by the fused epilogue
           const size_t tail0 = (size_t)(rows2p - kTileM) * KP2 * S * 2;
           X2C_TRY_CUDA(ctx, cudaMemsetAsync(reinterpret_cast<char *>(A2) + tail0, 0, (size_t)kTileM * KP2 * S * 2, st));
@@ -992,7 +995,7 @@ struct Runner {
             Arena a2 = a1;
             PairDesc *ds = reinterpret_cast<PairDesc *>(a2.take_bytes(ns * sizeof(PairDesc)));
             if (!ds) return X2C_ERR_NOMEM;
-            X2C_TRY_CUDA(ctx, cudaMemcpyAsync(ds, so.data(), ns * sizeof(PairDesc), cudaMemcpyHostToDevice, st));
+            X2C_TRY(upload(ctx, st, ds, so.data(), ns * sizeof(PairDesc)));
             const int srows1 = ns * TRA, srows2 = ns * cols1;
             const int srows2p = (srows2 + kTileM - 1) / kTileM * kTileM;
             if (srows2p > srows2) {
@@ -1025,7 +1028,7 @@ struct Runner {
             const int64_t per = (int64_t)4 * nA * nB;
             double *T1 = a2.take(so.size() * per);
             if (!ds || !T1) return X2C_ERR_NOMEM;
-            X2C_TRY_CUDA(ctx, cudaMemcpyAsync(ds, so.data(), so.size() * sizeof(PairDesc), cudaMemcpyHostToDevice, st));
+            X2C_TRY(upload(ctx, st, ds, so.data(), so.size() * sizeof(PairDesc)));
             X2C_TRY((gemm_f64<TileSo>(ctx, st, (int)so.size(), 4 * nA, nB, SoLeftC{ds, d_mols, inv4c2},
                                       UsStackC{ds, ut}, StoreT1{T1, per, nB}, SoDimsC{ds}, "split_spin_orbit")));
             X2C_TRY((gemm_f64<TileSo>(ctx, st, (int)so.size(), 4 * nA, nB, UsAdjLeft{ds, ut}, T1Op{T1, per, nB},
