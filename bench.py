@@ -244,17 +244,18 @@ def run_batched(args, cfg):
     lays = [(m.offsets, [order.index(b) for b in m.basis], gk) for m in mols]
     outs = [[torch.empty((m.nbf, m.nbf), dtype=torch.float64, device=dev)] for m in mols]
     ctx = x.Context(local)
+    ctx.set_graphs(bool(args.graphs))
     prec = x.PREC_SPLIT_BF16 if args.precision == "split" else x.PREC_FP64
     stream = torch.cuda.current_stream(dev)
 
     def build():
         x.x2c_build_dlu_batched(ctx, gs, lays, precision=prec, n_slices=args.slices, outs=outs, stream=stream)
 
+    # with graphs the warm-up's second build captures the step the timed region replays
     for _ in range(args.warmup):
         build()
     ctx.status(stream)
     counters = ctx.counters()
-    ctx.set_timing(True)
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
@@ -265,8 +266,7 @@ def run_batched(args, cfg):
         torch.cuda.synchronize()
     ctx.status(stream)
     ms_step = ev0.elapsed_time(ev1) / args.steps
-    ktimes = ctx.kernel_times(with_flops=True)
-    ctx.set_timing(False)
+    ktimes = kernel_pass(ctx, build, args.steps, stream)
     credited = counters["credited_flops"]
     n_mol = len(mols)
     dom_name, (dom_ms, dom_l, lib_flops) = max(ktimes.items(), key=lambda kv: kv[1][0])
@@ -301,7 +301,7 @@ def run_batched(args, cfg):
             "clocks": clk.summary(),
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in sorted(ktimes.items(), key=lambda kv: -kv[1][0])},
             "kernel_launches_per_step": {k: v[1] // args.steps for k, v in ktimes.items()},
-            "input_generation_s": t_gen}
+            "graphs": ctx.graph_stats(), "kernel_timing": KERNEL_TIMING, "input_generation_s": t_gen}
     if not args.no_e2e:
         pin = [{k: torch.from_numpy(v).pin_memory() for k, v in m.items()} for m in ms]
         hpin = [torch.empty((m.nbf, m.nbf), dtype=torch.float64).pin_memory() for m in mols]
@@ -335,6 +335,27 @@ def run_batched(args, cfg):
                                 "sample": f"dense oracle DLU of the first {done} of {n_mol} molecules ({dt:.1f} s)"}
     ctx.close()
     print(json.dumps(line), flush=True)
+
+
+KERNEL_TIMING = ("kernel_ms_per_step and the roofline's launch times: a second pass of the same steps with "
+                 "a CUDA event pair around every launch; value: the timed region without them")
+
+
+def kernel_pass(ctx, build, steps, stream):
+    """Per-kernel device times of `steps` more builds, each launch bracketed by CUDA events on
+    its own stream: {name: (ms, launches, library flops)}.  Run after the timed region, which
+    has no per-launch events (on small builds they cost up to a third of the step)."""
+    ctx.set_timing(True)
+    for _ in range(2):  # with graphs: an eager build, then the capture of the instrumented step
+        build()
+    ctx.status(stream)
+    ctx.set_timing(True)  # drops those two builds' times
+    for _ in range(steps):
+        build()
+    ctx.status(stream)
+    kt = ctx.kernel_times(with_flops=True)
+    ctx.set_timing(False)
+    return kt
 
 
 def max_over_ranks(value, dist=None, device="cpu"):
@@ -595,6 +616,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=2,
                     help="split runs: also time this many plain FP64 builds and compare h")
     ap.add_argument("--slices", type=int, default=0)
+    ap.add_argument("--graphs", type=int, default=1, choices=[0, 1],
+                    help="replay the build step from a captured CUDA graph (1) or enqueue it eagerly (0)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
@@ -646,6 +669,7 @@ def main():
     N = mol.nbf
     out = [torch.empty((N, N), dtype=torch.float64, device=dev) for _ in range(nc)]
     ctx = x.Context(local)
+    ctx.set_graphs(bool(args.graphs))
     prec = x.PREC_SPLIT_BF16 if args.precision == "split" else x.PREC_FP64
     stream = torch.cuda.current_stream(dev)
     kinds = [0] * mol.natoms
@@ -655,11 +679,11 @@ def main():
         x.x2c_build_dlu(ctx, g, mol.offsets, kinds, [gk], two_component=two_c, precision=prec, dlu_potential=dlu_pot,
                         n_slices=args.slices, out=out, stream=stream)
 
+    # with graphs the warm-up's second build captures the step the timed region replays
     for _ in range(args.warmup):
         build()
     ctx.status(stream)
     counters = ctx.counters()
-    ctx.set_timing(True)
     torch.cuda.synchronize()
     barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -672,8 +696,7 @@ def main():
     barrier()
     ctx.status(stream)
     ms = ev0.elapsed_time(ev1) / args.steps
-    ktimes = ctx.kernel_times(with_flops=True)
-    ctx.set_timing(False)
+    ktimes = kernel_pass(ctx, build, args.steps, stream)
     ms_max = max_over_ranks(ms, dist, dev)
     clocks = clk.summary()
     credited = counters["credited_flops"]
@@ -738,7 +761,7 @@ def main():
             "roofline": roof, "clocks": clocks,
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in sorted(ktimes.items(), key=lambda kv: -kv[1][0])},
             "autotune": ctx.tuning_log().strip().splitlines(),
-            "input_generation_s": t_gen}
+            "graphs": ctx.graph_stats(), "kernel_timing": KERNEL_TIMING, "input_generation_s": t_gen}
 
     if args.precision == "split" and args.fp64_steps > 0:
         # the plain FP64 path on the same inputs: its rate, and the split path's error in h

@@ -66,6 +66,13 @@ typedef enum {
                                  molecular matrices (Eq. 43 read literally); one solve per atom */
 } x2c_dlu_potential;
 
+typedef enum {
+  X2C_LOCAL_DLU = 0,  /* every pair block h_AB from the atomic transforms (Eq. 42 in Eq. 8) */
+  X2C_LOCAL_DLH = 1   /* diagonal local Hamiltonian (Sec. III.A): only the same-atom blocks
+                         h_AA are transformed (as in DLU); every atom-other-atom block is the
+                         non-relativistic T_AB + V_AB (spin parts zero) */
+} x2c_local_approx;
+
 typedef struct {
   double c;                  /* speed of light (a.u.); <= 0 selects 137.035999 */
   int32_t two_component;     /* 0 = scalar (spin-free), 1 = two-component with Wx, Wy, Wz */
@@ -74,7 +81,8 @@ typedef struct {
   int32_t so_same_atom_only; /* 1: Wx, Wy, Wz vanish outside same-atom blocks, so DLU reads
                                 only those blocks and skips the rest (two-component only) */
   int32_t n_slices;          /* split precision: BF16 slices per operand, 0 = default (5) */
-  int32_t reserved[3];       /* must be zero */
+  int32_t local_approx;      /* x2c_local_approx of the DLU calls (ignored by full X2C) */
+  int32_t reserved[2];       /* must be zero */
 } x2c_options;
 
 typedef struct {
@@ -151,6 +159,29 @@ x2c_status x2c_build_dlu_batched(x2c_ctx *ctx, const x2c_options *opt, int32_t n
 x2c_status x2c_build_dlu_with_transforms(x2c_ctx *ctx, const x2c_options *opt, const x2c_layout *layout,
                                          const x2c_uout *kind_U, const x2c_mats *mol, const x2c_hout *h,
                                          void *stream);
+
+/* Picture-change transformation of a one-electron property operator (Sec. II: the
+ * decoupling transforms are kept for this): for an operator with no large-small coupling
+ * (P^LS = 0, e.g. a multiplicative potential such as an electric field gradient or a contact
+ * density) whose large- and small-component matrices in the primitive basis are P^LL and
+ * P^SS, the two-component operator is
+ *     P2c = U^L+ P^LL U^L + U^S+ P^SS U^S      (Eq. 8 with the property in place of D).
+ * U^L, U^S: block-diagonal over the layout's atoms from kind_U (as in
+ * x2c_build_dlu_with_transforms; DLU, Eq. 42), or the full-X2C transforms of
+ * x2c_build_full(want_U) with a one-atom layout spanning the basis.  P^SS is quaternion-real
+ * like W (Eq. 5): SS[0] symmetric, SS[1..3] antisymmetric spin parts (two-component; NULL
+ * for a spin-free operator); P^LL is spin-free.  out: the quaternion parts of P2c (as h).
+ * opt->c is ignored (the transforms carry it); precision, two_component and
+ * so_same_atom_only apply as in the DLU calls (with so_same_atom_only = 1 the SS spin parts
+ * are read on same-atom blocks only).  Device matrices, n x n, leading dimension n. */
+typedef struct {
+  int32_t n;
+  const double *LL;     /* n x n symmetric */
+  const double *SS[4];  /* SS[0] n x n symmetric; SS[1..3] antisymmetric or NULL */
+} x2c_property;
+x2c_status x2c_picture_change(x2c_ctx *ctx, const x2c_options *opt, const x2c_layout *layout,
+                              const x2c_uout *kind_U, const x2c_property *P, const x2c_hout *out,
+                              void *stream);
 
 /* Atomic (or any) decoupling transforms U^L, U^S of n_problems independent input sets in
  * one batched solve (the matrix function of Eq. 43).  inputs, U: HOST arrays. */
@@ -241,6 +272,28 @@ const char *x2c_ctx_tuning_log(x2c_ctx *ctx);
  * autotuner off and no forced variant the default is 2 where it applies, else 0.  All
  * variants give bit-identical h. */
 x2c_status x2c_ctx_set_split_variant(x2c_ctx *ctx, int32_t variant);
+
+/* CUDA-graph replay of repeated builds (off by default).  With enable = 1, a build call
+ * (x2c_build_full, x2c_build_dlu, x2c_build_dlu_batched, x2c_build_dlu_with_transforms,
+ * x2c_atomic_transforms, x2c_build_dlu_host) whose launch plan equals that of an earlier
+ * call on this context -- the same options, sizes and layouts, the same input and output
+ * pointers, the same kernel choices -- is not enqueued kernel by kernel: the second such
+ * call captures its work into a CUDA graph (stream capture on a private stream of the
+ * context, with the autotuner's choice from the first call) and launches it on the
+ * caller's stream, and every later one launches that graph again.  The matrices are read
+ * when the graph runs, so their contents may change between calls; a changed pointer makes
+ * a new plan.  Per-kernel timing (x2c_ctx_set_timing) sees inside replays.  Graphs are kept
+ * for the 16 most recently used plans and dropped when the workspace grows; enable = 0
+ * drops them (and waits for the device).  Counters and x2c_ctx_counters() report a replayed
+ * call like an eager one. */
+x2c_status x2c_ctx_set_graphs(x2c_ctx *ctx, int32_t enable);
+typedef struct {
+  int64_t captures;       /* graphs captured on this context */
+  int64_t replays;        /* build calls served by launching a captured graph */
+  int32_t cached;         /* graphs held now */
+  int32_t last_replayed;  /* 1 if the last build call launched a captured graph */
+} x2c_graph_stats;
+x2c_status x2c_ctx_graph_stats(x2c_ctx *ctx, x2c_graph_stats *out);
 x2c_status x2c_ctx_kernel_times(x2c_ctx *ctx, int32_t max_entries, char *names, double *ms,
                                 int64_t *launches, double *flops, int32_t *n_entries);
 

@@ -15,6 +15,8 @@ from .x2c import (  # noqa: F401
     spinor_inputs,
     x2c_full,
     x2c_dlu,
+    x2c_dlh,
+    picture_change,
     dlu_atomic_transforms,
     dlu_pair_block,
     quaternion_parts,

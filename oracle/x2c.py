@@ -17,6 +17,8 @@ those of the paper (Peng, Middendorf, Weigend, Reiher, J. Chem. Phys. 138, 18410
            U^S = X U^L  (non-orthogonal form)                         (Sec. II.A)
 * Eqs. 42-43  DLU: U^{L,S} = direct sum of atomic blocks U^{L,S}_AA computed by the
            same matrix function from atomic inputs, then Eq. 8      (Sec. III.A)
+* DLH      relativistic same-atom blocks only, T + V elsewhere        (Sec. III.A)
+* picture change of a property:  U^L+ P^LL U^L + U^S+ P^SS U^S        (Sec. II, Eq. 8)
 
 No blocking, fusion or reordering beyond these definitions; LAPACK (via scipy) does the
 generalised Hermitian eigenproblem and the linear solves.
@@ -169,6 +171,33 @@ def x2c_dlu(m_mol: dict, offsets, atomic_per_atom=None, c: float = C_LIGHT):
     US = _blockdiag_spinor([u[1] for u in U], offsets, two_c)
     S, T, V, W = spinor_inputs(m_mol)
     return dict(h=_utrans(UL, US, V, T, W, c), UL=UL, US=US)
+
+
+def x2c_dlh(m_mol: dict, offsets, atomic_per_atom=None, c: float = C_LIGHT):
+    """Diagonal local approximation to the Hamiltonian, DLH (Sec. III.A): only the
+    same-atom blocks h_AA are relativistically transformed (Eq. 8 with the atomic U_AA of
+    Eq. 43, as in DLU); every atom-other-atom block is the non-relativistic T_AB + V_AB, with
+    no spin-dependent part.  Written as: the DLU h, with the atom-other-atom blocks replaced
+    by those of T + V (spinor form for two-component)."""
+    two_c = "Wx" in m_mol
+    h = x2c_dlu(m_mol, offsets, atomic_per_atom, c)["h"]
+    S, T, V, W = spinor_inputs(m_mol)
+    N = int(offsets[-1])
+    atom = np.repeat(np.arange(len(offsets) - 1), np.diff(np.asarray(offsets)))
+    same = atom[:, None] == atom[None, :]
+    if two_c:
+        same = np.kron(np.ones((2, 2), dtype=bool), same)
+    assert same.shape == h.shape == (N * (2 if two_c else 1),) * 2
+    return np.where(same, h, T + V)
+
+
+def picture_change(UL, US, PLL, PSS):
+    """Picture-change transformation of a one-electron property operator without
+    large-small coupling (Sec. II: the reason the decoupling transforms are kept):
+    P2c = U^L+ P^LL U^L + U^S+ P^SS U^S, i.e. Eq. 8 with [[P^LL, 0], [0, P^SS]] in place of
+    the Dirac matrix.  All matrices in one representation (real N x N, or the spin-blocked
+    complex 2N x 2N of spinor_inputs)."""
+    return UL.conj().T @ PLL @ UL + US.conj().T @ PSS @ US
 
 
 def dlu_pair_block(blocks: dict, ULa, USa, ULb, USb, c: float = C_LIGHT):

@@ -10,7 +10,8 @@ import ctypes
 import numpy as np
 
 from . import abi
-from .abi import DLU_FREE_ATOM, DLU_MOLECULAR_BLOCK, PREC_FP64, PREC_SPLIT_BF16, X2CError  # noqa: F401
+from .abi import (DLU_FREE_ATOM, DLU_MOLECULAR_BLOCK, LOCAL_DLH, LOCAL_DLU, PREC_FP64,  # noqa: F401
+                  PREC_SPLIT_BF16, X2CError)
 
 C_LIGHT = 137.035999
 _MAT_KEYS = ("S", "T", "V", "W0", "Wx", "Wy", "Wz")
@@ -58,6 +59,17 @@ class Context:
         """x2c_ctx_set_split_variant: force a split-kernel candidate (-1 = automatic)."""
         abi.check(self.lib.x2c_ctx_set_split_variant(self.handle, int(variant)), "x2c_ctx_set_split_variant")
 
+    def set_graphs(self, enable: bool):
+        """x2c_ctx_set_graphs: capture a build the second time its launch plan is seen and
+        replay the CUDA graph on every later identical call."""
+        abi.check(self.lib.x2c_ctx_set_graphs(self.handle, int(bool(enable))), "x2c_ctx_set_graphs")
+
+    def graph_stats(self):
+        """x2c_ctx_graph_stats: graphs captured, builds replayed, graphs held, last call replayed."""
+        g = abi.GraphStats()
+        abi.check(self.lib.x2c_ctx_graph_stats(self.handle, ctypes.byref(g)), "x2c_ctx_graph_stats")
+        return dict(captures=g.captures, replays=g.replays, cached=g.cached, last_replayed=bool(g.last_replayed))
+
     def tuning_log(self) -> str:
         """x2c_ctx_tuning_log: the autotuner's decisions, one line each."""
         return self.lib.x2c_ctx_tuning_log(self.handle).decode()
@@ -96,8 +108,9 @@ def _stream(stream):
 
 
 def options(two_component=False, c=None, precision=PREC_FP64, dlu_potential=DLU_FREE_ATOM,
-            so_same_atom_only=True, n_slices=0) -> abi.Options:
+            so_same_atom_only=True, n_slices=0, local_approx=LOCAL_DLU) -> abi.Options:
     o = abi.Options()
+    o.local_approx = int(local_approx)
     o.c = float(c) if c else C_LIGHT
     o.two_component = int(bool(two_component))
     o.precision = int(precision)
@@ -148,16 +161,18 @@ def _hout(parts):
     return h
 
 
-def x2c_build_full(ctx: Context, m: dict, two_component=False, c=None, want_U=False, stream=None):
-    """Full X2C: returns dict(h=[h0..], UL=[..], US=[..]) of CUDA tensors (quaternion parts)."""
+def x2c_build_full(ctx: Context, m: dict, two_component=False, c=None, want_U=False, stream=None,
+                   out=None, U_out=None):
+    """Full X2C: returns dict(h=[h0..], UL=[..], US=[..]) of CUDA tensors (quaternion parts).
+    out / U_out = (UL parts, US parts): caller-owned outputs instead of new tensors."""
     nc = 4 if two_component else 1
     ms = mats_struct(m, two_component)
     dev = m["S"].device
-    h = _alloc_parts(ms.n, nc, dev)
+    h = out if out is not None else _alloc_parts(ms.n, nc, dev)
     U = None
     out = dict(h=h)
-    if want_U:
-        UL, US = _alloc_parts(ms.n, nc, dev), _alloc_parts(ms.n, nc, dev)
+    if want_U or U_out is not None:
+        UL, US = U_out if U_out is not None else (_alloc_parts(ms.n, nc, dev), _alloc_parts(ms.n, nc, dev))
         U = abi.UOut()
         for q in range(nc):
             U.UL[q] = UL[q].data_ptr()
@@ -192,14 +207,14 @@ class LayoutHolder:
 
 def x2c_build_dlu(ctx: Context, m: dict, offsets, atom_kind=None, kinds=None, two_component=False,
                   c=None, precision=PREC_FP64, dlu_potential=DLU_FREE_ATOM, so_same_atom_only=True,
-                  n_slices=0, out=None, stream=None):
+                  n_slices=0, local_approx=LOCAL_DLU, out=None, stream=None):
     """DLU build.  m: molecular matrices (CUDA tensors); kinds: list of free-atom input dicts
     (FREE_ATOM mode) indexed by atom_kind.  Returns the list of h parts."""
     nc = 4 if two_component else 1
     ms = mats_struct(m, two_component)
     h = out if out is not None else _alloc_parts(ms.n, nc, m["S"].device)
     lay = LayoutHolder(offsets, atom_kind, kinds, two_component)
-    o = options(two_component, c, precision, dlu_potential, so_same_atom_only, n_slices)
+    o = options(two_component, c, precision, dlu_potential, so_same_atom_only, n_slices, local_approx)
     ho = _hout(h)
     abi.check(ctx.lib.x2c_build_dlu(ctx.handle, ctypes.byref(o), ctypes.byref(lay.s), ctypes.byref(ms),
                                     ctypes.byref(ho), _stream(stream)), "x2c_build_dlu", ctx.handle)
@@ -208,7 +223,7 @@ def x2c_build_dlu(ctx: Context, m: dict, offsets, atom_kind=None, kinds=None, tw
 
 def x2c_build_dlu_batched(ctx: Context, mols: list, layouts: list, two_component=False, c=None,
                           precision=PREC_FP64, dlu_potential=DLU_FREE_ATOM, so_same_atom_only=True,
-                          n_slices=0, outs=None, stream=None):
+                          n_slices=0, local_approx=LOCAL_DLU, outs=None, stream=None):
     """Batched DLU over several molecules.  mols: list of matrix dicts; layouts: list of
     (offsets, atom_kind, kinds) tuples.  Returns a list of h-part lists."""
     nc = 4 if two_component else 1
@@ -225,14 +240,15 @@ def x2c_build_dlu_batched(ctx: Context, mols: list, layouts: list, two_component
         h = outs[i] if outs is not None else _alloc_parts(ms[i].n, nc, m["S"].device)
         outs_.append(h)
         hs[i] = _hout(h)
-    o = options(two_component, c, precision, dlu_potential, so_same_atom_only, n_slices)
+    o = options(two_component, c, precision, dlu_potential, so_same_atom_only, n_slices, local_approx)
     abi.check(ctx.lib.x2c_build_dlu_batched(ctx.handle, ctypes.byref(o), n_mol, ls, ms, hs, _stream(stream)),
               "x2c_build_dlu_batched", ctx.handle)
     return outs_
 
 
-def x2c_atomic_transforms(ctx: Context, inputs: list, two_component=False, c=None, stream=None):
-    """Decoupling transforms of independent input sets: list of (UL parts, US parts)."""
+def x2c_atomic_transforms(ctx: Context, inputs: list, two_component=False, c=None, stream=None, out=None):
+    """Decoupling transforms of independent input sets: list of (UL parts, US parts)
+    (`out`: caller-owned list of the same form)."""
     nc = 4 if two_component else 1
     k = len(inputs)
     ms = (abi.Mats * k)()
@@ -240,7 +256,10 @@ def x2c_atomic_transforms(ctx: Context, inputs: list, two_component=False, c=Non
     res = []
     for i, m in enumerate(inputs):
         ms[i] = mats_struct(m, two_component)
-        UL, US = _alloc_parts(ms[i].n, nc, m["S"].device), _alloc_parts(ms[i].n, nc, m["S"].device)
+        if out is not None:
+            UL, US = out[i]
+        else:
+            UL, US = _alloc_parts(ms[i].n, nc, m["S"].device), _alloc_parts(ms[i].n, nc, m["S"].device)
         for q in range(nc):
             us[i].UL[q] = UL[q].data_ptr()
             us[i].US[q] = US[q].data_ptr()
@@ -278,7 +297,7 @@ def x2c_atomic_transforms_noalloc(inputs: list, two_component=False, c=None, out
 
 def x2c_build_dlu_host(ctx: Context, m: dict, offsets, atom_kind=None, kinds=None, two_component=False,
                        c=None, precision=PREC_FP64, dlu_potential=DLU_FREE_ATOM, so_same_atom_only=True,
-                       n_slices=0, out=None, stream=None):
+                       n_slices=0, local_approx=LOCAL_DLU, out=None, stream=None):
     """DLU build from HOST arrays (numpy float64 or CPU torch tensors, pinned or not);
     h parts are written into `out` (host arrays) or new numpy arrays."""
     nc = 4 if two_component else 1
@@ -309,7 +328,7 @@ def x2c_build_dlu_host(ctx: Context, m: dict, offsets, atom_kind=None, kinds=Non
     ho = abi.HOut()
     for q in range(nc):
         ho.h[q] = hp(out[q])
-    o = options(two_component, c, precision, dlu_potential, so_same_atom_only, n_slices)
+    o = options(two_component, c, precision, dlu_potential, so_same_atom_only, n_slices, local_approx)
     abi.check(ctx.lib.x2c_build_dlu_host(ctx.handle, ctypes.byref(o), ctypes.byref(lay.s), ctypes.byref(ms),
                                          ctypes.byref(ho), _stream(stream)), "x2c_build_dlu_host", ctx.handle)
     return out
@@ -328,7 +347,7 @@ def x2c_quaternion_to_dense(h_parts: list, stream=None):
 
 def x2c_build_dlu_with_transforms(ctx: Context, m: dict, offsets, atom_kind, kinds_U, kind_sizes,
                                   two_component=False, c=None, precision=PREC_FP64, so_same_atom_only=True,
-                                  n_slices=0, out=None, stream=None):
+                                  n_slices=0, local_approx=LOCAL_DLU, out=None, stream=None):
     """DLU build (free-atom mode) from given per-kind transforms: kinds_U is a list of
     (UL parts, US parts) CUDA tensors (e.g. from x2c_atomic_transforms), kind_sizes the
     kinds' basis sizes.  Returns the list of h parts."""
@@ -346,13 +365,50 @@ def x2c_build_dlu_with_transforms(ctx: Context, m: dict, offsets, atom_kind, kin
         for q in range(nc):
             us[i].UL[q] = UL[q].data_ptr()
             us[i].US[q] = US[q].data_ptr()
-    o = options(two_component, c, precision, DLU_FREE_ATOM, so_same_atom_only, n_slices)
+    o = options(two_component, c, precision, DLU_FREE_ATOM, so_same_atom_only, n_slices, local_approx)
     ho = _hout(h)
     abi.check(ctx.lib.x2c_build_dlu_with_transforms(ctx.handle, ctypes.byref(o), ctypes.byref(lay.s), us,
                                                     ctypes.byref(ms), ctypes.byref(ho), _stream(stream)),
               "x2c_build_dlu_with_transforms", ctx.handle)
     return h
 
+
+
+def x2c_picture_change(ctx: Context, P_LL, P_SS, offsets, atom_kind, kinds_U, kind_sizes, two_component=False,
+                       precision=PREC_FP64, so_same_atom_only=True, n_slices=0, out=None, stream=None):
+    """Picture-change transformation P2c = U^L+ P^LL U^L + U^S+ P^SS U^S of a property
+    operator without large-small coupling.  P_LL: CUDA tensor (n x n); P_SS: one tensor
+    (spin-free) or a list of the quaternion parts [SS0, SS1, SS2, SS3] (SS1..3 may be None);
+    the transforms as in x2c_build_dlu_with_transforms (one "atom" spanning the basis for
+    full-X2C transforms).  Returns the list of P2c parts."""
+    nc = 4 if two_component else 1
+    ss = list(P_SS) if isinstance(P_SS, (list, tuple)) else [P_SS]
+    ss += [None] * (4 - len(ss))
+    n = int(P_LL.shape[0])
+    for t in [P_LL] + ss:
+        _check_tensor(t, n)
+    p = abi.Property()
+    p.n = n
+    p.LL = P_LL.data_ptr()
+    for q in range(4):
+        p.SS[q] = ss[q].data_ptr() if ss[q] is not None else None
+    h = out if out is not None else _alloc_parts(n, nc, P_LL.device)
+    kind_structs = []
+    for kn in kind_sizes:
+        k = abi.Mats()
+        k.n = int(kn)
+        kind_structs.append(k)
+    lay = LayoutHolder(offsets, atom_kind, kind_structs, two_component)
+    us = (abi.UOut * len(kinds_U))()
+    for i, (UL, US) in enumerate(kinds_U):
+        for q in range(nc):
+            us[i].UL[q] = UL[q].data_ptr()
+            us[i].US[q] = US[q].data_ptr()
+    o = options(two_component, None, precision, DLU_FREE_ATOM, so_same_atom_only, n_slices)
+    ho = _hout(h)
+    abi.check(ctx.lib.x2c_picture_change(ctx.handle, ctypes.byref(o), ctypes.byref(lay.s), us, ctypes.byref(p),
+                                         ctypes.byref(ho), _stream(stream)), "x2c_picture_change", ctx.handle)
+    return h
 
 def x2c_query_workspace(ctx: Context, m: dict, offsets=None, atom_kind=None, kinds=None, two_component=False,
                         precision=PREC_FP64, dlu_potential=DLU_FREE_ATOM, full=False):
@@ -465,15 +521,15 @@ class Server:
         return s, lds.pop()
 
     def submit_dlu(self, m, offsets, atom_kind, kinds, kind_keys=None, two_component=False, c=None,
-                   precision=PREC_FP64, n_slices=0, so_same_atom_only=True, dlu_potential=DLU_FREE_ATOM,
-                   out=None, host=False, t_arrival=-1.0):
+                   precision=PREC_FP64, n_slices=0, local_approx=LOCAL_DLU, so_same_atom_only=True,
+                   dlu_potential=DLU_FREE_ATOM, out=None, host=False, t_arrival=-1.0):
         """Queue a DLU build.  m: molecular matrices (CUDA tensors, or host arrays with
         host=True; row-major views such as big[:n, :n] are allowed); kinds: free-atom input
         dicts; kind_keys: one integer cache key per kind (0 = not cached); out: result
         buffers (device, or host with host=True), None = server-allocated device result."""
         nc = 4 if two_component else 1
         req = abi.Request()
-        req.opt = options(two_component, c, precision, dlu_potential, so_same_atom_only, n_slices)
+        req.opt = options(two_component, c, precision, dlu_potential, so_same_atom_only, n_slices, local_approx)
         req.kind, req.memory = REQ_DLU, (MEM_HOST if host else MEM_DEVICE)
         req.mol, ld = self._mats(m, two_component, host)
         req.ld = ld

@@ -18,6 +18,7 @@ STATUS_NAMES = {0: "X2C_OK", 1: "X2C_ERR_ARG", 2: "X2C_ERR_NOMEM", 3: "X2C_ERR_C
                 10: "X2C_ERR_CANCELLED", 11: "X2C_ERR_NOT_FOUND"}
 PREC_FP64, PREC_SPLIT_BF16 = 0, 1
 DLU_FREE_ATOM, DLU_MOLECULAR_BLOCK = 0, 1
+LOCAL_DLU, LOCAL_DLH = 0, 1
 
 _dp = ctypes.POINTER(ctypes.c_double)
 
@@ -26,7 +27,7 @@ class Options(ctypes.Structure):
     _fields_ = [("c", ctypes.c_double), ("two_component", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("dlu_potential", ctypes.c_int32),
                 ("so_same_atom_only", ctypes.c_int32), ("n_slices", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("local_approx", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class Mats(ctypes.Structure):
@@ -52,6 +53,15 @@ class Layout(ctypes.Structure):
 class Counters(ctypes.Structure):
     _fields_ = [("pair_blocks", ctypes.c_int64), ("atomic_solves", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64), ("credited_flops", ctypes.c_double)]
+
+
+class Property(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("LL", ctypes.c_void_p), ("SS", ctypes.c_void_p * 4)]
+
+
+class GraphStats(ctypes.Structure):
+    _fields_ = [("captures", ctypes.c_int64), ("replays", ctypes.c_int64), ("cached", ctypes.c_int32),
+                ("last_replayed", ctypes.c_int32)]
 
 
 class ServerOptions(ctypes.Structure):
@@ -113,6 +123,11 @@ _SIGS = {
     "x2c_ctx_set_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "x2c_ctx_tuning_log": (ctypes.c_char_p, [ctypes.c_void_p]),
     "x2c_ctx_set_split_variant": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "x2c_ctx_set_graphs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "x2c_picture_change": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Options), ctypes.POINTER(Layout),
+                                          ctypes.POINTER(UOut), ctypes.POINTER(Property), ctypes.POINTER(HOut),
+                                          ctypes.c_void_p]),
+    "x2c_ctx_graph_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(GraphStats)]),
     "x2c_query_workspace": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Options), ctypes.c_int32,
                                            ctypes.POINTER(Layout), ctypes.POINTER(Mats),
                                            ctypes.POINTER(ctypes.c_size_t)]),

@@ -6,10 +6,33 @@
 
 #include "common.cuh"
 
+// A build captured into a CUDA graph (x2c_ctx_set_graphs), keyed by its launch plan.
+struct x2c_ctx::GraphEntry {
+  std::string key;
+  uint64_t hash = 0;
+  uint64_t ws_generation = 0;  // the workspace the graph's kernels point into
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<char *> pinned;  // sources of the captured descriptor uploads
+  struct Timed {
+    std::string name;
+    double flops;
+    cudaGraphNode_t begin, end;  // event-record nodes around the launch
+  };
+  std::vector<Timed> timed;
+  int64_t launches = 0, pair_blocks = 0, atomic_solves = 0;
+  double credited = 0;
+};
+
 namespace x2c {
 
 x2c_status ensure_workspace(x2c_ctx *ctx, size_t bytes, Arena *out, cudaStream_t st) {
   if (bytes > ctx->ws_bytes) {
+    if (ctx->capturing) {  // the graph would hold pointers into a buffer freed here
+      ctx->last_error = "workspace growth inside a graph capture";
+      return X2C_ERR_ARG;
+    }
+    ctx->ws_generation++;
     const size_t want = bytes + bytes / 8;
     cudaError_t e;
     if (ctx->pool) {
@@ -46,6 +69,28 @@ size_t workspace_after_growth(const x2c_ctx *ctx, size_t bytes) {
 x2c_status upload(x2c_ctx *ctx, cudaStream_t st, void *dst, const void *src, size_t bytes) {
   if (bytes == 0) return X2C_OK;
   const size_t need = (bytes + 255) & ~static_cast<size_t>(255);
+  if (ctx->capturing) {
+    // a captured copy reads its source at every replay: the source is a pinned block that
+    // belongs to the graph and is never rewritten
+    if (ctx->cap_pinned.empty() || ctx->cap_off + need > ctx->cap_cap) {
+      const size_t cap = std::max<size_t>(need, 1u << 20);
+      char *blk = nullptr;
+      cudaError_t e = cudaHostAlloc(reinterpret_cast<void **>(&blk), cap, cudaHostAllocDefault);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        ctx->last_error = std::string("pinned graph source allocation: ") + cudaGetErrorString(e);
+        return X2C_ERR_NOMEM;
+      }
+      ctx->cap_pinned.push_back(blk);
+      ctx->cap_off = 0;
+      ctx->cap_cap = cap;
+    }
+    char *h = ctx->cap_pinned.back() + ctx->cap_off;
+    ctx->cap_off += need;
+    std::memcpy(h, src, bytes);
+    X2C_TRY_CUDA(ctx, cudaMemcpyAsync(dst, h, bytes, cudaMemcpyHostToDevice, st));
+    return X2C_OK;
+  }
   auto retire = [&](const x2c_ctx::Staged &f) -> x2c_status {
     X2C_TRY_CUDA(ctx, cudaEventSynchronize(f.done));
     ctx->ring_events.push_back(f.done);
@@ -124,6 +169,7 @@ x2c_status check_options(const x2c_options *o) {
   if (o->precision != X2C_PREC_FP64 && o->precision != X2C_PREC_SPLIT_BF16) return X2C_ERR_ARG;
   if (o->dlu_potential != X2C_DLU_FREE_ATOM && o->dlu_potential != X2C_DLU_MOLECULAR_BLOCK) return X2C_ERR_ARG;
   if (o->n_slices < 0 || o->n_slices > 8) return X2C_ERR_ARG;
+  if (o->local_approx != X2C_LOCAL_DLU && o->local_approx != X2C_LOCAL_DLH) return X2C_ERR_ARG;
   for (int r : o->reserved)
     if (r != 0) return X2C_ERR_ARG;
   return X2C_OK;
@@ -156,10 +202,16 @@ struct Problem {
 
 // One logical build: a set of decoupling problems (grouped by size), a U table indexed by
 // problem, molecules and their pair list.
+struct NonRelFill {  // DLH: a molecule whose atom-other-atom blocks are T + V
+  int mol;
+  std::vector<int32_t> off;
+};
+
 struct BuildPlan {
   std::vector<Problem> problems;
   std::vector<MolDesc> mols;
   std::vector<PairDesc> pairs;
+  std::vector<NonRelFill> fills;
   int nc = 1;
   int max_n = 0;
   double credited = 0;
@@ -184,8 +236,10 @@ x2c_status run_plan(x2c_ctx *ctx, const x2c_options *opt, BuildPlan &plan, cudaS
   const size_t np = plan.problems.size();
   const size_t table_bytes = 2 * (((np * sizeof(double *) + 255) / 256) * 256);
   const size_t mol_bytes = ((plan.mols.size() * sizeof(MolDesc) + 255) / 256) * 256;
+  size_t fill_bytes = 0;
+  for (const auto &f : plan.fills) fill_bytes += ((f.off.size() * sizeof(int32_t) + 255) / 256) * 256;
   const size_t asm_ws = assemble_workspace_bytes(plan.pairs, nc, plan.max_n, opt->precision);
-  const size_t total = arena_doubles(u_doubles) + desc_bytes + table_bytes + mol_bytes +
+  const size_t total = arena_doubles(u_doubles) + desc_bytes + table_bytes + mol_bytes + fill_bytes +
                        std::max(solve_ws, asm_ws) + 8192;
   if (dry_bytes) {
     *dry_bytes = total;
@@ -198,6 +252,11 @@ x2c_status run_plan(x2c_ctx *ctx, const x2c_options *opt, BuildPlan &plan, cudaS
   double **dUS = reinterpret_cast<double **>(ar.take_bytes(np * sizeof(double *)));
   MolDesc *dmols = reinterpret_cast<MolDesc *>(ar.take_bytes(std::max<size_t>(1, plan.mols.size()) * sizeof(MolDesc)));
   if (!Ustore || !dUL || !dUS || !dmols) return X2C_ERR_NOMEM;
+  std::vector<int32_t *> doffs;
+  for (const auto &f : plan.fills) {
+    doffs.push_back(reinterpret_cast<int32_t *>(ar.take_bytes(f.off.size() * sizeof(int32_t))));
+    if (!doffs.back()) return X2C_ERR_NOMEM;
+  }
   std::vector<double *> hUL(np), hUS(np);
   for (size_t i = 0; i < np; ++i)
     if (plan.problems[i].preUL) {
@@ -269,6 +328,12 @@ x2c_status run_plan(x2c_ctx *ctx, const x2c_options *opt, BuildPlan &plan, cudaS
   X2C_TRY(upload(ctx, st, dUL, hUL.data(), np * sizeof(double *)));
   X2C_TRY(upload(ctx, st, dUS, hUS.data(), np * sizeof(double *)));
   X2C_TRY(upload(ctx, st, dmols, plan.mols.data(), plan.mols.size() * sizeof(MolDesc)));
+  for (size_t i = 0; i < plan.fills.size(); ++i) {
+    const auto &f = plan.fills[i];
+    const int L = (int)f.off.size() - 1;
+    X2C_TRY(upload(ctx, st, doffs[i], f.off.data(), f.off.size() * sizeof(int32_t)));
+    X2C_TRY(fill_nonrel_offdiag(ctx, st, dmols, f.mol, doffs[i], L, f.off[L], nc));
+  }
   UTable ut{dUL, dUS};
   const int so_all = (nc == 4 && !opt->so_same_atom_only) ? 1 : 0;
   for (const auto &P : plan.pairs) plan.credited += credited_pair_flops(P.nA, P.nB, nc, P.diag, so_all);
@@ -371,10 +436,13 @@ x2c_status add_molecule(BuildPlan &plan, const x2c_options *opt, const x2c_layou
     }
   }
   plan.mols.push_back(mol_desc(mol, h, nc));
+  // DLH: only the same-atom blocks are transformed; the rest is filled with T + V
+  const bool dlh = opt->local_approx == X2C_LOCAL_DLH;
+  if (dlh) plan.fills.push_back({mol_index, std::vector<int32_t>(lay->atom_offset, lay->atom_offset + L + 1)});
   for (int A = 0; A < L; ++A) {
     const int nA = lay->atom_offset[A + 1] - lay->atom_offset[A];
     plan.max_n = std::max(plan.max_n, nA);
-    for (int B = A; B < L; ++B) {
+    for (int B = A; B < (dlh ? A + 1 : L); ++B) {
       PairDesc P{};
       P.offA = lay->atom_offset[A];
       P.offB = lay->atom_offset[B];
@@ -420,6 +488,217 @@ void end_call(x2c_ctx *ctx, const BuildPlan &plan) {
   ctx->counters.credited_flops = plan.credited;
 }
 
+// ---------------------------------------------------------------------------------------
+// CUDA-graph replay.  A build's host work (plan, descriptor uploads, a few hundred launches)
+// is the same for every call with the same plan; with graphs enabled the second such call
+// captures the enqueued work on a private stream and every later one launches the
+// instantiated graph on the caller's stream.
+
+constexpr size_t kMaxGraphs = 16;
+constexpr size_t kMaxSeenPlans = 4096;
+
+struct KeyBuf {
+  std::string b;
+  template <class T>
+  void put(const T &v) { b.append(reinterpret_cast<const char *>(&v), sizeof(T)); }
+};
+
+// Everything that decides what a build enqueues: the entry point, the options, every
+// problem, molecule and pair descriptor (so every input and output pointer), extra output
+// pointers, and the context's kernel choices.
+std::string plan_key(const x2c_ctx *ctx, int entry, const x2c_options *opt, const BuildPlan &plan,
+                     const x2c_uout *U, int nU) {
+  static_assert(sizeof(PairDesc) == 40 && sizeof(MolDesc) == 88, "descriptors without padding");
+  KeyBuf k;
+  k.put(entry);
+  k.put(opt->c);
+  k.put(opt->two_component);
+  k.put(opt->precision);
+  k.put(opt->dlu_potential);
+  k.put(opt->so_same_atom_only);
+  k.put(opt->n_slices);
+  k.put(opt->local_approx);
+  k.put(plan.nc);
+  k.put(plan.max_n);
+  k.put(ctx->split_variant);
+  k.put(ctx->cta_cap);
+  k.put(ctx->timing);
+  k.put(plan.problems.size());
+  for (const auto &p : plan.problems) {
+    k.put(p.in.S);
+    k.put(p.in.T);
+    k.put(p.in.V);
+    for (const double *w : p.in.W) k.put(w);
+    k.put(p.in.ld);
+    k.put(p.n);
+    k.put(p.preUL);
+    k.put(p.preUS);
+  }
+  k.put(plan.mols.size());
+  k.b.append(reinterpret_cast<const char *>(plan.mols.data()), plan.mols.size() * sizeof(MolDesc));
+  k.put(plan.pairs.size());
+  k.b.append(reinterpret_cast<const char *>(plan.pairs.data()), plan.pairs.size() * sizeof(PairDesc));
+  for (const auto &f : plan.fills) {
+    k.put(f.mol);
+    k.put(f.off.size());
+    k.b.append(reinterpret_cast<const char *>(f.off.data()), f.off.size() * sizeof(int32_t));
+  }
+  for (int i = 0; i < nU; ++i)
+    for (int q = 0; q < 4; ++q) {
+      k.put(U[i].UL[q]);
+      k.put(U[i].US[q]);
+    }
+  return std::move(k.b);
+}
+
+uint64_t fnv1a(const std::string &b) {
+  uint64_t h = 1469598103934665603ull;
+  for (unsigned char ch : b) h = (h ^ ch) * 1099511628211ull;
+  return h;
+}
+
+void destroy_entry(x2c_ctx::GraphEntry *e) {
+  if (e->exec) cudaGraphExecDestroy(e->exec);
+  if (e->graph) cudaGraphDestroy(e->graph);
+  for (char *p : e->pinned) cudaFreeHost(p);
+  delete e;
+}
+
+// Launch a captured build on `st`: fresh timing events for its record nodes, the call's
+// counters as the capture counted them.
+x2c_status replay(x2c_ctx *ctx, x2c_ctx::GraphEntry *e, cudaStream_t st, BuildPlan &plan) {
+  if (ctx->timing)
+    for (const auto &t : e->timed) {
+      cudaEvent_t b = next_event(ctx), en = next_event(ctx);
+      if (!b || !en) return cuda_fail(ctx, cudaErrorMemoryAllocation, "timing event");
+      X2C_TRY_CUDA(ctx, cudaGraphExecEventRecordNodeSetEvent(e->exec, t.begin, b));
+      X2C_TRY_CUDA(ctx, cudaGraphExecEventRecordNodeSetEvent(e->exec, t.end, en));
+      ctx->pending.push_back({t.name, ctx->ev_used - 2, t.flops});
+    }
+  X2C_TRY_CUDA(ctx, cudaGraphLaunch(e->exec, st));
+  ctx->launches += e->launches;
+  ctx->counters.pair_blocks = e->pair_blocks;
+  ctx->counters.atomic_solves = e->atomic_solves;
+  plan.credited += e->credited;
+  ctx->graph_replays++;
+  ctx->last_replayed = true;
+  return X2C_OK;
+}
+
+// Run one build: eagerly (graphs off, or a plan seen for the first time), else as a launch of
+// the graph captured for this plan.  enqueue(stream, dry_bytes) enqueues the build's work on
+// `stream`, or with dry_bytes non-NULL only sizes its workspace.
+template <class KeyFn, class F>
+x2c_status graph_run(x2c_ctx *ctx, cudaStream_t st, KeyFn &&make_key, BuildPlan &plan, F &&enqueue) {
+  ctx->last_replayed = false;
+  if (!ctx->graphs || ctx->pool) return enqueue(st, nullptr);
+  const std::string key = make_key();
+  const uint64_t hash = fnv1a(key);
+  auto &cache = ctx->graph_cache;
+  // graphs that point into a workspace that has moved since
+  {
+    bool stale = false;
+    for (auto *e : cache) stale |= e->ws_generation != ctx->ws_generation;
+    if (stale) {
+      X2C_TRY_CUDA(ctx, cudaDeviceSynchronize());
+      std::vector<x2c_ctx::GraphEntry *> keep;
+      for (auto *e : cache)
+        if (e->ws_generation == ctx->ws_generation) keep.push_back(e);
+        else destroy_entry(e);
+      cache.swap(keep);
+    }
+  }
+  for (size_t i = 0; i < cache.size(); ++i)
+    if (cache[i]->hash == hash && cache[i]->key == key) {
+      auto *e = cache[i];
+      cache.erase(cache.begin() + i);
+      cache.push_back(e);
+      return replay(ctx, e, st, plan);
+    }
+  if (ctx->graph_seen.size() > kMaxSeenPlans) ctx->graph_seen.clear();
+  if (++ctx->graph_seen[hash] < 2) return enqueue(st, nullptr);  // first call: eager (and tuned)
+
+  // capture: size the workspace first (no growth may happen inside the capture)
+  size_t need = 0;
+  X2C_TRY(enqueue(st, &need));
+  Arena unused;
+  X2C_TRY(ensure_workspace(ctx, need, &unused, st));
+  if (!ctx->cap_stream) X2C_TRY_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+  const size_t ev0 = ctx->ev_used, pend0 = ctx->pending.size();
+  const int64_t launches0 = ctx->launches;
+  const double credited0 = plan.credited;
+  X2C_TRY_CUDA(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeRelaxed));
+  ctx->capturing = true;
+  ctx->cap_pinned.clear();
+  ctx->cap_off = ctx->cap_cap = 0;
+  const x2c_status s = enqueue(ctx->cap_stream, nullptr);
+  ctx->capturing = false;
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(ctx->cap_stream, &graph);
+  auto *e = new x2c_ctx::GraphEntry();
+  e->pinned.swap(ctx->cap_pinned);
+  e->graph = graph;
+  e->key = key;
+  e->hash = hash;
+  e->ws_generation = ctx->ws_generation;
+  e->launches = ctx->launches - launches0;
+  e->pair_blocks = ctx->counters.pair_blocks;
+  e->atomic_solves = ctx->counters.atomic_solves;
+  e->credited = plan.credited - credited0;
+  ctx->launches = launches0;
+  plan.credited = credited0;
+  // the timing events of the capture name its event-record nodes
+  std::vector<x2c_ctx::Pending> timed(ctx->pending.begin() + pend0, ctx->pending.end());
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> tev;
+  for (const auto &p : timed) tev.push_back({ctx->ev_pool[p.begin], ctx->ev_pool[p.begin + 1]});
+  ctx->pending.resize(pend0);
+  ctx->ev_used = ev0;
+  if (s != X2C_OK || ce != cudaSuccess || !graph) {
+    cudaGetLastError();
+    destroy_entry(e);
+    return s != X2C_OK ? s : cuda_fail(ctx, ce, "graph capture");
+  }
+  if (!timed.empty()) {
+    size_t nn = 0;
+    X2C_TRY_CUDA(ctx, cudaGraphGetNodes(graph, nullptr, &nn));
+    std::vector<cudaGraphNode_t> nodes(nn);
+    X2C_TRY_CUDA(ctx, cudaGraphGetNodes(graph, nodes.data(), &nn));
+    std::map<cudaEvent_t, cudaGraphNode_t> rec;
+    for (auto nd : nodes) {
+      cudaGraphNodeType ty;
+      X2C_TRY_CUDA(ctx, cudaGraphNodeGetType(nd, &ty));
+      if (ty != cudaGraphNodeTypeEventRecord) continue;
+      cudaEvent_t ev;
+      X2C_TRY_CUDA(ctx, cudaGraphEventRecordNodeGetEvent(nd, &ev));
+      rec[ev] = nd;
+    }
+    for (size_t i = 0; i < timed.size(); ++i) {
+      auto b = rec.find(tev[i].first), en = rec.find(tev[i].second);
+      if (b == rec.end() || en == rec.end()) {
+        destroy_entry(e);
+        ctx->last_error = "graph capture: timing event without a record node";
+        return X2C_ERR_CUDA;
+      }
+      e->timed.push_back({timed[i].name, timed[i].flops, b->second, en->second});
+    }
+  }
+  const cudaError_t ie = cudaGraphInstantiate(&e->exec, graph, 0);
+  if (ie != cudaSuccess) {
+    cudaGetLastError();
+    e->exec = nullptr;
+    destroy_entry(e);
+    return cuda_fail(ctx, ie, "cudaGraphInstantiate");
+  }
+  if (cache.size() >= kMaxGraphs) {  // least recently used; a replay may still read its sources
+    X2C_TRY_CUDA(ctx, cudaDeviceSynchronize());
+    destroy_entry(cache.front());
+    cache.erase(cache.begin());
+  }
+  cache.push_back(e);
+  ctx->graph_captures++;
+  return replay(ctx, e, st, plan);
+}
+
 }  // namespace
 
 x2c_status ensure_stage(x2c_ctx *ctx, size_t bytes) {
@@ -438,6 +717,15 @@ x2c_status ensure_stage(x2c_ctx *ctx, size_t bytes) {
   return X2C_OK;
 }
 
+void drop_graphs(x2c_ctx *ctx) {
+  if (!ctx->graph_cache.empty()) {
+    cudaDeviceSynchronize();  // a replay in flight still reads the pinned sources
+    for (auto *e : ctx->graph_cache) destroy_entry(e);
+  }
+  ctx->graph_cache.clear();
+  ctx->graph_seen.clear();
+}
+
 x2c_status full_build(x2c_ctx *ctx, const x2c_options *opt, const x2c_mats *mol, const x2c_hout *h,
                       const x2c_uout *U, cudaStream_t st, size_t *dry_bytes) {
   X2C_TRY(begin_call(ctx));
@@ -448,6 +736,7 @@ x2c_status full_build(x2c_ctx *ctx, const x2c_options *opt, const x2c_mats *mol,
   o.dlu_potential = X2C_DLU_MOLECULAR_BLOCK;
   o.precision = X2C_PREC_FP64;
   o.so_same_atom_only = 1;  // one atom: the only pair is the diagonal one
+  o.local_approx = X2C_LOCAL_DLU;
   int32_t offs[2] = {0, mol->n};
   x2c_layout lay{1, offs, nullptr, 0, nullptr};
   BuildPlan plan;
@@ -455,15 +744,18 @@ x2c_status full_build(x2c_ctx *ctx, const x2c_options *opt, const x2c_mats *mol,
   KindIndex kinds;
   X2C_TRY(add_molecule(plan, &o, &lay, mol, h, 0, kinds));
   std::vector<double *> ULp, USp;
-  X2C_TRY(run_plan(ctx, &o, plan, st, &ULp, &USp, dry_bytes));
-  if (dry_bytes) return X2C_OK;
-  if (U) {
+  auto enqueue = [&](cudaStream_t s, size_t *dry) -> x2c_status {
+    X2C_TRY(run_plan(ctx, &o, plan, s, &ULp, &USp, dry));
+    if (dry || !U) return X2C_OK;
     const size_t n2 = (size_t)mol->n * mol->n;
     for (int q = 0; q < nc; ++q) {
-      if (U->UL[q]) X2C_TRY_CUDA(ctx, cudaMemcpyAsync(U->UL[q], ULp[0] + q * n2, n2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
-      if (U->US[q]) X2C_TRY_CUDA(ctx, cudaMemcpyAsync(U->US[q], USp[0] + q * n2, n2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      if (U->UL[q]) X2C_TRY_CUDA(ctx, cudaMemcpyAsync(U->UL[q], ULp[0] + q * n2, n2 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      if (U->US[q]) X2C_TRY_CUDA(ctx, cudaMemcpyAsync(U->US[q], USp[0] + q * n2, n2 * sizeof(double), cudaMemcpyDeviceToDevice, s));
     }
-  }
+    return X2C_OK;
+  };
+  if (dry_bytes) return enqueue(st, dry_bytes);
+  X2C_TRY(graph_run(ctx, st, [&] { return plan_key(ctx, 0, &o, plan, U, U ? 1 : 0); }, plan, enqueue));
   end_call(ctx, plan);
   return X2C_OK;
 }
@@ -479,8 +771,10 @@ x2c_status dlu_build(x2c_ctx *ctx, const x2c_options *opt, int n_mol, const x2c_
   KindIndex kinds;
   for (int i = 0; i < n_mol; ++i)
     X2C_TRY(add_molecule(plan, opt, &layouts[i], &mols[i], &h[i], i, kinds, ku ? &ku[i] : nullptr));
-  X2C_TRY(run_plan(ctx, opt, plan, st, nullptr, nullptr, dry_bytes));
-  if (!dry_bytes) end_call(ctx, plan);
+  auto enqueue = [&](cudaStream_t s, size_t *dry) { return run_plan(ctx, opt, plan, s, nullptr, nullptr, dry); };
+  if (dry_bytes) return enqueue(st, dry_bytes);
+  X2C_TRY(graph_run(ctx, st, [&] { return plan_key(ctx, 1, opt, plan, nullptr, 0); }, plan, enqueue));
+  end_call(ctx, plan);
   return X2C_OK;
 }
 
@@ -498,17 +792,80 @@ x2c_status transforms_build(x2c_ctx *ctx, const x2c_options *opt, int n_problems
     plan.problems.push_back({input_desc(&inputs[i], plan.nc, 0, inputs[i].n), inputs[i].n});
   }
   std::vector<double *> ULp, USp;
-  X2C_TRY(run_plan(ctx, opt, plan, st, &ULp, &USp, dry_bytes));
-  if (dry_bytes) return X2C_OK;
-  for (int i = 0; i < n_problems; ++i) {
-    const size_t n2 = (size_t)inputs[i].n * inputs[i].n;
-    for (int q = 0; q < plan.nc; ++q) {
-      X2C_TRY_CUDA(ctx, cudaMemcpyAsync(U[i].UL[q], ULp[i] + q * n2, n2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
-      X2C_TRY_CUDA(ctx, cudaMemcpyAsync(U[i].US[q], USp[i] + q * n2, n2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  auto enqueue = [&](cudaStream_t s, size_t *dry) -> x2c_status {
+    X2C_TRY(run_plan(ctx, opt, plan, s, &ULp, &USp, dry));
+    if (dry) return X2C_OK;
+    for (int i = 0; i < n_problems; ++i) {
+      const size_t n2 = (size_t)inputs[i].n * inputs[i].n;
+      for (int q = 0; q < plan.nc; ++q) {
+        X2C_TRY_CUDA(ctx, cudaMemcpyAsync(U[i].UL[q], ULp[i] + q * n2, n2 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        X2C_TRY_CUDA(ctx, cudaMemcpyAsync(U[i].US[q], USp[i] + q * n2, n2 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      }
     }
-  }
+    return X2C_OK;
+  };
+  if (dry_bytes) return enqueue(st, dry_bytes);
+  X2C_TRY(graph_run(ctx, st, [&] { return plan_key(ctx, 2, opt, plan, U, n_problems); }, plan, enqueue));
   end_call(ctx, plan);
   return X2C_OK;
+}
+
+// DLU assembly from given per-kind transforms, gathered part-major into the staging area.
+// With P (picture change) instead of mol, the assembly runs on the property: V = P^LL,
+// T = 0, W = P^SS and 4c^2 = 1 turn the middle matrix [[V, T], [T, W/4c^2 - T]] of Eq. 8
+// into [[P^LL, 0], [0, P^SS]]; the zero matrix (and absent spin parts) sit in the staging area.
+x2c_status with_transforms(x2c_ctx *ctx, const x2c_options *opt, const x2c_layout *layout, const x2c_uout *kind_U,
+                           const x2c_mats *mol, const x2c_property *P, const x2c_hout *h, cudaStream_t st) {
+  X2C_TRY(begin_call(ctx));
+  X2C_TRY(check_options(opt));
+  if (!layout || !kind_U || (!mol && !P) || layout->n_kinds < 1 || !layout->kinds ||
+      opt->dlu_potential != X2C_DLU_FREE_ATOM)
+    return X2C_ERR_ARG;
+  const int nc = opt->two_component ? 4 : 1;
+  const int nk = layout->n_kinds;
+  // the assembly reads each kind's parts contiguously (part-major): gather them into the
+  // staging area unless they already are
+  std::vector<size_t> off(nk + 1, 0);
+  for (int k = 0; k < nk; ++k) {
+    const int n = layout->kinds[k].n;
+    if (n < 1) return X2C_ERR_ARG;
+    for (int q = 0; q < nc; ++q)
+      if (!kind_U[k].UL[q] || !kind_U[k].US[q]) return X2C_ERR_ARG;
+    off[k + 1] = off[k] + 2 * (size_t)nc * n * n;
+  }
+  const size_t zero_doubles = P ? ((size_t)P->n * P->n + 31) / 32 * 32 : 0;
+  X2C_TRY(ensure_stage(ctx, (off[nk] + zero_doubles) * sizeof(double)));
+  double *stage = reinterpret_cast<double *>(ctx->stage);
+  std::vector<const double *> ul(nk), us(nk);
+  for (int k = 0; k < nk; ++k) {
+    const size_t n2 = (size_t)layout->kinds[k].n * layout->kinds[k].n;
+    double *dst = stage + off[k];
+    for (int q = 0; q < nc; ++q) {
+      X2C_TRY_CUDA(ctx, cudaMemcpyAsync(dst + q * n2, kind_U[k].UL[q], n2 * sizeof(double),
+                                        cudaMemcpyDeviceToDevice, st));
+      X2C_TRY_CUDA(ctx, cudaMemcpyAsync(dst + (nc + q) * n2, kind_U[k].US[q], n2 * sizeof(double),
+                                        cudaMemcpyDeviceToDevice, st));
+    }
+    ul[k] = dst;
+    us[k] = dst + nc * n2;
+  }
+  KindTransforms ku{ul.data(), us.data()};
+  if (!P) return dlu_build(ctx, opt, 1, layout, mol, h, &ku, st, nullptr);
+  double *zero = stage + off[nk];
+  X2C_TRY_CUDA(ctx, cudaMemsetAsync(zero, 0, zero_doubles * sizeof(double), st));
+  x2c_mats pm{};
+  pm.n = P->n;
+  pm.S = P->LL;  // not read: the transforms are given
+  pm.T = zero;
+  pm.V = P->LL;
+  pm.W0 = P->SS[0];
+  pm.Wx = P->SS[1] ? P->SS[1] : zero;
+  pm.Wy = P->SS[2] ? P->SS[2] : zero;
+  pm.Wz = P->SS[3] ? P->SS[3] : zero;
+  x2c_options o = *opt;
+  o.c = 0.5;
+  o.local_approx = X2C_LOCAL_DLU;
+  return dlu_build(ctx, &o, 1, layout, &pm, h, &ku, st, nullptr);
 }
 
 }  // namespace x2c
@@ -559,6 +916,8 @@ x2c_status x2c_ctx_destroy(x2c_ctx *ctx) {
   if (!ctx) return X2C_OK;
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
+  drop_graphs(ctx);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->stage) cudaFree(ctx->stage);
   for (auto e : ctx->ev_pool) cudaEventDestroy(e);
@@ -644,6 +1003,23 @@ x2c_status x2c_ctx_set_split_variant(x2c_ctx *ctx, int32_t variant) {
   return X2C_OK;
 }
 
+x2c_status x2c_ctx_set_graphs(x2c_ctx *ctx, int32_t enable) {
+  if (!ctx || (enable != 0 && enable != 1)) return X2C_ERR_ARG;
+  X2C_TRY_CUDA(ctx, cudaSetDevice(ctx->device));
+  if (!enable) drop_graphs(ctx);
+  ctx->graphs = enable != 0;
+  return X2C_OK;
+}
+
+x2c_status x2c_ctx_graph_stats(x2c_ctx *ctx, x2c_graph_stats *out) {
+  if (!ctx || !out) return X2C_ERR_ARG;
+  out->captures = ctx->graph_captures;
+  out->replays = ctx->graph_replays;
+  out->cached = (int32_t)ctx->graph_cache.size();
+  out->last_replayed = ctx->last_replayed ? 1 : 0;
+  return X2C_OK;
+}
+
 x2c_status x2c_ctx_kernel_times(x2c_ctx *ctx, int32_t max_entries, char *names, double *ms,
                                 int64_t *launches, double *flops, int32_t *n_entries) {
   if (!ctx || max_entries < 0 || !n_entries) return X2C_ERR_ARG;
@@ -695,41 +1071,14 @@ x2c_status x2c_build_dlu_batched(x2c_ctx *ctx, const x2c_options *opt, int32_t n
 x2c_status x2c_build_dlu_with_transforms(x2c_ctx *ctx, const x2c_options *opt, const x2c_layout *layout,
                                          const x2c_uout *kind_U, const x2c_mats *mol, const x2c_hout *h,
                                          void *stream) {
-  X2C_TRY(begin_call(ctx));
-  X2C_TRY(check_options(opt));
-  if (!layout || !kind_U || !mol || layout->n_kinds < 1 || !layout->kinds ||
-      opt->dlu_potential != X2C_DLU_FREE_ATOM)
-    return X2C_ERR_ARG;
-  const int nc = opt->two_component ? 4 : 1;
-  const int nk = layout->n_kinds;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  // the assembly reads each kind's parts contiguously (part-major): gather them into the
-  // staging area unless they already are
-  std::vector<size_t> off(nk + 1, 0);
-  for (int k = 0; k < nk; ++k) {
-    const int n = layout->kinds[k].n;
-    if (n < 1) return X2C_ERR_ARG;
-    for (int q = 0; q < nc; ++q)
-      if (!kind_U[k].UL[q] || !kind_U[k].US[q]) return X2C_ERR_ARG;
-    off[k + 1] = off[k] + 2 * (size_t)nc * n * n;
-  }
-  X2C_TRY(ensure_stage(ctx, off[nk] * sizeof(double)));
-  double *stage = reinterpret_cast<double *>(ctx->stage);
-  std::vector<const double *> ul(nk), us(nk);
-  for (int k = 0; k < nk; ++k) {
-    const size_t n2 = (size_t)layout->kinds[k].n * layout->kinds[k].n;
-    double *dst = stage + off[k];
-    for (int q = 0; q < nc; ++q) {
-      X2C_TRY_CUDA(ctx, cudaMemcpyAsync(dst + q * n2, kind_U[k].UL[q], n2 * sizeof(double),
-                                        cudaMemcpyDeviceToDevice, st));
-      X2C_TRY_CUDA(ctx, cudaMemcpyAsync(dst + (nc + q) * n2, kind_U[k].US[q], n2 * sizeof(double),
-                                        cudaMemcpyDeviceToDevice, st));
-    }
-    ul[k] = dst;
-    us[k] = dst + nc * n2;
-  }
-  KindTransforms ku{ul.data(), us.data()};
-  return dlu_build(ctx, opt, 1, layout, mol, h, &ku, st, nullptr);
+  return with_transforms(ctx, opt, layout, kind_U, mol, nullptr, h, static_cast<cudaStream_t>(stream));
+}
+
+x2c_status x2c_picture_change(x2c_ctx *ctx, const x2c_options *opt, const x2c_layout *layout,
+                              const x2c_uout *kind_U, const x2c_property *P, const x2c_hout *out,
+                              void *stream) {
+  if (!P || P->n < 1 || !P->LL || !P->SS[0]) return X2C_ERR_ARG;
+  return with_transforms(ctx, opt, layout, kind_U, nullptr, P, out, static_cast<cudaStream_t>(stream));
 }
 
 x2c_status x2c_atomic_transforms(x2c_ctx *ctx, const x2c_options *opt, int32_t n_problems,

@@ -283,4 +283,36 @@ x2c_status assemble_pairs_fp64(x2c_ctx *ctx, cudaStream_t st, double c, int nc, 
   return X2C_OK;
 }
 
+// DLH (Sec. III.A): every atom-other-atom block of h is the non-relativistic T + V; the
+// spin parts of those blocks are zero.  One CTA per row i (grid-strided): the atom of i by
+// bisection of the offsets, then the row streamed outside [off[a], off[a+1]).
+__global__ void nonrel_offdiag_kernel(const MolDesc *mols, int mol, const int32_t *off, int L, int nc) {
+  const MolDesc &m = mols[mol];
+  const int N = off[L];
+  for (int i = blockIdx.x; i < N; i += gridDim.x) {
+    int lo = 0, hi = L;  // off[lo] <= i < off[hi]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (off[mid] <= i) lo = mid;
+      else hi = mid;
+    }
+    const int a0 = off[lo], a1 = off[lo + 1];
+    const int64_t row = static_cast<int64_t>(i) * m.ld;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+      if (j >= a0 && j < a1) continue;
+      m.h[0][row + j] = m.T[row + j] + m.V[row + j];
+      for (int q = 1; q < nc; ++q) m.h[q][row + j] = 0.0;
+    }
+  }
+}
+
+x2c_status fill_nonrel_offdiag(x2c_ctx *ctx, cudaStream_t st, const MolDesc *d_mols, int mol, const int32_t *d_off,
+                               int L, int N, int nc) {
+  if (L < 2) return X2C_OK;
+  const int blocks = std::min(N, 152 * 8);
+  tbegin(ctx, st);
+  nonrel_offdiag_kernel<<<blocks, 256, 0, st>>>(d_mols, mol, d_off, L, nc);
+  return launched(ctx, "dlh_offdiag", st, 0);
+}
+
 }  // namespace x2c

@@ -67,6 +67,18 @@ struct x2c_ctx {
   std::map<uint64_t, int> tuned;
   std::string tune_log;
   cudaEvent_t tune_ev[2] = {nullptr, nullptr};
+  // CUDA-graph replay of repeated identical builds (x2c_ctx_set_graphs; abi.cu)
+  struct GraphEntry;
+  bool graphs = false;
+  bool capturing = false;                 // a build is being captured into a graph
+  uint64_t ws_generation = 0;             // bumped whenever the workspace moves
+  std::vector<GraphEntry *> graph_cache;  // least recently used first
+  std::map<uint64_t, int> graph_seen;     // plan hash -> eager calls with that plan
+  std::vector<char *> cap_pinned;         // pinned sources of the current capture's uploads
+  size_t cap_off = 0, cap_cap = 0;
+  cudaStream_t cap_stream = nullptr;
+  int64_t graph_captures = 0, graph_replays = 0;
+  bool last_replayed = false;
 };
 
 namespace x2c {
@@ -105,10 +117,16 @@ inline cudaEvent_t next_event(x2c_ctx *ctx) {
   }
   return ctx->ev_pool[ctx->ev_used++];
 }
+// Inside a stream capture the record must become a node of the graph (an external record);
+// a plain record would only order the captured work.
+inline void record_timing_event(x2c_ctx *ctx, cudaEvent_t e, cudaStream_t st) {
+  if (ctx->capturing) cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+  else cudaEventRecord(e, st);
+}
 inline void tbegin(x2c_ctx *ctx, cudaStream_t st) {
   if (!ctx->timing) return;
   cudaEvent_t e = next_event(ctx);
-  if (e) cudaEventRecord(e, st);
+  if (e) record_timing_event(ctx, e, st);
 }
 
 // Check the launch that was just enqueued and count it; `flops` = the launch's algorithmic
@@ -121,7 +139,7 @@ inline x2c_status launched(x2c_ctx *ctx, const char *name, cudaStream_t st = nul
     const size_t begin = ctx->ev_used - 1;
     cudaEvent_t ev = next_event(ctx);
     if (ev) {
-      cudaEventRecord(ev, st);
+      record_timing_event(ctx, ev, st);
       ctx->pending.push_back({name, begin, flops});
     }
   }
@@ -171,12 +189,16 @@ struct Arena {
 inline size_t arena_doubles(size_t n) { return ((n * sizeof(double) + 255) / 256) * 256; }
 
 // Grow the context workspace to at least `bytes` (synchronises the device when it grows,
-// unless the context has a pool: then the growth is stream-ordered on `st`).
+// unless the context has a pool: then the growth is stream-ordered on `st`).  Growth
+// bumps ctx->ws_generation and is refused while a build is being captured.
 x2c_status ensure_workspace(x2c_ctx *ctx, size_t bytes, Arena *out, cudaStream_t st);
 // Copy `bytes` of host memory to the device on `st` through the context's pinned staging
 // ring, so that the call returns at once: cudaMemcpyAsync from pageable memory would first
 // wait for all work already queued on the stream.  The host data may be reused on return.
 x2c_status upload(x2c_ctx *ctx, cudaStream_t st, void *dst, const void *src, size_t bytes);
+
+// Destroy the context's captured graphs (waits for the device first).
+void drop_graphs(x2c_ctx *ctx);
 
 // Auxiliary streams of the context (created on first use, at most kMaxAuxStreams).
 constexpr int kMaxAuxStreams = 4;
@@ -248,5 +270,9 @@ x2c_status assemble_pairs_split(x2c_ctx *ctx, cudaStream_t st, double c, int nc,
                                 const std::vector<const double *> &hUL, const std::vector<const double *> &hUS,
                                 int n_slices, Arena &ar);
 size_t assemble_workspace_bytes(const std::vector<PairDesc> &pairs, int nc, int max_n, int precision);
+// DLH: h = T + V (spin parts 0) on every block of molecule `mol` outside the same-atom
+// blocks; d_off: device copy of the molecule's L + 1 atom offsets, N = d_off[L].
+x2c_status fill_nonrel_offdiag(x2c_ctx *ctx, cudaStream_t st, const MolDesc *d_mols, int mol, const int32_t *d_off,
+                               int L, int N, int nc);
 
 }  // namespace x2c

@@ -212,7 +212,8 @@ x2c_status prepare(x2c_server *s, const x2c_request *in, Request &r) {
   r.out_kept = in->out.h[0] == nullptr;
   r.batchable = free_atom;
   r.group = r.batchable ? (static_cast<uint64_t>(in->opt.two_component) | (uint64_t)in->opt.precision << 1 |
-                           (uint64_t)in->opt.n_slices << 4 | (uint64_t)in->opt.so_same_atom_only << 8) ^
+                           (uint64_t)in->opt.n_slices << 4 | (uint64_t)in->opt.so_same_atom_only << 8 |
+                           (uint64_t)in->opt.local_approx << 9) ^
                               (dbits(x2c::speed_of_light(&in->opt)) * 0x9E3779B97F4A7C15ull)
                         : 0;
   (void)s;

@@ -1082,7 +1082,7 @@ x2c_status run_tuned(x2c_ctx *ctx, cudaStream_t st, double c, int nc, int so_all
   auto it = ctx->tuned.find(key);
   if (it != ctx->tuned.end())
     return run_choice<S>(it->second, ctx, st, c, nc, so_all, pairs, d_mols, ut, hUL, hUS, ar);
-  if (!ctx->autotune || n_choices == 1) {
+  if (!ctx->autotune || n_choices == 1 || ctx->capturing) {  // (no timing runs inside a capture)
     // untuned default: the transposed stage 1 where it exists (fastest on every measured shape)
     const int def = n_choices == 3 ? 2 : (S <= 5 ? 0 : 1);
     ctx->tuned[key] = def;

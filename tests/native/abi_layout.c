@@ -5,9 +5,10 @@
 #include "x2c.h"
 
 int main(void) {
-  printf("options %zu %zu %zu %zu %zu %zu\n", sizeof(x2c_options), offsetof(x2c_options, two_component),
+  printf("options %zu %zu %zu %zu %zu %zu %zu\n", sizeof(x2c_options), offsetof(x2c_options, two_component),
          offsetof(x2c_options, precision), offsetof(x2c_options, so_same_atom_only),
-         offsetof(x2c_options, n_slices), offsetof(x2c_options, reserved));
+         offsetof(x2c_options, n_slices), offsetof(x2c_options, local_approx), offsetof(x2c_options, reserved));
+  printf("property %zu %zu %zu\n", sizeof(x2c_property), offsetof(x2c_property, LL), offsetof(x2c_property, SS));
   printf("mats %zu %zu %zu\n", sizeof(x2c_mats), offsetof(x2c_mats, S), offsetof(x2c_mats, Wz));
   printf("hout %zu\n", sizeof(x2c_hout));
   printf("uout %zu %zu\n", sizeof(x2c_uout), offsetof(x2c_uout, US));
@@ -23,5 +24,7 @@ int main(void) {
          offsetof(x2c_result, slot));
   printf("server_stats %zu %zu %zu %zu\n", sizeof(x2c_server_stats), offsetof(x2c_server_stats, latency_p50_ms),
          offsetof(x2c_server_stats, bytes_in_use), offsetof(x2c_server_stats, max_concurrent));
+  printf("graph_stats %zu %zu %zu\n", sizeof(x2c_graph_stats), offsetof(x2c_graph_stats, cached),
+         offsetof(x2c_graph_stats, last_replayed));
   return 0;
 }

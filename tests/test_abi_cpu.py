@@ -43,7 +43,9 @@ def test_ctypes_structs_match_header(tmp_path):
                subprocess.check_output([str(exe)], text=True).splitlines())
     O = abi.Options
     assert out["options"] == [ctypes.sizeof(O), O.two_component.offset, O.precision.offset,
-                              O.so_same_atom_only.offset, O.n_slices.offset, O.reserved.offset]
+                              O.so_same_atom_only.offset, O.n_slices.offset, O.local_approx.offset,
+                              O.reserved.offset]
+    assert out["property"] == [ctypes.sizeof(abi.Property), abi.Property.LL.offset, abi.Property.SS.offset]
     assert out["mats"] == [ctypes.sizeof(abi.Mats), abi.Mats.S.offset, abi.Mats.Wz.offset]
     assert out["hout"] == [ctypes.sizeof(abi.HOut)]
     assert out["uout"] == [ctypes.sizeof(abi.UOut), abi.UOut.US.offset]
@@ -57,6 +59,8 @@ def test_ctypes_structs_match_header(tmp_path):
     assert out["result"] == [ctypes.sizeof(Re), Re.h.offset, Re.t_end.offset, Re.slot.offset]
     assert out["server_stats"] == [ctypes.sizeof(SS), SS.latency_p50_ms.offset, SS.bytes_in_use.offset,
                                    SS.max_concurrent.offset]
+    G = abi.GraphStats
+    assert out["graph_stats"] == [ctypes.sizeof(G), G.cached.offset, G.last_replayed.offset]
 
 
 def _spinor(parts):

@@ -241,3 +241,74 @@ def test_dlu_molecular_block_mode_differs_from_free_atom_but_is_close():
     fa = O.x2c_dlu(m, mol.offsets, [w.atomic_inputs(47.0, "s30", False)] * 4)["h"]
     assert _rel(mb, full) < 1e-6 and _rel(fa, full) < 1e-6
     assert _rel(mb, fa) > 1e-12
+
+
+@pytest.mark.parametrize("two_c", [False, True])
+def test_dlh_pins(two_c):
+    """DLH (Sec. III.A): one atom -> full X2C; same-atom blocks exactly decoupled (their
+    eigenvalues over S_AA are the positive-energy 4c eigenvalues of the block problem, Eq. 1
+    restricted to the block, molecular-block mode); atom-other-atom blocks are T + V; c -> oo
+    gives T + V with a c^-2 error."""
+    at = w.atomic_inputs(47.0, "s30", two_c)
+    assert _rel(O.x2c_dlh(at, np.array([0, 30]), [at]), O.x2c_full(at)["h"]) < 1e-14
+    mol = w.silver_cluster(3, "s30")
+    m = w.molecule_inputs(mol, two_c)
+    N, off = mol.nbf, mol.offsets
+    h = O.x2c_dlh(m, off)
+    assert _rel(h, h.conj().T) < 1e-13
+    S, T, V, W = O.spinor_inputs(m)
+    sp = (lambda r: np.r_[r, N + r]) if two_c else (lambda r: r)
+    for A in range(3):
+        ra = sp(np.arange(off[A], off[A + 1]))
+        for B in range(3):
+            rb = sp(np.arange(off[B], off[B + 1]))
+            blk = h[np.ix_(ra, rb)]
+            if A != B:
+                assert np.array_equal(blk, (T + V)[np.ix_(ra, rb)])
+                continue
+            n = len(ra)
+            s, t, v, wb = (X[np.ix_(ra, ra)] for X in (S, T, V, W))
+            Z = np.zeros_like(s)
+            D = np.block([[v, t], [t, wb / (4 * C * C) - t]])
+            M = np.block([[s, Z], [Z, t / (2 * C * C)]])
+            eps = sla.eigh(D, M, eigvals_only=True)[n:]
+            e = sla.eigh(blk, s, eigvals_only=True)
+            assert np.abs(e - eps)[e < 0].max() < 1e-8
+            assert np.abs(e - eps).max() <= 1e-11 * np.abs(eps).max()
+    # the free-atom transforms change only the same-atom blocks
+    fa = O.x2c_dlh(m, off, [at] * 3)
+    diff = np.abs(fa - h)
+    for A in range(3):
+        for B in range(3):
+            if A != B:
+                ra, rb = sp(np.arange(off[A], off[A + 1])), sp(np.arange(off[B], off[B + 1]))
+                assert diff[np.ix_(ra, rb)].max() == 0.0
+    nr = T + V
+    err = [_rel(O.x2c_dlh(m, off, None, c), nr) for c in (1e6, 1e7)]
+    assert 95 < err[0] / err[1] < 105
+
+
+@pytest.mark.parametrize("two_c", [False, True])
+def test_picture_change_pins(two_c):
+    """Picture change (Sec. II): with P^LL = S and P^SS = T/2c^2 it is the renormalisation
+    condition Eq. 9 and returns S; with the Dirac blocks (V, W/4c^2 - T) plus the L-S terms
+    it returns h (Eq. 8); for one atom the DLU transforms give the full-X2C result; and for
+    c -> oo (U^L, U^S -> identity) it tends to P^LL + P^SS with a c^-2 error."""
+    mol = w.silver_cluster(2, "s30")
+    m = w.molecule_inputs(mol, two_c)
+    S, T, V, W = O.spinor_inputs(m)
+    r = O.x2c_full(m)
+    UL, US = r["UL"], r["US"]
+    assert _rel(O.picture_change(UL, US, S, T / (2 * C * C)), S) < 1e-11
+    h = O.picture_change(UL, US, V, W / (4 * C * C) - T) + UL.conj().T @ T @ US + US.conj().T @ T @ UL
+    assert _rel(h, r["h"]) < 1e-13
+    at = w.atomic_inputs(47.0, "s30", two_c)
+    Sa, Ta, Va, Wa = O.spinor_inputs(at)
+    ra = O.x2c_full(at)
+    d = O.x2c_dlu(at, np.array([0, 30]), [at])
+    assert _rel(O.picture_change(d["UL"], d["US"], Va, Wa), O.picture_change(ra["UL"], ra["US"], Va, Wa)) < 1e-13
+    err = []
+    for c in (1e6, 1e7):
+        rc = O.x2c_full(m, c)
+        err.append(_rel(O.picture_change(rc["UL"], rc["US"], V, S), V + S))
+    assert 95 < err[0] / err[1] < 105 and err[1] < 1e-5
