@@ -67,41 +67,6 @@ struct ClassInfo {
   double inv4c2;
 };
 
-// Stage-1 A rows: (pair, Y, i) with K = (X, k) over atom B.
-struct MidRows {
-  ClassInfo ci;
-  __device__ __forceinline__ double operator()(int r, int k) const {
-    const int per = 2 * ci.nA;
-    const int p = r / per, rr = r - p * per;
-    const PairDesc &P = ci.pairs[p];
-    const MolDesc &m = ci.mols[P.mol];
-    const int Y = rr >= ci.nA, X = k >= ci.nB;
-    const int i = rr - Y * ci.nA, kk = k - X * ci.nB;
-    const int64_t o = static_cast<int64_t>(P.offA + i) * m.ld + (P.offB + kk);
-    if (!Y && !X) return m.V[o];
-    if (Y != X) return m.T[o];
-    return m.W0[o] * ci.inv4c2 - m.T[o];
-  }
-};
-
-// Stage-1 A rows laid out one pair per tile of TRA rows (rows 2 nA..TRA-1 are zero).
-struct MidRowsPadded {
-  ClassInfo ci;
-  int TRA;
-  __device__ __forceinline__ double operator()(int r, int k) const {
-    const int p = r / TRA, rr = r - p * TRA;
-    if (rr >= 2 * ci.nA) return 0.0;
-    const PairDesc &P = ci.pairs[p];
-    const MolDesc &m = ci.mols[P.mol];
-    const int Y = rr >= ci.nA, X = k >= ci.nB;
-    const int i = rr - Y * ci.nA, kk = k - X * ci.nB;
-    const int64_t o = static_cast<int64_t>(P.offA + i) * m.ld + (P.offB + kk);
-    if (!Y && !X) return m.V[o];
-    if (Y != X) return m.T[o];
-    return m.W0[o] * ci.inv4c2 - m.T[o];
-  }
-};
-
 // Stage-1 A rows of the same-atom spin-orbit term, one quaternion part k = 1..3 of the middle
 // matrix i sigma.W / 4c^2 at a time: only the small-small block (Y = X = 1) is non-zero.
 struct SoMidRowsPadded {
@@ -193,6 +158,93 @@ __global__ void __launch_bounds__(256) slice8_fp64_kernel(Src src, int rows, int
     const int s2 = t / words, wd = t - s2 * words;
     reinterpret_cast<uint4 *>(out + core_off(r0, 0, TR, KP, S, s2))[wd] =
         reinterpret_cast<const uint4 *>(stg + s2 * 8 * KP)[wd];
+  }
+}
+
+// Stage-1 A operand, one pair per CTA: the middle matrix Mid_AB = [[V, T], [T, W']]_AB
+// (W' = W0/4c^2 - T) cut into S digit slices, in the tile layout of slice8_fp64_kernel with
+// TR = TRA rows per pair.  Each element (i, k) of the atom blocks is read once and feeds the
+// four Mid elements it determines; a warp takes row i (and row nA + i) with lanes along k, so
+// the two row exponents are warp maxima.  The pair's S slices are staged in shared memory in
+// core-matrix chunks padded by 16 bytes (the four 8-lane groups of a warp then hit different
+// banks) and written out with 16-byte stores.  Rows 2 nA..TRA-1 and columns 2 nB..KP-1 are 0.
+constexpr int kChunkPad = 72;  // BF16 per staged core-matrix chunk (64 + 8)
+template <int S>
+__global__ void __launch_bounds__(512) slice_mid_pair_kernel(ClassInfo ci, int TRA, int KP, const int *kexp,
+                                                             __nv_bfloat16 *out, int *rexp) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __nv_bfloat16 *stg = reinterpret_cast<__nv_bfloat16 *>(smem_raw);
+  const int p = blockIdx.x;
+  const int nA = ci.nA, nB = ci.nB;
+  const int KG = KP >> 3;
+  const int chunks = (TRA >> 3) * KG;  // core-matrix chunks per slice
+  const int words = S * chunks * kChunkPad / 8;
+  for (int o = threadIdx.x; o < words; o += blockDim.x) reinterpret_cast<uint4 *>(stg)[o] = make_uint4(0, 0, 0, 0);
+  __syncthreads();
+  const PairDesc &P = ci.pairs[p];
+  const MolDesc &m = ci.mols[P.mol];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  int kxl[2], kxh[2];
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const int kk = lane + 32 * c;
+    kxl[c] = kk < nB ? kexp[kk] : 0;
+    kxh[c] = kk < nB ? kexp[nB + kk] : 0;
+  }
+  auto put = [&](int row, int col, double x, int shift) {
+    int d[S];
+    digits<S>(fixed_point(x, shift), d);
+    const int off = ((row >> 3) * KG + (col >> 3)) * kChunkPad + (row & 7) * 8 + (col & 7);
+#pragma unroll
+    for (int s2 = 0; s2 < S; ++s2) stg[s2 * chunks * kChunkPad + off] = int_to_bf16(d[s2]);
+  };
+  for (int i = warp; i < nA; i += nw) {
+    const int64_t o = static_cast<int64_t>(P.offA + i) * m.ld + P.offB;
+    double v[2], t[2], w[2];
+    int eT = kNoExp, eB = kNoExp;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int kk = lane + 32 * c;
+      v[c] = t[c] = w[c] = 0.0;
+      if (kk < nB) {
+        v[c] = m.V[o + kk];
+        t[c] = m.T[o + kk];
+        w[c] = m.W0[o + kk] * ci.inv4c2 - t[c];
+      }
+      const int fv = frexp_exp(v[c]), ft = frexp_exp(t[c]), fw = frexp_exp(w[c]);
+      if (fv != kNoExp) eT = max(eT, fv + kxl[c]);
+      if (ft != kNoExp) {
+        eT = max(eT, ft + kxh[c]);
+        eB = max(eB, ft + kxl[c]);
+      }
+      if (fw != kNoExp) eB = max(eB, fw + kxh[c]);
+    }
+    eT = warp_max(eT);
+    eB = warp_max(eB);
+    if (eT == kNoExp) eT = 0;
+    if (eB == kNoExp) eB = 0;
+    if (lane == 0) {
+      rexp[static_cast<size_t>(p) * TRA + i] = eT;
+      rexp[static_cast<size_t>(p) * TRA + nA + i] = eB;
+    }
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int kk = lane + 32 * c;
+      if (kk < nB) {
+        put(i, kk, v[c], 8 * S - eT + kxl[c]);
+        put(i, nB + kk, t[c], 8 * S - eT + kxh[c]);
+        put(nA + i, kk, t[c], 8 * S - eB + kxl[c]);
+        put(nA + i, nB + kk, w[c], 8 * S - eB + kxh[c]);
+      }
+    }
+  }
+  for (int r = 2 * nA + threadIdx.x; r < TRA; r += blockDim.x) rexp[static_cast<size_t>(p) * TRA + r] = 0;
+  __syncthreads();
+  uint4 *dst = reinterpret_cast<uint4 *>(out + static_cast<size_t>(p) * S * TRA * KP);
+  const int per_slice = chunks * 8;  // 16-byte words of one slice: chunk-major, 8 rows each
+  for (int wd = threadIdx.x; wd < S * per_slice; wd += blockDim.x) {
+    const int s2 = wd / per_slice, c = wd - s2 * per_slice;
+    dst[wd] = *reinterpret_cast<const uint4 *>(stg + (s2 * chunks + (c >> 3)) * kChunkPad + (c & 7) * 8);
   }
 }
 
@@ -894,6 +946,18 @@ struct Runner {
     return launched(ctx, name, st);
   }
 
+  // The stage-1 A operand of np pairs (one CTA each; requires nB <= 64, TRA >= 2 nA, KP >= 2 nB).
+  static x2c_status slice_mid(x2c_ctx *ctx, cudaStream_t st, const ClassInfo &ci, int np, int TRA, int KP,
+                              const int *kexp, __nv_bfloat16 *out, int *rexp) {
+    if (ci.nB > 64 || TRA < 2 * ci.nA || KP < 2 * ci.nB || (TRA & 7) || (KP & 7)) return X2C_ERR_ARG;
+    const int smem = S * (TRA / 8) * (KP / 8) * kChunkPad * 2;
+    auto kern = slice_mid_pair_kernel<S>;
+    X2C_TRY_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    tbegin(ctx, st);
+    kern<<<np, 512, smem, st>>>(ci, TRA, KP, kexp, out, rexp);
+    return launched(ctx, "split_slice_mid", st);
+  }
+
   template <class Src>
   static x2c_status kexp(x2c_ctx *ctx, cudaStream_t st, const Src &src, int rows, int K, int *kpos, int *kneg) {
     tbegin(ctx, st);
@@ -966,8 +1030,7 @@ struct Runner {
           X2C_TRY_CUDA(ctx, cudaMemsetAsync(reinterpret_cast<char *>(A2) + tail0, 0, (size_t)kTileM * KP2 * S * 2, st));
         }
         ClassInfo ci{dp, d_mols, nA, nB, nc, inv4c2};
-        X2C_TRY(slice(ctx, st, MidRowsPadded{ci, TRA}, rows1, rows1, 2 * nB, KP1, TRA, 1, k1p, A1, e1,
-                      "split_slice_mid"));
+        X2C_TRY(slice_mid(ctx, st, ci, np, TRA, KP1, k1p, A1, e1));
         if (trm)
           X2C_TRY(gemm_t_any(ctx, st, KP2, KP1, A1, Fs, np, ntile1,
                              Stage1T<S>{e1, k2p, eF, A2, e2, np, nA, cols1, KP2, TRA, 0}, "split_stage1"));
