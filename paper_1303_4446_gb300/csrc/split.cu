@@ -49,10 +49,38 @@ __device__ __forceinline__ size_t core_off(int r, int k, int TR, int KP, int S, 
          static_cast<size_t>((rr >> 3) * (KP >> 3) + (k >> 3)) * 64 + (rr & 7) * 8 + (k & 7);
 }
 
-// BF16 of a small integer |d| <= 256: the FP32 value has at most 8 significant bits, so its
-// upper 16 bits are the exact BF16 encoding.
-__device__ __forceinline__ __nv_bfloat16 int_to_bf16(int d) {
-  return __ushort_as_bfloat16(static_cast<unsigned short>(__float_as_uint(static_cast<float>(d)) >> 16));
+// Balanced base-256 digits of F (|F| < 2^(8S), 3 <= S <= 6) in FP32 arithmetic: the low 24
+// bits of F and the rest (plus the carry out of the low part) are exact in FP32, and each
+// digit is x - 256 rne(x / 256) with rne(y) = (y + 1.5 2^23) - 1.5 2^23 (exact for
+// |y| < 2^22); so F = sum_s d_s 2^8(S-1-s), |d_s| <= 128 for s >= 1, |d_0| <= 256 (ties go
+// to even: a valid decomposition, not necessarily the one of x2c::digits).  b[s] receives
+// the FP32 bit pattern of d_s, whose upper 16 bits are its exact BF16 encoding; no
+// int-to-float conversion per digit.
+template <int S>
+__device__ __forceinline__ void digits_f32(long long F, uint32_t (&b)[S]) {
+  static_assert(S >= 3 && S <= 6, "slices");
+  constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
+  auto cut = [&](float &x) -> float {      // returns the digit, leaves the quotient in x
+    const float q = __fsub_rn(__fmaf_rn(x, 0.00390625f, kMagic), kMagic);
+    const float d = __fmaf_rn(q, -256.0f, x);
+    x = q;
+    return d;
+  };
+  float x = static_cast<float>(static_cast<int>(F & 0xFFFFFF));
+  b[S - 1] = __float_as_uint(cut(x));
+  b[S - 2] = __float_as_uint(cut(x));
+  if constexpr (S == 3) {
+    b[0] = __float_as_uint(__fadd_rn(x, static_cast<float>(static_cast<int>(F >> 24) * 256)));
+  } else {
+    b[S - 3] = __float_as_uint(cut(x));
+    float h = __fadd_rn(static_cast<float>(static_cast<int>(F >> 24)), x);  // + carry (0 or 1)
+#pragma unroll
+    for (int s = S - 4; s >= 1; --s) b[s] = __float_as_uint(cut(h));
+    b[0] = __float_as_uint(h);
+  }
+}
+__device__ __forceinline__ __nv_bfloat16 bits_to_bf16(uint32_t f) {
+  return __ushort_as_bfloat16(static_cast<unsigned short>(f >> 16));
 }
 
 // Maximum over the warp (one redux.sync instruction).
@@ -146,10 +174,10 @@ __global__ void __launch_bounds__(256) slice8_fp64_kernel(Src src, int rows, int
   for (int i = 0; i < 4; ++i) {
     const int k = lane + 32 * i;
     if (k < KP) {
-      int d[S];
-      digits<S>(fixed_point(v[i], 8 * S - e + kx[i]), d);
+      uint32_t d[S];
+      digits_f32<S>(fixed_point(v[i], 8 * S - e + kx[i]), d);
 #pragma unroll
-      for (int s2 = 0; s2 < S; ++s2) stg[s2 * 8 * KP + (k >> 3) * 64 + rr * 8 + (k & 7)] = int_to_bf16(d[s2]);
+      for (int s2 = 0; s2 < S; ++s2) stg[s2 * 8 * KP + (k >> 3) * 64 + rr * 8 + (k & 7)] = bits_to_bf16(d[s2]);
     }
   }
   __syncthreads();
@@ -192,11 +220,11 @@ __global__ void __launch_bounds__(512) slice_mid_pair_kernel(ClassInfo ci, int T
     kxh[c] = kk < nB ? kexp[nB + kk] : 0;
   }
   auto put = [&](int row, int col, double x, int shift) {
-    int d[S];
-    digits<S>(fixed_point(x, shift), d);
+    uint32_t d[S];
+    digits_f32<S>(fixed_point(x, shift), d);
     const int off = ((row >> 3) * KG + (col >> 3)) * kChunkPad + (row & 7) * 8 + (col & 7);
 #pragma unroll
-    for (int s2 = 0; s2 < S; ++s2) stg[s2 * chunks * kChunkPad + off] = int_to_bf16(d[s2]);
+    for (int s2 = 0; s2 < S; ++s2) stg[s2 * chunks * kChunkPad + off] = bits_to_bf16(d[s2]);
   };
   for (int i = warp; i < nA; i += nw) {
     const int64_t o = static_cast<int64_t>(P.offA + i) * m.ld + P.offB;
@@ -265,15 +293,20 @@ __global__ void kexp_kernel(Src src, int rows, int K, int *kexp_pos, int *kexp_n
 }
 
 // ------------------------------------------------------------------ warp-specialised GEMM
-// Roles (576 threads): warp 0 lane 0 streams A digit slices through a kStages ring of bulk
-// copies; warp 1 lane 0 issues the tcgen05 MMAs; warps 2..17 (four per TMEM lane quarter,
-// each owning a quarter of the tile's columns) drain the S accumulators of a tile into int64
-// registers, release TMEM so the next tile's MMAs can start, and then run the epilogue.
-constexpr int kEpiWarps = 16;
-constexpr int kGemmThreads = 64 + 32 * kEpiWarps;
+// Roles: warp 0 lane 0 streams A digit slices through a kStages ring of bulk copies; warp 1
+// lane 0 issues the tcgen05 MMAs; the epilogue warps 2.. (WQ per TMEM lane quarter, each
+// owning 1/WQ of the tile's columns) drain the S accumulators of a tile into int64 registers,
+// release TMEM so the next tile's MMAs can start, and then run the epilogue.
+// The number of epilogue warps per TMEM lane quarter, WQ, is the epilogue's choice
+// (Epi::wq<NT>()): 6 for the transposed stage 1 on 96-column tiles (16 columns per warp, more
+// warps in flight for its latency-bound digit cut), 4 elsewhere (measured: the stage-2
+// epilogue is slower with 6).
+constexpr int kMaxWQ = 6;
 constexpr int kStages = 4;
 
-__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"r"(32 * kEpiWarps) : "memory"); }
+// Epilogue threads of the running CTA (all threads but the producer and MMA warps).
+__device__ __forceinline__ uint32_t epi_threads() { return blockDim.x - 64; }
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"r"(epi_threads()) : "memory"); }
 
 // True on every epilogue thread iff `v` holds on all of them (named barrier 1 with an AND
 // reduction), so the epilogue warps always take the same branch and meet at every barrier.
@@ -282,7 +315,7 @@ __device__ __forceinline__ bool epi_all(bool v) {
   asm volatile(
       "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}"
       : "=r"(r)
-      : "r"(static_cast<uint32_t>(v)), "r"(32 * kEpiWarps)
+      : "r"(static_cast<uint32_t>(v)), "r"(epi_threads())
       : "memory");
   return r != 0;
 }
@@ -292,13 +325,14 @@ struct GemmShape {
   static constexpr int KG = KP / 8;
   static constexpr uint32_t A_TILE = kTileM * KP * 2;
   static constexpr uint32_t B_TILE = NT * KP * 2;
-  static constexpr int COLS_PER_WARP = NT / 4;  // per epilogue warp
   static constexpr uint32_t TMEM_COLS = 512;
   static_assert(S * NT <= 512, "accumulators exceed TMEM");
   static_assert(KP % 16 == 0 && KP <= 128, "K");
   static_assert(NT % 16 == 0 && NT >= 16 && NT <= 256, "N");
-  static_assert(COLS_PER_WARP % 8 == 0, "columns per epilogue warp");
 };
+
+// Threads of an ozaki_gemm_kernel whose epilogue runs WQ warps per TMEM lane quarter.
+__host__ __device__ constexpr int gemm_threads(int wq) { return 64 + 128 * wq; }
 
 // Stage 1 epilogue fused with the slicing of the stage-2 A operand.  A tile is one pair:
 // rows (Y, i) of atom A (2 nA <= 128), columns c = (j, q) of the N tile.  For each group of
@@ -316,7 +350,9 @@ struct Stage1Fused {
   int n_pairs, nA, cols1, KP2, tra;
   int perm;
   static int stage_bytes(int NT) { return 4 * NT * 4 + 64; }  // per (quarter, column) maxima
-  template <int NC>
+  template <int NT>
+  __host__ __device__ static constexpr int wq() { return 4; }
+  template <int NC, int WQ>
   __device__ __forceinline__ void operator()(int mt, int nt, int NT, int rloc, int c0, const long long (&I)[NC],
                                              int lane, uint8_t *stage) const {
     int *red = reinterpret_cast<int *>(stage);  // [4 quarters][NT columns]
@@ -367,12 +403,12 @@ struct Stage1Fused {
         if (quat_sign(q ^ perm, q) < 0) v = -v;
       }
       const int r2 = p * cols1 + cd;
-      int d[S];
-      digits<S>(rowv ? shift_round(v, ek - bl[j] + 8 * S) : 0, d);
+      uint32_t d[S];
+      digits_f32<S>(rowv ? shift_round(v, ek - bl[j] + 8 * S) : 0, d);
       const size_t o0 = core_off(r2, rloc, kTileM, KP2, S, 0);
       const size_t slice_stride = static_cast<size_t>(kTileM) * KP2;
 #pragma unroll
-      for (int s2 = 0; s2 < S; ++s2) A2[o0 + s2 * slice_stride] = int_to_bf16(d[s2]);
+      for (int s2 = 0; s2 < S; ++s2) A2[o0 + s2 * slice_stride] = bits_to_bf16(d[s2]);
       if (rloc == 0) e2[r2] = bl[j] + eF[c] - 8 * (S + 1);
     }
     epi_sync();
@@ -393,15 +429,18 @@ struct Stage1T {
   int *e2;
   int n_pairs, nA, cols1, KP2, tra;  // tra = rows of the streamed operand per pair (NT)
   int perm;                           // spin-orbit pass k (SOP): row (j, q) -> (j, q xor k), signed
-  static int stage_bytes(int) { return 2 * 4 * 4 * 32 * 4 + 64; }  // [parity][quarter][sub][lane]
-  template <int NC>
+  static int stage_bytes(int) { return 2 * 4 * kMaxWQ * 32 * 4 + 64; }  // [parity][quarter][sub][lane]
+  template <int NT>
+  __host__ __device__ static constexpr int wq() { return NT % 48 == 0 ? 6 : 4; }
+  template <int NC, int WQ>
   __device__ __forceinline__ void operator()(int mt, int nt, int NT, int rloc, int c0, const long long (&I)[NC],
                                              int lane, uint8_t *stage) const {
     static_assert(NC % 8 == 0, "columns per warp");
     const int p = mt;
     const int quarter = rloc >> 5, sub = c0 / NC;
     const int par = ((mt - static_cast<int>(blockIdx.y)) / static_cast<int>(gridDim.y)) & 1;
-    int *red = reinterpret_cast<int *>(stage) + par * (4 * 4 * 32);
+    int *red = reinterpret_cast<int *>(stage) + par * (4 * kMaxWQ * 32);
+    constexpr int wq = WQ;  // warps of this lane quarter
     const int c = nt * kTileM + rloc;
     const bool cv = c < cols1;
     const int rows_p = 2 * nA;
@@ -416,10 +455,10 @@ struct Stage1T {
         m = max(m, 64 - __clzll(static_cast<long long>(a)) + __ldg(e1p + r) + __ldg(k2p + r));
       }
     }
-    red[(quarter * 4 + sub) * 32 + lane] = m;
-    asm volatile("bar.sync %0, 128;" ::"r"(2 + quarter) : "memory");
-    m = max(max(red[(quarter * 4) * 32 + lane], red[(quarter * 4 + 1) * 32 + lane]),
-            max(red[(quarter * 4 + 2) * 32 + lane], red[(quarter * 4 + 3) * 32 + lane]));
+    red[(quarter * kMaxWQ + sub) * 32 + lane] = m;
+    asm volatile("bar.sync %0, %1;" ::"r"(2 + quarter), "r"(32 * wq) : "memory");
+#pragma unroll
+    for (int u = 0; u < wq; ++u) m = max(m, red[(quarter * kMaxWQ + u) * 32 + lane]);
     m = max(m, __shfl_xor_sync(0xffffffffu, m, 1));  // the 4 quaternion rows of one j
     m = max(m, __shfl_xor_sync(0xffffffffu, m, 2));
     if (m == kNoExp) m = 0;
@@ -439,16 +478,15 @@ struct Stage1T {
       uint32_t w[S][4];
 #pragma unroll
       for (int jj = 0; jj < 8; jj += 2) {
-        int d0[S], d1[S];
+        uint32_t d0[S], d1[S];
         const int j = g + jj;
         const long long v0 = neg ? -I[j] : I[j], v1 = neg ? -I[j + 1] : I[j + 1];
         const int r0 = c0 + j, r1 = r0 + 1;
-        digits<S>(r0 < rows_p ? shift_round(v0, __ldg(e1p + r0) + __ldg(k2p + r0) - m + 8 * S) : 0, d0);
-        digits<S>(r1 < rows_p ? shift_round(v1, __ldg(e1p + r1) + __ldg(k2p + r1) - m + 8 * S) : 0, d1);
+        digits_f32<S>(r0 < rows_p ? shift_round(v0, __ldg(e1p + r0) + __ldg(k2p + r0) - m + 8 * S) : 0, d0);
+        digits_f32<S>(r1 < rows_p ? shift_round(v1, __ldg(e1p + r1) + __ldg(k2p + r1) - m + 8 * S) : 0, d1);
 #pragma unroll
         for (int s2 = 0; s2 < S; ++s2)
-          w[s2][jj >> 1] = static_cast<uint32_t>(__bfloat16_as_ushort(int_to_bf16(d0[s2]))) |
-                           (static_cast<uint32_t>(__bfloat16_as_ushort(int_to_bf16(d1[s2]))) << 16);
+          w[s2][jj >> 1] = __byte_perm(d0[s2], d1[s2], 0x7632);  // upper halves: two BF16
       }
       const size_t o0 = core_off(r2, c0 + g, kTileM, KP2, S, 0);
 #pragma unroll
@@ -485,10 +523,12 @@ struct Stage2Store {
   static constexpr int JT = kTileM / NCQ;
   static constexpr int JTP = NCQ == 4 ? JT + 1 : JT;  // two-component: padded row stride
   static int stage_bytes(int NT) { return NT * JTP * 8 + JT * static_cast<int>(sizeof(SlotInfo<NCQ>)) + 16; }
-  template <int NC>
+  template <int NT>
+  __host__ __device__ static constexpr int wq() { return 4; }
+  template <int NC, int WQ>
   __device__ __forceinline__ void operator()(int mt, int nt, int NT, int rloc, int c0, const long long (&I)[NC],
                                              int lane, uint8_t *stage) const {
-    constexpr int IT = 4 * NC / NCQ;  // i' slots per tile (NT = 4 NC columns: compile-time)
+    constexpr int IT = WQ * NC / NCQ;  // i' slots per tile (NT = WQ NC columns: compile-time)
     (void)NT;
     double *sv = reinterpret_cast<double *>(stage);
     SlotInfo<NCQ> *slot = reinterpret_cast<SlotInfo<NCQ> *>(stage + static_cast<size_t>(NT) * JTP * 8);
@@ -568,7 +608,7 @@ struct Stage2Store {
     }
     (void)lane;
     epi_sync();
-    constexpr int nthr = 32 * kEpiWarps;
+    constexpr int nthr = 128 * WQ;
     const int iv = min(IT, nA - nt * IT);  // valid i' slots of this N tile
     const int ip0 = nt * IT;
     // h_AB: rows offA + i', contiguous along j
@@ -602,10 +642,12 @@ struct Stage2Store {
 // (128 rows) stays resident per CTA (M tile blockIdx.x) and NT-row B tiles stream; the
 // pointer A is always the streamed operand and B the resident one.
 template <int S, int NT, int KP, class Epi, bool TRM = false>
-__global__ void __launch_bounds__(kGemmThreads, 1)
+__global__ void __launch_bounds__(gemm_threads(Epi::template wq<NT>()), 1)
     ozaki_gemm_kernel(const __nv_bfloat16 *__restrict__ A, const __nv_bfloat16 *__restrict__ B, int m_tiles,
                       int a_rows, Epi epi, int stage_bytes, int *status) {
   using G = GemmShape<S, NT, KP>;
+  constexpr int WQ = Epi::template wq<NT>();
+  static_assert((NT / WQ) % 8 == 0 && NT % WQ == 0, "columns per epilogue warp");
   constexpr uint32_t RES_TILE = TRM ? G::A_TILE : G::B_TILE;   // resident slice bytes
   constexpr uint32_t STR_TILE = TRM ? G::B_TILE : G::A_TILE;   // streamed slice bytes
   extern __shared__ __align__(128) uint8_t smem[];
@@ -628,7 +670,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       umma::mbar_init(&empty[i], 1);
     }
     umma::mbar_init(acc_full, 1);
-    umma::mbar_init(acc_empty, kEpiWarps);
+    umma::mbar_init(acc_empty, 4 * WQ);
     umma::fence_barrier_init();
   }
   if (warp == 0) {
@@ -723,7 +765,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     const int e = warp - 2;
     const int quarter = warp & 3;              // TMEM lanes 32*quarter .. +31
     const int sub = e >> 2;                    // which quarter of the columns
-    constexpr int CW = G::COLS_PER_WARP;
+    constexpr int CW = NT / WQ;
     const int rloc = quarter * 32 + lane;
     const uint32_t lane_addr = tmem + (static_cast<uint32_t>(quarter * 32) << 16);
     for (int ti = 0; ti < n_my; ++ti) {
@@ -758,7 +800,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       umma::fence_before_sync();
       __syncwarp();
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(umma::smem_u32(acc_empty)) : "memory");
-      epi.template operator()<CW>(mt, nt, NT, rloc, sub * CW, I, lane, sStage);
+      epi.template operator()<CW, WQ>(mt, nt, NT, rloc, sub * CW, I, lane, sStage);
     }
   }
   __syncthreads();
@@ -866,7 +908,7 @@ struct Runner {
     const int per_n = std::max(1, std::min(m_tiles, std::max(1, sms / n_tiles)));
     dim3 grid(n_tiles, per_n);
     tbegin(ctx, st);
-    kern<<<grid, kGemmThreads, smem, st>>>(A, B, m_tiles, a_rows, epi, stage_bytes, ctx->d_status);
+    kern<<<grid, gemm_threads(Epi::template wq<NT>()), smem, st>>>(A, B, m_tiles, a_rows, epi, stage_bytes, ctx->d_status);
     return launched(ctx, name, st);
   }
 
@@ -900,7 +942,7 @@ struct Runner {
     const int per_n = std::max(1, std::min(m_tiles, std::max(1, sms / n_tiles)));
     dim3 grid(n_tiles, per_n);
     tbegin(ctx, st);
-    kern<<<grid, kGemmThreads, smem, st>>>(Astream, Bres, m_tiles, NTs, epi, stage_bytes, ctx->d_status);
+    kern<<<grid, gemm_threads(Epi::template wq<NTs>()), smem, st>>>(Astream, Bres, m_tiles, NTs, epi, stage_bytes, ctx->d_status);
     return launched(ctx, name, st);
   }
   static bool trm_ok(int nc, int KP1, int KP2) {
