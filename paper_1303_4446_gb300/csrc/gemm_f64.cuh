@@ -23,9 +23,15 @@ struct TileCfg {
 };
 
 // Shapes: M(b), N(b), K(b) per batch entry; the K loop runs over [K0(b), K(b)).
+// An optional gate: with gate set, a launch for iteration `step` does nothing (M = 0, every
+// CTA returns at once) when *gate <= step — iterations the device has found unnecessary.
+__device__ __forceinline__ bool gated(const int *gate, int step) { return gate && *gate <= step; }
+
 struct UniformDims {
   int m, n, k;
-  __device__ int M(int) const { return m; }
+  const int *gate = nullptr;
+  int step = 0;
+  __device__ int M(int) const { return gated(gate, step) ? 0 : m; }
   __device__ int N(int) const { return n; }
   __device__ int K(int) const { return k; }
   __device__ int K0(int) const { return 0; }
@@ -36,7 +42,9 @@ struct UniformDims {
 // of their part are skipped and the epilogue writes the mirror.
 struct HermDims {
   int m, n, k, part;
-  __device__ int M(int) const { return m; }
+  const int *gate = nullptr;
+  int step = 0;
+  __device__ int M(int) const { return gated(gate, step) ? 0 : m; }
   __device__ int N(int) const { return n; }
   __device__ int K(int) const { return k; }
   __device__ int K0(int) const { return 0; }
@@ -143,6 +151,40 @@ struct StoreShiftIdentityHerm {
     double v = alpha * acc;
     if (r == c && r < m) v += shift;
     out[b * bs + (int64_t)r * ld + c] = v;
+    if (i < c) out[b * bs + (int64_t)(p * m + c) * ld + i] = p == 0 ? v : -v;
+  }
+};
+
+// Newton-Schulz sign step with a per-problem coefficient a = a_k[b * stride] (device):
+// out = (3a/2) Z - (a^3/2) acc, acc = Z Y.  The Herm variant writes i <= c and mirrors.
+struct StoreSignStep {
+  double *out;
+  const double *z;
+  int64_t ld, bs;
+  const double *a;
+  int stride;
+  __device__ __forceinline__ void operator()(int b, int r, int c, double acc) const {
+    const double av = a[b * stride];
+    const int64_t o = b * bs + (int64_t)r * ld + c;
+    double v = (-0.5 * av * av * av) * acc;
+    v += (1.5 * av) * z[o];
+    out[o] = v;
+  }
+};
+struct StoreSignStepHerm {
+  double *out;
+  const double *z;
+  int64_t ld, bs;
+  const double *a;
+  int stride, m;
+  __device__ __forceinline__ void operator()(int b, int r, int c, double acc) const {
+    const int p = r / m, i = r - p * m;
+    if (i > c) return;
+    const double av = a[b * stride];
+    const int64_t o = b * bs + (int64_t)r * ld + c;
+    double v = (-0.5 * av * av * av) * acc;
+    v += (1.5 * av) * z[o];
+    out[o] = v;
     if (i < c) out[b * bs + (int64_t)(p * m + c) * ld + i] = p == 0 ? v : -v;
   }
 };
@@ -255,7 +297,9 @@ struct SplitOpB {
 };
 struct SplitDims {
   int m, n, k, kc, batch;
-  __device__ int M(int) const { return m; }
+  const int *gate = nullptr;
+  int step = 0;
+  __device__ int M(int) const { return gated(gate, step) ? 0 : m; }
   __device__ int N(int) const { return n; }
   __device__ int K0(int b) const { return (b / batch) * kc; }
   __device__ int K(int b) const { return min(k, (b / batch + 1) * kc); }
@@ -270,7 +314,9 @@ struct PartialStore {
   }
 };
 template <class COp>
-__global__ void splitk_reduce_kernel(const double *part, int splits, int batch, int m, int n, COp C) {
+__global__ void splitk_reduce_kernel(const double *part, int splits, int batch, int m, int n, COp C,
+                                     const int *gate, int step) {
+  if (gated(gate, step)) return;
   const int64_t mn = static_cast<int64_t>(m) * n;
   const int64_t total = mn * batch;
   for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
@@ -287,16 +333,18 @@ __global__ void splitk_reduce_kernel(const double *part, int splits, int batch, 
 // `part` must hold splits * batch * m * n doubles (splits chosen by the caller).
 template <class Cfg, class AOp, class BOp, class COp>
 inline x2c_status gemm_f64_splitk(x2c_ctx *ctx, cudaStream_t st, int batch, int m, int n, int k, int splits,
-                                  double *part, const AOp &A, const BOp &B, const COp &C, const char *name) {
-  if (splits <= 1) return gemm_f64<Cfg>(ctx, st, batch, m, n, A, B, C, UniformDims{m, n, k}, name);
+                                  double *part, const AOp &A, const BOp &B, const COp &C, const char *name,
+                                  const int *gate = nullptr, int step = 0) {
+  if (splits <= 1) return gemm_f64<Cfg>(ctx, st, batch, m, n, A, B, C, UniformDims{m, n, k, gate, step}, name);
   const int kc = ((k + splits - 1) / splits + Cfg::KC - 1) / Cfg::KC * Cfg::KC;
   splits = (k + kc - 1) / kc;
   X2C_TRY((gemm_f64<Cfg>(ctx, st, batch * splits, m, n, SplitOp<AOp>{A, batch}, SplitOpB<BOp>{B, batch},
-                         PartialStore{part, static_cast<int64_t>(m) * n, n}, SplitDims{m, n, k, kc, batch}, name)));
+                         PartialStore{part, static_cast<int64_t>(m) * n, n},
+                         SplitDims{m, n, k, kc, batch, gate, step}, name)));
   const int64_t total = static_cast<int64_t>(m) * n * batch;
   const int blocks = static_cast<int>(std::min<int64_t>((total + 255) / 256, 152 * 8));
   tbegin(ctx, st);
-  splitk_reduce_kernel<<<blocks, 256, 0, st>>>(part, splits, batch, m, n, C);
+  splitk_reduce_kernel<<<blocks, 256, 0, st>>>(part, splits, batch, m, n, C, gate, step);
   return launched(ctx, "splitk_reduce", st);
 }
 

@@ -31,10 +31,19 @@
 namespace x2c {
 namespace {
 
-constexpr double kSignLowerBound = 1e-6;   // assumed min |eig| / ||Z|| for the schedule
+constexpr double kSignLowerBound = 1e-6;   // smallest min |eig| / ||Z|| the schedule allows for
+// The per-problem schedule starts from l0 = kSignGap c^2 / G (G: the Gershgorin bound that
+// scales Z), clamped to [kSignLowerBound, 0.5]: the eigenvalues of Z = H^p + c^2 are E + c^2,
+// the negative-energy branch lies below -c^2 and the electronic one above -c^2 (1 - sqrt(1 -
+// (Z/c)^2)) for a point nucleus, so |E + c^2| >= 0.5 c^2 up to Z = 118; the margin of 2 more
+// covers basis and potential variations.  A violation costs iterations (up to the schedule of
+// kSignLowerBound) or, beyond that, the convergence check's X2C_ERR_NOCONV: never a wrong h.
 constexpr int kSqrtIters = 8;              // coupled Newton-Schulz steps for P_LL^(+-1/2)
 constexpr double kSignTol = 1e-7;          // ||Z^2 - 1|| at the last sign step
+constexpr double kSignGap = 0.25;
 constexpr double kSqrtTol = 1e-7;          // ||T - 1|| at the last square-root step
+
+constexpr int kSignMaxSteps = 64;  // bound on any schedule length (sign_schedule stops at 61)
 
 std::vector<double> sign_schedule(double l0) {
   std::vector<double> a;
@@ -301,6 +310,39 @@ __global__ void scale_kernel(int64_t per, double *Z, const unsigned long long *m
     z[idx] *= inv;
 }
 
+// Per-problem scaled Newton-Schulz schedule (the host's sign_schedule, from the problem's own
+// lower bound l0 = kSignGap c^2 / G): a[b * kmax + k] for k < kmax, then 1.0 (plain steps,
+// which leave a converged sign unchanged).  *n_eff = the longest schedule, rounded up to the
+// parity of kmax so that the last executed step leaves the iterate in the buffer the host
+// expects after kmax steps; steps k >= *n_eff are skipped (the gate of their products).
+__global__ void sign_schedule_kernel(int nb, double c2, const unsigned long long *mx, double *a, int kmax,
+                                     int *n_eff) {
+  __shared__ int nmax;
+  if (threadIdx.x == 0) nmax = 0;
+  __syncthreads();
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    double g = __longlong_as_double(static_cast<long long>(mx[b]));
+    if (!(g > 0.0) || !isfinite(g)) g = 1.0;
+    double l = fmin(fmax(kSignGap * c2 / g, kSignLowerBound), 0.5);
+    int k = 0;
+    while (1.0 - l > 1e-15 && k < kmax - 1) {
+      const double al = sqrt(3.0 / (1.0 + l + l * l));
+      a[b * kmax + k++] = al;
+      const double x = al * l;
+      l = fmin(1.5 * x - 0.5 * x * x * x, 1.5 * al - 0.5 * al * al * al);
+    }
+    const int n = k + 1;  // and one plain step to settle the rounding level
+    for (; k < kmax; ++k) a[b * kmax + k] = 1.0;
+    atomicMax(&nmax, n);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int n = nmax;
+    if ((kmax - n) & 1) ++n;
+    *n_eff = min(n, kmax);
+  }
+}
+
 // Convergence checks: ||Y - 1||_max of the last squared iterate (into dev[problem]) and,
 // for the sign function, trace Z_0 (into tr[problem]); both zeroed before.
 __global__ void deviation_kernel(int d, int nc, const double *Y, unsigned long long *dev) {
@@ -396,7 +438,8 @@ SolvePlan plan_product(int nb, int M, int m, int K, bool can_split) {
 // Small problems are split along K into a partial buffer (`part`, see quat_part_doubles).
 template <class COp>
 x2c_status quat_gemm(x2c_ctx *ctx, cudaStream_t st, int nb, int m, int nc, const double *A,
-                     const double *B, double scale, const COp &C, double *part) {
+                     const double *B, double scale, const COp &C, double *part, const int *gate = nullptr,
+                     int step = 0) {
   QuatLeft<false> a{A, m, (int64_t)nc * m * m, (int64_t)m * m, m, nc, scale};
   Mat<false> b{B, m, (int64_t)nc * m * m, 1.0};
   const int M = nc * m, K = nc * m;
@@ -404,14 +447,15 @@ x2c_status quat_gemm(x2c_ctx *ctx, cudaStream_t st, int nb, int m, int nc, const
   const char *name = "solve_quat_gemm";
   switch (p.tile) {
     case SolveTile::Tiny:
-      if (p.splits > 1) return gemm_f64_splitk<TileTiny>(ctx, st, nb, M, m, K, p.splits, part, a, b, C, name);
-      return gemm_f64<TileTiny>(ctx, st, nb, M, m, a, b, C, UniformDims{M, m, K}, name);
+      if (p.splits > 1)
+        return gemm_f64_splitk<TileTiny>(ctx, st, nb, M, m, K, p.splits, part, a, b, C, name, gate, step);
+      return gemm_f64<TileTiny>(ctx, st, nb, M, m, a, b, C, UniformDims{M, m, K, gate, step}, name);
     case SolveTile::Small:
-      return gemm_f64_splitk<TileSmall>(ctx, st, nb, M, m, K, p.splits, part, a, b, C, name);
+      return gemm_f64_splitk<TileSmall>(ctx, st, nb, M, m, K, p.splits, part, a, b, C, name, gate, step);
     case SolveTile::Large:
-      return gemm_f64<TileLarge>(ctx, st, nb, M, m, a, b, C, UniformDims{M, m, K}, name);
+      return gemm_f64<TileLarge>(ctx, st, nb, M, m, a, b, C, UniformDims{M, m, K, gate, step}, name);
     default:
-      return gemm_f64<TileSolve>(ctx, st, nb, M, m, a, b, C, UniformDims{M, m, K}, name);
+      return gemm_f64<TileSolve>(ctx, st, nb, M, m, a, b, C, UniformDims{M, m, K, gate, step}, name);
   }
 }
 
@@ -421,11 +465,11 @@ x2c_status quat_gemm(x2c_ctx *ctx, cudaStream_t st, int nb, int m, int nc, const
 constexpr int kHermMin = 256;
 template <class COp>
 x2c_status quat_gemm_herm(x2c_ctx *ctx, cudaStream_t st, int nb, int m, int nc, const double *A,
-                          const double *B, const COp &C) {
+                          const double *B, const COp &C, const int *gate = nullptr, int step = 0) {
   QuatLeft<false> a{A, m, (int64_t)nc * m * m, (int64_t)m * m, m, nc, 1.0};
   Mat<false> b{B, m, (int64_t)nc * m * m, 1.0};
   const int M = nc * m, K = nc * m;
-  return gemm_f64<TileLarge>(ctx, st, nb, M, m, a, b, C, HermDims{M, m, K, m}, "solve_quat_gemm");
+  return gemm_f64<TileLarge>(ctx, st, nb, M, m, a, b, C, HermDims{M, m, K, m, gate, step}, "solve_quat_gemm");
 }
 
 // Square-ish products of the solve (no split-K): tile by size.
@@ -505,7 +549,8 @@ size_t solve_workspace_bytes(int nb, int n, int nc) {
   const size_t per = (6 + 23 * (size_t)nc) * n2;
   const size_t part = std::max(quat_part_doubles(nb, 2 * n, nc), quat_part_doubles(nb, n, nc));
   const size_t big = n > kMaxSolveN ? arena_doubles(n2) + arena_doubles(n2 / 4 + 32 * (size_t)n) : 0;
-  return arena_doubles(per * nb) + arena_doubles(part) + big + 2 * arena_doubles(nb) + 20 * 256;
+  return arena_doubles(per * nb) + arena_doubles(part) + big + 2 * arena_doubles(nb) +
+         arena_doubles((size_t)nb * kSignMaxSteps) + arena_doubles(1) + 20 * 256;
 }
 
 x2c_status solve_transforms(x2c_ctx *ctx, cudaStream_t st, double c, int nb, int n, int nc,
@@ -525,7 +570,9 @@ x2c_status solve_transforms(x2c_ctx *ctx, cudaStream_t st, double c, int nb, int
   double *XR = ar.take(nb * nc * n2), *tmp2 = ar.take(nb * nc * n2);
   auto *slot = reinterpret_cast<unsigned long long *>(ar.take(nb));
   double *trace = ar.take(nb);
-  if (!tmp2 || !slot || !trace) return X2C_ERR_NOMEM;
+  double *sched = ar.take((size_t)nb * kSignMaxSteps);
+  int *gate = reinterpret_cast<int *>(ar.take(1));
+  if (!tmp2 || !slot || !trace || !sched || !gate) return X2C_ERR_NOMEM;
   const size_t part_n = std::max(quat_part_doubles(nb, d, nc), quat_part_doubles(nb, n, nc));
   double *part = part_n ? ar.take(part_n) : nullptr;
   if (part_n && !part) return X2C_ERR_NOMEM;
@@ -581,19 +628,26 @@ x2c_status solve_transforms(x2c_ctx *ctx, cudaStream_t st, double c, int nb, int
   tbegin(ctx, st);
   scale_kernel<<<aux_grid(nb, nc * d2), 256, 0, st>>>(nc * d2, Z, slot, status);
   X2C_TRY(launched(ctx, "scale_kernel", st));
-  // 3. Sign function by the scaled Newton-Schulz schedule.
-  const std::vector<double> sched = sign_schedule(kSignLowerBound);
+  // 3. Sign function by the scaled Newton-Schulz schedule, per problem (sign_schedule_kernel);
+  // the host enqueues the longest possible schedule and the device skips the steps past the
+  // longest one it needs.
+  const int kmax = static_cast<int>(sign_schedule(kSignLowerBound).size());
+  if (kmax > kSignMaxSteps) return X2C_ERR_ARG;
+  tbegin(ctx, st);
+  sign_schedule_kernel<<<1, 256, 0, st>>>(nb, c * c, slot, sched, kmax, gate);
+  X2C_TRY(launched(ctx, "sign_schedule_kernel", st));
   const bool herm_d = d >= kHermMin, herm_n = n >= kHermMin;
-  for (double a : sched) {
+  for (int k = 0; k < kmax; ++k) {
     // Y = Z Z;  Zn = (3a/2) Z - (a^3/2) Z Y   (Z, Y commute and are Hermitian)
     if (herm_d) {
-      X2C_TRY(quat_gemm_herm(ctx, st, nb, d, nc, Z, Z, StoreAxpbyHerm{Y, nullptr, d, (int64_t)nc * d2, 1.0, 0.0, d}));
+      X2C_TRY(quat_gemm_herm(ctx, st, nb, d, nc, Z, Z, StoreAxpbyHerm{Y, nullptr, d, (int64_t)nc * d2, 1.0, 0.0, d},
+                             gate, k));
       X2C_TRY(quat_gemm_herm(ctx, st, nb, d, nc, Z, Y,
-                             StoreAxpbyHerm{Zn, Z, d, (int64_t)nc * d2, -0.5 * a * a * a, 1.5 * a, d}));
+                             StoreSignStepHerm{Zn, Z, d, (int64_t)nc * d2, sched + k, kmax, d}, gate, k));
     } else {
-      X2C_TRY(quat_gemm(ctx, st, nb, d, nc, Z, Z, 1.0, store_plain(Y, d, nc), part));
-      StoreAxpby upd{Zn, Z, d, (int64_t)nc * d2, -0.5 * a * a * a, 1.5 * a};
-      X2C_TRY(quat_gemm(ctx, st, nb, d, nc, Z, Y, 1.0, upd, part));
+      X2C_TRY(quat_gemm(ctx, st, nb, d, nc, Z, Z, 1.0, store_plain(Y, d, nc), part, gate, k));
+      StoreSignStep upd{Zn, Z, d, (int64_t)nc * d2, sched + k, kmax};
+      X2C_TRY(quat_gemm(ctx, st, nb, d, nc, Z, Y, 1.0, upd, part, gate, k));
     }
     std::swap(Z, Zn);
   }
