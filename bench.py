@@ -809,7 +809,12 @@ def main():
         t_e2e = (time.perf_counter() - t0) / args.e2e_steps
         t_e2e_max = max_over_ranks(t_e2e, dist, dev)
         sz = np.diff(mol.offsets)
-        h2d = 8 * (3 * N * N + (3 * int((sz * sz).sum()) if two_c else 0) + (3 + (4 if two_c else 1)) * len(kind["S"]) ** 2)
+        # what x2c_build_dlu_host copies: the upper block triangle of T, V, W0, the same-atom
+        # blocks of Wx..Wz (and of S in molecular-block mode), the kind matrices
+        upper = int((sz * (N - np.asarray(mol.offsets[:-1]))).sum())
+        diag = int((sz * sz).sum())
+        kinds_h2d = 0 if cfg.get("mb") else (3 + (4 if two_c else 1)) * len(kind["S"]) ** 2
+        h2d = 8 * (3 * upper + (3 * diag if two_c else 0) + (diag if cfg.get("mb") else 0) + kinds_h2d)
         line["e2e"] = {"value": job_rate(world, t_e2e_max), "unit": "builds/s", "h2d_bytes_per_step": int(h2d),
                        "d2h_bytes_per_step": int(8 * nc * N * N), "steps": args.e2e_steps}
         del pin, hout

@@ -219,7 +219,10 @@ x2c_status x2c_atomic_transforms_noalloc(const x2c_options *opt, int32_t n_probl
 /* DLU from HOST buffers (pageable or pinned): copies the inputs the method reads to the
  * device, builds, and copies h back into the caller's host buffers, all on `stream`;
  * returns after the stream has finished.  Arguments as x2c_build_dlu, but every matrix
- * pointer (mol, kinds, h) is a host pointer. */
+ * pointer (mol, kinds, h) is a host pointer.  Only what the build reads crosses to the
+ * device: the upper block triangle (blocks A <= B) of T, V and W0 (DLH: T and V whole, the
+ * same-atom blocks of W0), the same-atom blocks of S (molecular-block mode) and of Wx, Wy,
+ * Wz (so_same_atom_only = 1; else their upper block triangle); h comes back whole. */
 x2c_status x2c_build_dlu_host(x2c_ctx *ctx, const x2c_options *opt, const x2c_layout *layout,
                               const x2c_mats *mol, const x2c_hout *h, void *stream);
 

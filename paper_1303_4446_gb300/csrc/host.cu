@@ -19,6 +19,18 @@ x2c_status copy_diag_blocks(x2c_ctx *ctx, double *dst, const double *src, int64_
   return X2C_OK;
 }
 
+// Copy the upper block triangle (rows of atom a, columns from the atom's first function to
+// N - 1) of an N x N host matrix into the same places of a device matrix.
+x2c_status copy_upper_blocks(x2c_ctx *ctx, double *dst, const double *src, int64_t N, const x2c_layout *lay,
+                             cudaStream_t st) {
+  for (int a = 0; a < lay->n_atoms; ++a) {
+    const int64_t o = lay->atom_offset[a], n = lay->atom_offset[a + 1] - o;
+    X2C_TRY_CUDA(ctx, cudaMemcpy2DAsync(dst + o * N + o, N * sizeof(double), src + o * N + o, N * sizeof(double),
+                                        (N - o) * sizeof(double), n, cudaMemcpyHostToDevice, st));
+  }
+  return X2C_OK;
+}
+
 }  // namespace
 
 extern "C" x2c_status x2c_build_dlu_host(x2c_ctx *ctx, const x2c_options *opt, const x2c_layout *lay,
@@ -53,14 +65,41 @@ extern "C" x2c_status x2c_build_dlu_host(x2c_ctx *ctx, const x2c_options *opt, c
   double *dh[4] = {nullptr, nullptr, nullptr, nullptr};
   for (int q = 0; q < nc; ++q) { dh[q] = next; next += N2; }
   const size_t full = N2 * sizeof(double);
-  X2C_TRY_CUDA(ctx, cudaMemcpyAsync(dT, mol->T, full, cudaMemcpyHostToDevice, st));
-  X2C_TRY_CUDA(ctx, cudaMemcpyAsync(dV, mol->V, full, cudaMemcpyHostToDevice, st));
-  X2C_TRY_CUDA(ctx, cudaMemcpyAsync(dW0, mol->W0, full, cudaMemcpyHostToDevice, st));
-  if (mb) X2C_TRY(copy_diag_blocks(ctx, dS, mol->S, N, lay, st));
+  // The copies are spread over the call's stream and three side streams of the context, so
+  // that several copy engines move the matrices at once; the side streams start after the
+  // work already on `st` and `st` waits for them before the build (and again for the copies
+  // of h back).
+  X2C_TRY(x2c::ensure_aux_streams(ctx, 3));
+  cudaStream_t cs[4] = {st, ctx->aux[0], ctx->aux[1], ctx->aux[2]};
+  auto fork = [&]() -> x2c_status {
+    X2C_TRY_CUDA(ctx, cudaEventRecord(ctx->aux_fork, st));
+    for (int i = 1; i < 4; ++i) X2C_TRY_CUDA(ctx, cudaStreamWaitEvent(cs[i], ctx->aux_fork, 0));
+    return X2C_OK;
+  };
+  auto join = [&]() -> x2c_status {
+    for (int i = 1; i < 4; ++i) {
+      X2C_TRY_CUDA(ctx, cudaEventRecord(ctx->aux_join[i - 1], cs[i]));
+      X2C_TRY_CUDA(ctx, cudaStreamWaitEvent(st, ctx->aux_join[i - 1], 0));
+    }
+    return X2C_OK;
+  };
+  X2C_TRY(fork());
+  // the pair assembly reads the blocks A <= B; DLH reads T and V everywhere and W0 on the
+  // same-atom blocks only
+  if (opt->local_approx == X2C_LOCAL_DLH) {
+    X2C_TRY_CUDA(ctx, cudaMemcpyAsync(dT, mol->T, full, cudaMemcpyHostToDevice, cs[0]));
+    X2C_TRY_CUDA(ctx, cudaMemcpyAsync(dV, mol->V, full, cudaMemcpyHostToDevice, cs[1]));
+    X2C_TRY(copy_diag_blocks(ctx, dW0, mol->W0, N, lay, cs[2]));
+  } else {
+    X2C_TRY(copy_upper_blocks(ctx, dT, mol->T, N, lay, cs[0]));
+    X2C_TRY(copy_upper_blocks(ctx, dV, mol->V, N, lay, cs[1]));
+    X2C_TRY(copy_upper_blocks(ctx, dW0, mol->W0, N, lay, cs[2]));
+  }
+  if (mb) X2C_TRY(copy_diag_blocks(ctx, dS, mol->S, N, lay, cs[3]));
   const double *hw[3] = {mol->Wx, mol->Wy, mol->Wz};
   for (int k = 0; k < 3 && nc == 4; ++k) {
-    if (so_blocks) X2C_TRY(copy_diag_blocks(ctx, dW[k], hw[k], N, lay, st));
-    else X2C_TRY_CUDA(ctx, cudaMemcpyAsync(dW[k], hw[k], full, cudaMemcpyHostToDevice, st));
+    if (so_blocks) X2C_TRY(copy_diag_blocks(ctx, dW[k], hw[k], N, lay, cs[3]));
+    else X2C_TRY(copy_upper_blocks(ctx, dW[k], hw[k], N, lay, cs[(k + 1) % 4]));
   }
   std::vector<x2c_mats> dk;
   if (!mb) {
@@ -75,7 +114,7 @@ extern "C" x2c_status x2c_build_dlu_host(x2c_ctx *ctx, const x2c_options *opt, c
         if (!src[i]) return X2C_ERR_ARG;
         dst[i] = next;
         next += (size_t)km.n * km.n;
-        X2C_TRY_CUDA(ctx, cudaMemcpyAsync(dst[i], src[i], nb, cudaMemcpyHostToDevice, st));
+        X2C_TRY_CUDA(ctx, cudaMemcpyAsync(dst[i], src[i], nb, cudaMemcpyHostToDevice, cs[3]));
       }
       d.S = dst[0]; d.T = dst[1]; d.V = dst[2]; d.W0 = dst[3];
       d.Wx = dst[4]; d.Wy = dst[5]; d.Wz = dst[6];
@@ -90,9 +129,12 @@ extern "C" x2c_status x2c_build_dlu_host(x2c_ctx *ctx, const x2c_options *opt, c
   if (!mb) dl.kinds = dk.data();
   x2c_hout dho{};
   for (int q = 0; q < nc; ++q) dho.h[q] = dh[q];
+  X2C_TRY(join());
   X2C_TRY(x2c_build_dlu(ctx, opt, &dl, &dm, &dho, stream));
+  X2C_TRY(fork());
   for (int q = 0; q < nc; ++q)
-    X2C_TRY_CUDA(ctx, cudaMemcpyAsync(h->h[q], dh[q], full, cudaMemcpyDeviceToHost, st));
+    X2C_TRY_CUDA(ctx, cudaMemcpyAsync(h->h[q], dh[q], full, cudaMemcpyDeviceToHost, cs[q]));
+  X2C_TRY(join());
   X2C_TRY_CUDA(ctx, cudaStreamSynchronize(st));
   return X2C_OK;
 }

@@ -204,13 +204,30 @@ def test_batched_equals_single(ctx):
             assert (a - b).abs().max().item() <= 1e-13 * b.abs().max().item()
 
 
-def test_host_buffers_equal_device(ctx):
+@pytest.mark.parametrize("approx", [x.LOCAL_DLU, x.LOCAL_DLH])
+@pytest.mark.parametrize("prec", [x.PREC_FP64, x.PREC_SPLIT_BF16])
+def test_host_buffers_equal_device(ctx, approx, prec):
+    """The host-buffer call copies only the blocks the build reads: NaN in every other block
+    of the host inputs must not reach h."""
     mol = w.silver_cluster(3, "s30")
     m = w.molecule_inputs(mol, True)
     kind = w.atomic_inputs(47.0, "s30", True)
-    hd = x.x2c_build_dlu(ctx, dev(m), mol.offsets, [0] * 3, [dev(kind)], two_component=True)
+    kw = dict(two_component=True, precision=prec, local_approx=approx)
+    hd = x.x2c_build_dlu(ctx, dev(m), mol.offsets, [0] * 3, [dev(kind)], **kw)
     ctx.status()
-    hh = x.x2c_build_dlu_host(ctx, m, mol.offsets, [0] * 3, [kind], two_component=True)
+    atom = np.repeat(np.arange(3), np.diff(mol.offsets))
+    lower = atom[:, None] > atom[None, :]
+    other = atom[:, None] != atom[None, :]
+    hm = {k: v.copy() for k, v in m.items()}
+    hm["S"][other] = np.nan
+    for k in ("Wx", "Wy", "Wz"):
+        hm[k][other] = np.nan
+    if approx == x.LOCAL_DLU:
+        for k in ("T", "V", "W0"):
+            hm[k][lower] = np.nan
+    else:
+        hm["W0"][other] = np.nan
+    hh = x.x2c_build_dlu_host(ctx, hm, mol.offsets, [0] * 3, [kind], **kw)
     for a, b in zip(hd, hh):
         assert np.array_equal(a.cpu().numpy(), b)
 
