@@ -444,15 +444,19 @@ struct Stage1T {
     const int c = nt * kTileM + rloc;
     const bool cv = c < cols1;
     const int rows_p = 2 * nA;
-    // the column exponents e1 + kexp2 are read twice (L1 hits) instead of held in registers
+    // the column exponents e1 + kexp2 of this warp's NC columns (the same for every lane):
+    // lane j holds the one of column c0 + j and shuffles hand it to the others
+    static_assert(NC <= 32, "one column exponent per lane");
     const int *e1p = e1 + p * tra;
+    const int ekl = (lane < NC && c0 + lane < rows_p) ? __ldg(e1p + c0 + lane) + __ldg(k2p + c0 + lane) : 0;
     int m = kNoExp;
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
       const int r = c0 + j;
+      const int ek = __shfl_sync(0xffffffffu, ekl, j);
       if (r < rows_p && I[j] != 0) {
         const unsigned long long a = I[j] < 0 ? static_cast<unsigned long long>(-I[j]) : static_cast<unsigned long long>(I[j]);
-        m = max(m, 64 - __clzll(static_cast<long long>(a)) + __ldg(e1p + r) + __ldg(k2p + r));
+        m = max(m, 64 - __clzll(static_cast<long long>(a)) + ek);
       }
     }
     red[(quarter * kMaxWQ + sub) * 32 + lane] = m;
@@ -471,7 +475,8 @@ struct Stage1T {
     }
     const int r2 = p * cols1 + cd;
     if (cv && sub == 0) e2[r2] = m + eF[c] - 8 * (S + 1);
-    if (!cv) return;
+    // every lane stays to the end: the shuffles below need the whole warp (lanes of columns
+    // c >= cols1 compute and drop their digits)
     const size_t slice_stride = static_cast<size_t>(kTileM) * KP2;
 #pragma unroll
     for (int g = 0; g < NC; g += 8) {
@@ -482,16 +487,19 @@ struct Stage1T {
         const int j = g + jj;
         const long long v0 = neg ? -I[j] : I[j], v1 = neg ? -I[j + 1] : I[j + 1];
         const int r0 = c0 + j, r1 = r0 + 1;
-        digits_f32<S>(r0 < rows_p ? shift_round(v0, __ldg(e1p + r0) + __ldg(k2p + r0) - m + 8 * S) : 0, d0);
-        digits_f32<S>(r1 < rows_p ? shift_round(v1, __ldg(e1p + r1) + __ldg(k2p + r1) - m + 8 * S) : 0, d1);
+        const int ek0 = __shfl_sync(0xffffffffu, ekl, j), ek1 = __shfl_sync(0xffffffffu, ekl, j + 1);
+        digits_f32<S>(r0 < rows_p ? shift_round(v0, ek0 - m + 8 * S) : 0, d0);
+        digits_f32<S>(r1 < rows_p ? shift_round(v1, ek1 - m + 8 * S) : 0, d1);
 #pragma unroll
         for (int s2 = 0; s2 < S; ++s2)
           w[s2][jj >> 1] = __byte_perm(d0[s2], d1[s2], 0x7632);  // upper halves: two BF16
       }
-      const size_t o0 = core_off(r2, c0 + g, kTileM, KP2, S, 0);
+      if (cv) {
+        const size_t o0 = core_off(r2, c0 + g, kTileM, KP2, S, 0);
 #pragma unroll
-      for (int s2 = 0; s2 < S; ++s2)
-        *reinterpret_cast<uint4 *>(A2 + o0 + s2 * slice_stride) = make_uint4(w[s2][0], w[s2][1], w[s2][2], w[s2][3]);
+        for (int s2 = 0; s2 < S; ++s2)
+          *reinterpret_cast<uint4 *>(A2 + o0 + s2 * slice_stride) = make_uint4(w[s2][0], w[s2][1], w[s2][2], w[s2][3]);
+      }
     }
   }
 };
