@@ -438,10 +438,13 @@ void x2c_server::launch(int si, std::vector<ReqPtr> &batch) {
       const Blocks pair = r.rq.kind == X2C_REQ_FULL ? kAll : kUpper;
       const Blocks same = r.rq.kind == X2C_REQ_FULL ? kAll : kDiag;
       const Blocks so = (r.rq.kind == X2C_REQ_FULL || !opt.so_same_atom_only) ? pair : kDiag;
+      // DLH fills the atom-other-atom blocks with T + V: all of T and V, W0 on the same-atom
+      // blocks only
+      const bool dlh = r.rq.kind == X2C_REQ_DLU && opt.local_approx == X2C_LOCAL_DLH;
       if (r.copy_in) {
-        r.dmol.T = put(r.rq.mol.T, r.n, r.ld, pair);
-        r.dmol.V = put(r.rq.mol.V, r.n, r.ld, pair);
-        r.dmol.W0 = put(r.rq.mol.W0, r.n, r.ld, pair);
+        r.dmol.T = put(r.rq.mol.T, r.n, r.ld, dlh ? kAll : pair);
+        r.dmol.V = put(r.rq.mol.V, r.n, r.ld, dlh ? kAll : pair);
+        r.dmol.W0 = put(r.rq.mol.W0, r.n, r.ld, dlh ? kDiag : pair);
         // free-atom DLU never reads the molecular S: any valid device address will do
         r.dmol.S = free_atom ? r.dmol.T : put(r.rq.mol.S, r.n, r.ld, same);
         if (nc == 4) {

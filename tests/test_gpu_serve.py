@@ -114,6 +114,16 @@ def test_serving_mix_same_as_alone(ctx):
                                [ks_dev[False][0]])
     ctx.status()
 
+    # a DLH request from host memory: the server must copy all of T and V for it
+    dmol = w.silver_cluster(3, "s30")
+    dm = w.molecule_inputs(dmol, True)
+    ref_dlh = x.x2c_build_dlu(ctx, dev(dm), dmol.offsets, [0] * 3, [ks_dev[True][0]], two_component=True,
+                              local_approx=x.LOCAL_DLH)
+    ctx.status()
+    dm_h = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in dm.items()}
+    dk_h = {k: torch.from_numpy(v).pin_memory() for k, v in ks[True]["s30"].items()}
+    dlh_out = [torch.empty((dmol.nbf, dmol.nbf), dtype=torch.float64).pin_memory() for _ in range(4)]
+
     srv = x.Server(0, max_inflight=3, max_batch=4, hbm_budget_bytes=8 << 30)
     try:
         tickets, host_out = [], {}
@@ -130,6 +140,8 @@ def test_serving_mix_same_as_alone(ctx):
                                    precision=r["prec"], out=out, host=r["host"])
             tickets.append(t)
         t_view = srv.submit_dlu(view, big.offsets[:4], [0, 0, 0], [ks_dev[False][0]], kind_keys=[KEY[("s30", False)]])
+        t_dlh = srv.submit_dlu(dm_h, dmol.offsets, [0] * 3, [dk_h], kind_keys=[KEY[("s30", True)]], two_component=True,
+                               local_approx=x.LOCAL_DLH, out=dlh_out, host=True)
         results = [srv.wait(t) for t in tickets]
         for i, (r, res) in enumerate(zip(reqs, results)):
             assert res["state"] == x.STATE_DONE and res["status"] == 0, (i, res)
@@ -141,8 +153,11 @@ def test_serving_mix_same_as_alone(ctx):
         rv = srv.wait(t_view)
         assert rv["status"] == 0 and rel(srv.result_tensors(t_view, rv), ref_view) <= SAME_TOL
         srv.release(t_view)
+        rd = srv.wait(t_dlh)
+        assert rd["status"] == 0 and rel([t.cuda() for t in dlh_out], ref_dlh) <= SAME_TOL
+        srv.release(t_dlh)
         st = srv.stats()
-        assert st["completed"] == len(reqs) + 1 and st["failed"] == 0
+        assert st["completed"] == len(reqs) + 2 and st["failed"] == 0
         assert st["cache_hits"] > 0 and st["cache_misses"] <= 4
         assert st["peak_bytes"] <= st["budget_bytes"]
         assert max(res["batch_size"] for res in results) > 1
