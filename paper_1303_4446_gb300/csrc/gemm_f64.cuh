@@ -255,10 +255,11 @@ __global__ void __launch_bounds__(Cfg::NT) gemm_f64_kernel(AOp A, BOp B, COp C, 
 // Algorithmic flops of one launch, where the shape is uniform (0 otherwise).
 template <class Dims>
 inline double dims_flops(const Dims &, int) { return 0.0; }
-inline double dims_flops(const UniformDims &d, int batch) { return 2.0 * d.m * d.n * d.k * batch; }
+// A gated launch reports no flops: the device decides whether it runs.
+inline double dims_flops(const UniformDims &d, int batch) { return d.gate ? 0.0 : 2.0 * d.m * d.n * d.k * batch; }
 // Hermitian products: the upper triangle of every part (about half of the full product).
 inline double dims_flops(const HermDims &d, int batch) {
-  return (double)d.m / d.part * d.part * (d.part + 1.0) * d.k * batch;
+  return d.gate ? 0.0 : (double)d.m / d.part * d.part * (d.part + 1.0) * d.k * batch;
 }
 struct SplitDims;
 inline double dims_flops(const SplitDims &d, int);
@@ -304,7 +305,7 @@ struct SplitDims {
   __device__ int K0(int b) const { return (b / batch) * kc; }
   __device__ int K(int b) const { return min(k, (b / batch + 1) * kc); }
 };
-inline double dims_flops(const SplitDims &d, int) { return 2.0 * d.m * d.n * d.k * d.batch; }
+inline double dims_flops(const SplitDims &d, int) { return d.gate ? 0.0 : 2.0 * d.m * d.n * d.k * d.batch; }
 struct PartialStore {
   double *part;
   int64_t mn;

@@ -439,12 +439,11 @@ SolvePlan plan_product(int nb, int M, int m, int K, bool can_split) {
 template <class COp>
 x2c_status quat_gemm(x2c_ctx *ctx, cudaStream_t st, int nb, int m, int nc, const double *A,
                      const double *B, double scale, const COp &C, double *part, const int *gate = nullptr,
-                     int step = 0) {
+                     int step = 0, const char *name = "solve_quat_gemm") {
   QuatLeft<false> a{A, m, (int64_t)nc * m * m, (int64_t)m * m, m, nc, scale};
   Mat<false> b{B, m, (int64_t)nc * m * m, 1.0};
   const int M = nc * m, K = nc * m;
   const SolvePlan p = plan_product(nb, M, m, K, part != nullptr);
-  const char *name = "solve_quat_gemm";
   switch (p.tile) {
     case SolveTile::Tiny:
       if (p.splits > 1)
@@ -465,11 +464,12 @@ x2c_status quat_gemm(x2c_ctx *ctx, cudaStream_t st, int nb, int m, int nc, const
 constexpr int kHermMin = 256;
 template <class COp>
 x2c_status quat_gemm_herm(x2c_ctx *ctx, cudaStream_t st, int nb, int m, int nc, const double *A,
-                          const double *B, const COp &C, const int *gate = nullptr, int step = 0) {
+                          const double *B, const COp &C, const int *gate = nullptr, int step = 0,
+                          const char *name = "solve_quat_gemm") {
   QuatLeft<false> a{A, m, (int64_t)nc * m * m, (int64_t)m * m, m, nc, 1.0};
   Mat<false> b{B, m, (int64_t)nc * m * m, 1.0};
   const int M = nc * m, K = nc * m;
-  return gemm_f64<TileLarge>(ctx, st, nb, M, m, a, b, C, HermDims{M, m, K, m, gate, step}, "solve_quat_gemm");
+  return gemm_f64<TileLarge>(ctx, st, nb, M, m, a, b, C, HermDims{M, m, K, m, gate, step}, name);
 }
 
 // Square-ish products of the solve (no split-K): tile by size.
@@ -639,15 +639,18 @@ x2c_status solve_transforms(x2c_ctx *ctx, cudaStream_t st, double c, int nb, int
   const bool herm_d = d >= kHermMin, herm_n = n >= kHermMin;
   for (int k = 0; k < kmax; ++k) {
     // Y = Z Z;  Zn = (3a/2) Z - (a^3/2) Z Y   (Z, Y commute and are Hermitian)
+    // (named apart from the other products: how many of them run is decided on the device, so
+    // they report no flops)
+    const char *sign_name = "solve_sign_gemm";
     if (herm_d) {
       X2C_TRY(quat_gemm_herm(ctx, st, nb, d, nc, Z, Z, StoreAxpbyHerm{Y, nullptr, d, (int64_t)nc * d2, 1.0, 0.0, d},
-                             gate, k));
+                             gate, k, sign_name));
       X2C_TRY(quat_gemm_herm(ctx, st, nb, d, nc, Z, Y,
-                             StoreSignStepHerm{Zn, Z, d, (int64_t)nc * d2, sched + k, kmax, d}, gate, k));
+                             StoreSignStepHerm{Zn, Z, d, (int64_t)nc * d2, sched + k, kmax, d}, gate, k, sign_name));
     } else {
-      X2C_TRY(quat_gemm(ctx, st, nb, d, nc, Z, Z, 1.0, store_plain(Y, d, nc), part, gate, k));
+      X2C_TRY(quat_gemm(ctx, st, nb, d, nc, Z, Z, 1.0, store_plain(Y, d, nc), part, gate, k, sign_name));
       StoreSignStep upd{Zn, Z, d, (int64_t)nc * d2, sched + k, kmax};
-      X2C_TRY(quat_gemm(ctx, st, nb, d, nc, Z, Y, 1.0, upd, part, gate, k));
+      X2C_TRY(quat_gemm(ctx, st, nb, d, nc, Z, Y, 1.0, upd, part, gate, k, sign_name));
     }
     std::swap(Z, Zn);
   }
