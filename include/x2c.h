@@ -203,8 +203,8 @@ x2c_status x2c_atomic_transforms(x2c_ctx *ctx, const x2c_options *opt, int32_t n
  * all n_problems input sets must have the same n.  The call calls no cudaMalloc, cudaFree or
  * allocating library routine.  It returns X2C_ERR_NOMEM, before enqueueing anything, when the
  * problems need more scratch than the array holds: about 8 (2 nc + 6 + 23 nc) n^2 bytes per
- * problem plus 5 KB (nc = 1 spin-free, 4 two-component): e.g. up to 16 two-component problems
- * of n = 48, or 58 spin-free ones.
+ * problem plus about 6 KB (nc = 1 spin-free, 4 two-component): e.g. about 16 two-component
+ * problems of n = 48, or 58 spin-free ones.
  *
  * The first call on a device looks up the array's device address (once per device, with
  * that device current); make that first call before any stream capture.  The call is
