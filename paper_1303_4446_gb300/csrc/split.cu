@@ -1096,42 +1096,8 @@ struct Runner {
         else
           X2C_TRY((gemm_any<NT4, NT1>(ctx, st, nc, KP2, A2, Gs, rows2p / kTileM, cols2,
                            Stage2Store<1>{dp, d_mols, e2, eG, rows2, nA, nB, S, 0}, 2, kTileM, "split_stage2")));
-        // spin-orbit middle term.  Same-atom blocks only (the usual case): three more split
-        // passes over the diagonal pairs, one per quaternion part k of i sigma.W / 4c^2, whose
-        // stage 2 adds U_A+ (E_k R) to h.  All pairs (general case): FP64 products.
-        if (nc == 4 && !so_all) {
-          std::vector<PairDesc> so;
-          for (int i = 0; i < np; ++i)
-            if (cls[c0 + i].diag) so.push_back(cls[c0 + i]);
-          if (!so.empty()) {
-            const int ns = (int)so.size();
-            Arena a2 = a1;
-            PairDesc *ds = reinterpret_cast<PairDesc *>(a2.take_bytes(ns * sizeof(PairDesc)));
-            if (!ds) return X2C_ERR_NOMEM;
-            X2C_TRY(upload(ctx, st, ds, so.data(), ns * sizeof(PairDesc)));
-            const int srows1 = ns * TRA, srows2 = ns * cols1;
-            const int srows2p = (srows2 + kTileM - 1) / kTileM * kTileM;
-            if (srows2p > srows2) {
-              const size_t tail0 = (size_t)(srows2p - kTileM) * KP2 * S * 2;
-              X2C_TRY_CUDA(ctx, cudaMemsetAsync(reinterpret_cast<char *>(A2) + tail0, 0, (size_t)kTileM * KP2 * S * 2, st));
-            }
-            ClassInfo cs{ds, d_mols, nA, nB, nc, inv4c2};
-            for (int k = 1; k <= 3; ++k) {
-              X2C_TRY(slice(ctx, st, SoMidRowsPadded{cs, TRA, k}, srows1, srows1, 2 * nB, KP1, TRA, 1, k1p, A1, e1,
-                            "split_slice_so"));
-              if (trm)
-                X2C_TRY(gemm_t_any(ctx, st, KP2, KP1, A1, Fs, ns, ntile1,
-                                   Stage1T<S, true>{e1, k2p, eF, A2, e2, ns, nA, cols1, KP2, TRA, k}, "split_spin_orbit"));
-              else
-                X2C_TRY((gemm_any<NT4, NT1>(ctx, st, nc, KP1, A1, Fs, ns, cols1,
-                                            Stage1Fused<S, 4, true>{e1, k2p, eF, A2, e2, ns, nA, cols1, KP2, TRA, k}, 1,
-                                            TRA, "split_spin_orbit")));
-              X2C_TRY((gemm_any<NT4, NT1>(ctx, st, nc, KP2, A2, Gs, srows2p / kTileM, cols2,
-                                          Stage2Store<4>{ds, d_mols, e2, eG, srows2, nA, nB, S, 1}, 2, kTileM,
-                                          "split_spin_orbit")));
-            }
-          }
-        }
+        // spin-orbit middle term, all pairs (general case): FP64 products.  (Same-atom blocks
+        // only, the usual case: split passes after the chunk loop.)
         if (nc == 4 && so_all) {
           std::vector<PairDesc> so;
           for (int i = 0; i < np; ++i) so.push_back(cls[c0 + i]);
@@ -1146,6 +1112,47 @@ struct Runner {
                                       UsStackC{ds, ut}, StoreT1{T1, per, nB}, SoDimsC{ds}, "split_spin_orbit")));
             X2C_TRY((gemm_f64<TileSo>(ctx, st, (int)so.size(), 4 * nA, nB, UsAdjLeft{ds, ut}, T1Op{T1, per, nB},
                                       AddH{ds, d_mols}, SoDims2{ds}, "split_spin_orbit")));
+          }
+        }
+      }
+      // spin-orbit middle term, same-atom blocks only (the usual case): after every chunk of the
+      // class has written its h blocks, three more split passes over all the class's diagonal
+      // pairs at once (few, full launches), one per quaternion part k of i sigma.W / 4c^2, whose
+      // stage 2 adds U_A+ (E_k R) to h.
+      if (nc == 4 && !so_all) {
+        std::vector<PairDesc> so;
+        for (const auto &P : cls)
+          if (P.diag) so.push_back(P);
+        for (size_t s0 = 0; s0 < so.size(); s0 += chunk) {
+          const int ns = (int)std::min(chunk, so.size() - s0);
+          Arena a1 = a0;
+          PairDesc *ds = reinterpret_cast<PairDesc *>(a1.take_bytes(ns * sizeof(PairDesc)));
+          const int srows1 = ns * TRA, srows2 = ns * cols1;
+          const int srows2p = (srows2 + kTileM - 1) / kTileM * kTileM;
+          __nv_bfloat16 *A1 = reinterpret_cast<__nv_bfloat16 *>(a1.take_bytes((size_t)srows1 * KP1 * S * 2));
+          int *e1 = reinterpret_cast<int *>(a1.take_bytes((size_t)srows1 * 4));
+          __nv_bfloat16 *A2 = reinterpret_cast<__nv_bfloat16 *>(a1.take_bytes((size_t)srows2p * KP2 * S * 2));
+          int *e2 = reinterpret_cast<int *>(a1.take_bytes((size_t)srows2p * 4));
+          if (!ds || !A1 || !e1 || !A2 || !e2) return X2C_ERR_NOMEM;
+          X2C_TRY(upload(ctx, st, ds, so.data() + s0, ns * sizeof(PairDesc)));
+          if (srows2p > srows2) {
+            const size_t tail0 = (size_t)(srows2p - kTileM) * KP2 * S * 2;
+            X2C_TRY_CUDA(ctx, cudaMemsetAsync(reinterpret_cast<char *>(A2) + tail0, 0, (size_t)kTileM * KP2 * S * 2, st));
+          }
+          ClassInfo cs{ds, d_mols, nA, nB, nc, inv4c2};
+          for (int k = 1; k <= 3; ++k) {
+            X2C_TRY(slice(ctx, st, SoMidRowsPadded{cs, TRA, k}, srows1, srows1, 2 * nB, KP1, TRA, 1, k1p, A1, e1,
+                          "split_slice_so"));
+            if (trm)
+              X2C_TRY(gemm_t_any(ctx, st, KP2, KP1, A1, Fs, ns, ntile1,
+                                 Stage1T<S, true>{e1, k2p, eF, A2, e2, ns, nA, cols1, KP2, TRA, k}, "split_spin_orbit"));
+            else
+              X2C_TRY((gemm_any<NT4, NT1>(ctx, st, nc, KP1, A1, Fs, ns, cols1,
+                                          Stage1Fused<S, 4, true>{e1, k2p, eF, A2, e2, ns, nA, cols1, KP2, TRA, k}, 1,
+                                          TRA, "split_spin_orbit")));
+            X2C_TRY((gemm_any<NT4, NT1>(ctx, st, nc, KP2, A2, Gs, srows2p / kTileM, cols2,
+                                        Stage2Store<4>{ds, d_mols, e2, eG, srows2, nA, nB, S, 1}, 2, kTileM,
+                                        "split_spin_orbit")));
           }
         }
       }
