@@ -15,6 +15,7 @@ from .x2c import (  # noqa: F401
     spinor_inputs,
     x2c_full,
     x2c_dlu,
+    dlu_from_transforms,
     x2c_dlh,
     picture_change,
     dlu_atomic_transforms,

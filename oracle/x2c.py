@@ -162,15 +162,22 @@ def _blockdiag_spinor(blocks, offsets, two_c: bool):
     return U
 
 
+def dlu_from_transforms(m_mol: dict, offsets, transforms, c: float = C_LIGHT):
+    """Eq. 8 with the block-diagonal U^{L,S} of Eq. 42 built from given atomic transforms
+    (one (U^L_AA, U^S_AA) pair per atom, real n x n or spin-blocked complex 2n x 2n), e.g.
+    identity matrices for light atoms (the non-relativistic treatment of Sec. III.A).
+    Returns dict(h, UL, US)."""
+    two_c = "Wx" in m_mol
+    UL = _blockdiag_spinor([u[0] for u in transforms], offsets, two_c)
+    US = _blockdiag_spinor([u[1] for u in transforms], offsets, two_c)
+    S, T, V, W = spinor_inputs(m_mol)
+    return dict(h=_utrans(UL, US, V, T, W, c), UL=UL, US=US)
+
+
 def x2c_dlu(m_mol: dict, offsets, atomic_per_atom=None, c: float = C_LIGHT):
     """DLU Hamiltonian: U^{L,S} = (+)_A U^{L,S}_AA (Eq. 42), then Eq. 8 with the
     molecular V, T, W (Sec. III.A).  Returns dict(h, UL, US)."""
-    two_c = "Wx" in m_mol
-    U = dlu_atomic_transforms(m_mol, offsets, atomic_per_atom, c)
-    UL = _blockdiag_spinor([u[0] for u in U], offsets, two_c)
-    US = _blockdiag_spinor([u[1] for u in U], offsets, two_c)
-    S, T, V, W = spinor_inputs(m_mol)
-    return dict(h=_utrans(UL, US, V, T, W, c), UL=UL, US=US)
+    return dlu_from_transforms(m_mol, offsets, dlu_atomic_transforms(m_mol, offsets, atomic_per_atom, c), c)
 
 
 def x2c_dlh(m_mol: dict, offsets, atomic_per_atom=None, c: float = C_LIGHT):

@@ -126,3 +126,24 @@ def test_picture_change_full_x2c_renormalisation(ctx, two_c):
         r = O.x2c_full(m)
         ref = O.picture_change(r["UL"], r["US"], V_, W_ / (4 * C * C))
         assert rel(P2, ref, True) <= 1e-10
+
+
+@pytest.mark.parametrize("prec", [x.PREC_FP64, x.PREC_SPLIT_BF16])
+def test_light_atom_identity_transforms(ctx, prec):
+    """The non-relativistic treatment of light atoms (Sec. III.A): identity transforms for the
+    light kind, the heavy kind's own, through x2c_build_dlu_with_transforms."""
+    mol = w.Molecule(w.fcc_sites(3), np.array([47.0, 1.0, 47.0]), ["s30"] * 3)
+    m = w.molecule_inputs(mol, True)
+    ag = w.atomic_inputs(47.0, "s30", True)
+    (UL, US), = x.x2c_atomic_transforms(ctx, [dev(ag)], two_component=True)
+    eye = torch.eye(30, dtype=torch.float64, device="cuda")
+    zero = torch.zeros_like(eye)
+    ident = ([eye, zero, zero, zero], [eye, zero, zero, zero])
+    h = x.x2c_build_dlu_with_transforms(ctx, dev(m), mol.offsets, [0, 1, 0], [(UL, US), ident], [30, 30],
+                                        two_component=True, precision=prec)
+    ctx.status()
+    r = O.x2c_full(ag)
+    e2 = (np.eye(60), np.eye(60))
+    ref = O.dlu_from_transforms(m, mol.offsets, [(r["UL"], r["US"]), e2, (r["UL"], r["US"])])["h"]
+    tol = 1e-9 if prec == x.PREC_SPLIT_BF16 else 1e-10
+    assert rel(h, ref, True) <= tol

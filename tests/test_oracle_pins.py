@@ -312,3 +312,26 @@ def test_picture_change_pins(two_c):
         rc = O.x2c_full(m, c)
         err.append(_rel(O.picture_change(rc["UL"], rc["US"], V, S), V + S))
     assert 95 < err[0] / err[1] < 105 and err[1] < 1e-5
+
+
+@pytest.mark.parametrize("two_c", [False, True])
+def test_identity_transforms_give_the_closed_form(two_c):
+    """The non-relativistic treatment of light atoms (Sec. III.A: their atomic transforms set
+    to identity): with U^L = U^S = 1 on every atom Eq. 8 collapses to V + T + W/4c^2, exactly;
+    with identity on one atom only, the blocks of the other atoms keep their DLU values."""
+    mol = w.Molecule(w.fcc_sites(3), np.array([47.0, 1.0, 47.0]), ["s30"] * 3)
+    m = w.molecule_inputs(mol, two_c)
+    S, T, V, W = O.spinor_inputs(m)
+    n = 30 * (2 if two_c else 1)
+    eye = (np.eye(n), np.eye(n))
+    h = O.dlu_from_transforms(m, mol.offsets, [eye] * 3)["h"]
+    assert _rel(h, V + T + W / (4 * C * C)) < 1e-15
+    ag = O.x2c_full(w.atomic_inputs(47.0, "s30", two_c))
+    mixed = O.dlu_from_transforms(m, mol.offsets, [(ag["UL"], ag["US"]), eye, (ag["UL"], ag["US"])])["h"]
+    dlu = O.x2c_dlu(m, mol.offsets, [w.atomic_inputs(47.0, "s30", two_c), w.atomic_inputs(1.0, "s30", two_c),
+                                      w.atomic_inputs(47.0, "s30", two_c)])["h"]
+    N = mol.nbf
+    a = np.r_[0:30, N:N + 30] if two_c else np.r_[0:30]
+    b = np.r_[60:90, N + 60:N + 90] if two_c else np.r_[60:90]
+    for blk in (np.ix_(a, a), np.ix_(a, b), np.ix_(b, b)):
+        assert np.abs(mixed[blk] - dlu[blk]).max() <= 1e-12 * np.abs(dlu).max()
