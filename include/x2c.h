@@ -183,6 +183,24 @@ x2c_status x2c_picture_change(x2c_ctx *ctx, const x2c_options *opt, const x2c_la
                               const x2c_uout *kind_U, const x2c_property *P, const x2c_hout *out,
                               void *stream);
 
+/* The input matrices over primitive s Gaussians g(r) = (2a/pi)^{3/4} exp(-a |r - A|^2) with
+ * point nuclei, computed on the device (Sec. II: the modified Dirac equation needs S, T, V
+ * and W; for s functions W is its scalar part W0 = sum_k p_k V p_k, the spin-orbit parts
+ * vanish): S overlap, T kinetic energy, V nuclear attraction, W0 = <grad g_a|V|grad g_b>, in
+ * closed form with the Boys functions F0, F1, F2.  All arrays are device memory: nuc_xyz
+ * (3 n_nuc, bohr), nuc_z (n_nuc charges), bf_xyz (3 n centres), bf_alpha (n exponents);
+ * outputs n x n row-major, exactly symmetric; any output may be NULL.  n_nuc <= 1536.
+ * Asynchronous on `stream`; X2C_ERR_ARG for bad arguments. */
+typedef struct {
+  int32_t n_nuc;
+  int32_t n;
+  const double *nuc_xyz;
+  const double *nuc_z;
+  const double *bf_xyz;
+  const double *bf_alpha;
+} x2c_s_basis;
+x2c_status x2c_s_integrals(const x2c_s_basis *basis, double *S, double *T, double *V, double *W0, void *stream);
+
 /* Atomic (or any) decoupling transforms U^L, U^S of n_problems independent input sets in
  * one batched solve (the matrix function of Eq. 43).  inputs, U: HOST arrays. */
 x2c_status x2c_atomic_transforms(x2c_ctx *ctx, const x2c_options *opt, int32_t n_problems,

@@ -334,6 +334,26 @@ def x2c_build_dlu_host(ctx: Context, m: dict, offsets, atom_kind=None, kinds=Non
     return out
 
 
+def x2c_s_integrals(nuc_xyz, nuc_z, bf_xyz, bf_alpha, want=("S", "T", "V", "W0"), stream=None):
+    """S, T, V, W0 over primitive s Gaussians computed on the device (x2c_s_integrals).
+    Arguments: CUDA float64 tensors (nuclei (L, 3) and (L,), basis centres (n, 3) and
+    exponents (n,)).  Returns a dict of n x n CUDA tensors for the requested matrices."""
+    torch = _torch()
+    args = [nuc_xyz, nuc_z, bf_xyz, bf_alpha]
+    for t in args:
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+            raise ValueError("expected contiguous float64 CUDA tensors")
+    n = int(bf_alpha.shape[0])
+    b = abi.SBasis()
+    b.n_nuc = int(nuc_z.shape[0])
+    b.n = n
+    b.nuc_xyz, b.nuc_z, b.bf_xyz, b.bf_alpha = (t.data_ptr() for t in args)
+    out = {k: torch.empty((n, n), dtype=torch.float64, device=bf_alpha.device) for k in want}
+    ptr = [out[k].data_ptr() if k in out else None for k in ("S", "T", "V", "W0")]
+    abi.check(abi.load().x2c_s_integrals(ctypes.byref(b), *ptr, _stream(stream)), "x2c_s_integrals")
+    return out
+
+
 def x2c_quaternion_to_dense(h_parts: list, stream=None):
     """Dense spin-blocked complex 2n x 2n matrix (complex128 CUDA tensor) from h parts."""
     torch = _torch()

@@ -55,6 +55,11 @@ class Counters(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int64), ("credited_flops", ctypes.c_double)]
 
 
+class SBasis(ctypes.Structure):
+    _fields_ = [("n_nuc", ctypes.c_int32), ("n", ctypes.c_int32), ("nuc_xyz", ctypes.c_void_p),
+                ("nuc_z", ctypes.c_void_p), ("bf_xyz", ctypes.c_void_p), ("bf_alpha", ctypes.c_void_p)]
+
+
 class Property(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("LL", ctypes.c_void_p), ("SS", ctypes.c_void_p * 4)]
 
@@ -124,6 +129,8 @@ _SIGS = {
     "x2c_ctx_tuning_log": (ctypes.c_char_p, [ctypes.c_void_p]),
     "x2c_ctx_set_split_variant": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "x2c_ctx_set_graphs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "x2c_s_integrals": (ctypes.c_int, [ctypes.POINTER(SBasis), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p]),
     "x2c_picture_change": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Options), ctypes.POINTER(Layout),
                                           ctypes.POINTER(UOut), ctypes.POINTER(Property), ctypes.POINTER(HOut),
                                           ctypes.c_void_p]),
