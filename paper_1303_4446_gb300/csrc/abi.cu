@@ -551,9 +551,18 @@ std::string plan_key(const x2c_ctx *ctx, int entry, const x2c_options *opt, cons
   return std::move(k.b);
 }
 
+// Hash of a plan key, eight bytes at a time (keys of large builds are megabytes; a match is
+// always confirmed by comparing the whole key).
 uint64_t fnv1a(const std::string &b) {
   uint64_t h = 1469598103934665603ull;
-  for (unsigned char ch : b) h = (h ^ ch) * 1099511628211ull;
+  size_t i = 0;
+  for (; i + 8 <= b.size(); i += 8) {
+    uint64_t w;
+    std::memcpy(&w, b.data() + i, 8);
+    h = (h ^ w) * 1099511628211ull;
+    h ^= h >> 29;
+  }
+  for (; i < b.size(); ++i) h = (h ^ static_cast<unsigned char>(b[i])) * 1099511628211ull;
   return h;
 }
 
