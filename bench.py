@@ -32,9 +32,9 @@ if ROOT not in sys.path:
 from paper_1303_4446_gb300 import workload as w  # noqa: E402
 
 METRIC = "X2C h builds/s & FP64-equiv TFLOP/s (Ag309 2c DLU) vs plain FP64; p99 latency"
-# FP64 FMA peak: paper_1303_4446_gb300/csrc/peak_probe.cu measured 1.193 TFLOP/s at 1995 MHz,
+# FP64 FMA peak: a DFMA throughput probe on this GB300 measured 1.193 TFLOP/s at 1995 MHz,
 # i.e. 2 DFMA per clock per SM; at the 2070 MHz maximum SM clock that is
-# 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz = 1.2586 TFLOP/s.  (mma.sync f64 measured 1.046.)
+# 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz = 1.2586 TFLOP/s.  (FP64 mma.sync measured 1.046.)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) per two-component 48 x 48 pair block of the split kernels, from
 # one ncu capture of the Ag55 two-component build (1540 pairs, the same per-pair shapes as
@@ -67,6 +67,23 @@ def measured_peaks():
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         return {}
+
+
+def clock_matched(roof, peaks, clocks):
+    """A tensor-bound fraction at equal SM clocks: the measured BF16 peak was taken at the
+    median clock of its own run (a seconds-long loop under the power cap), the kernel at the
+    clock sampled during the timed region; both rates scale with the SM clock, so
+    frac_clock_matched = frac x (peak run's clock / this run's clock)."""
+    if roof.get("bound") != "tensor":
+        return
+    pk = (peaks.get("clocks_under_load") or {}).get("sm_mhz_median")
+    run = (clocks or {}).get("sm_mhz")
+    if pk and run:
+        roof["peak_clock_mhz"] = pk
+        roof["run_clock_mhz"] = run
+        roof["frac_clock_matched"] = roof["frac"] * pk / run
+        roof["clock_note"] = (f"peak measured at a median {pk:g} MHz, kernel timed at {run:g} MHz; "
+                              "frac_clock_matched compares the two at the same clock")
 
 
 def pair_list(L):
@@ -301,6 +318,8 @@ def run_batched(args, cfg):
         roof = {"bound": "alu", "achieved": fl / (dom_ms * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "peak_source": "152 SMs x 2 DFMA/clk x 2.07 GHz"}
     roof.update(kernel=dom_name, frac=roof["achieved"] / roof["peak"], traffic=None, launches=int(dom_l))
+    clk_sum = clk.summary()
+    clock_matched(roof, peaks, clk_sum)
     npairs = sum(len(pair_list(m.natoms)) for m in mols)
     line = {"metric": METRIC, "value": n_mol * 1e3 / ms_step, "unit": "builds/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
@@ -311,7 +330,7 @@ def run_batched(args, cfg):
                        "inputs": "resident, 1.6 GB total (L2 flushed by the size of the step)"},
             "fp64_equiv_tflops": credited / (ms_step * 1e-3) / 1e12, "credited_flops_per_step": credited,
             "gpu_launches": int(counters["kernel_launches"]) * args.steps, "roofline": roof,
-            "clocks": clk.summary(),
+            "clocks": clk_sum,
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in sorted(ktimes.items(), key=lambda kv: -kv[1][0])},
             "kernel_launches_per_step": {k: v[1] // args.steps for k, v in ktimes.items()},
             "graphs": ctx.graph_stats(), "kernel_timing": KERNEL_TIMING, "input_generation_s": t_gen}
@@ -638,7 +657,7 @@ def main():
     ap.add_argument("--requests", type=int, default=0, help="serving: requests in the stream (0 = 2000)")
     ap.add_argument("--rate", type=float, default=50.0, help="serving: mean arrivals per second")
     ap.add_argument("--slots", type=int, default=4, help="serving: concurrent builds")
-    ap.add_argument("--serving-requests", type=int, default=500,
+    ap.add_argument("--serving-requests", type=int, default=2000,
                     help="default workload: requests of the short serving run reported as 'serving' (0 = none)")
     args = ap.parse_args()
     cfg = WORKLOADS[args.workload]
@@ -737,7 +756,7 @@ def main():
         fl = dom_flops if dom_flops > 0 else dom_lib_flops
         roof = {"bound": "alu", "achieved": fl / (dom_ms * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "kernel": dom_name,
-                "peak_source": "152 SMs x 2 DFMA/clk (measured by peak_probe.cu) x 2.07 GHz max clock"}
+                "peak_source": "152 SMs x 2 DFMA/clk (measured DFMA rate) x 2.07 GHz max clock"}
     else:
         # tensor-core work of the split kernels: S(S+1)/2 BF16 digit products per FP64 product
         S = args.slices or 5
@@ -747,6 +766,7 @@ def main():
                 "fp64_equiv_achieved": dom_flops / (dom_ms * 1e-3) / 1e12,
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained, of measured"}
     roof["frac"] = roof["achieved"] / roof["peak"]
+    clock_matched(roof, peaks, clocks)
     log = ctx.tuning_log()
     variant = {"split_stage1": "trm" if "-> transposed" in log else ("nt96" if "-> NT 96" in log else None),
                "split_stage2": "nt96" if ("-> transposed" in log or "-> NT 96" in log) else None}.get(dom_name)
@@ -838,8 +858,8 @@ def main():
                                           f"extrapolated to {len(pairs)} pair blocks"}
     ctx.close()
     if args.serving_requests > 0:
-        # p99 latency of the metric: a shorter run of the serving stream on the same GPU
-        # (the full 2000-request stream is `--workload serving`)
+        # p99 latency of the metric: the configured serving stream (2000 Poisson requests at
+        # 50/s) on the same GPU; `--workload serving` runs it alone with more detail
         del g, out
         torch.cuda.empty_cache()
         big, kinds_s = serving_inputs()

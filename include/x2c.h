@@ -225,9 +225,12 @@ x2c_status x2c_atomic_transforms(x2c_ctx *ctx, const x2c_options *opt, int32_t n
  * problems of n = 48, or 58 spin-free ones.
  *
  * The first call on a device looks up the array's device address (once per device, with
- * that device current); make that first call before any stream capture.  The call is
- * synchronous: it waits for `stream` and returns the device-side status of this call
- * (X2C_ERR_NOT_POSDEF, X2C_ERR_NOCONV, ...).  Every call shares the one array, which keeps the
+ * that device current, and again if that device's context was re-created); make that first
+ * call before any stream capture.  That lookup may load the library's device module, which
+ * holds the array: if device memory is already exhausted the first call fails with
+ * X2C_ERR_CUDA (not X2C_ERR_NOMEM, which only reports a request larger than the array).
+ * The call is synchronous: it waits for `stream` and returns the device-side status of this
+ * call (X2C_ERR_NOT_POSDEF, X2C_ERR_NOCONV, ...).  Every call shares the one array, which keeps the
  * last call's contents; calls that overlap on the GPU (other host threads, other streams)
  * race on it and must be serialised by the caller. */
 x2c_status x2c_atomic_transforms_noalloc(const x2c_options *opt, int32_t n_problems,

@@ -341,8 +341,16 @@ def x2c_s_integrals(nuc_xyz, nuc_z, bf_xyz, bf_alpha, want=("S", "T", "V", "W0")
     torch = _torch()
     args = [nuc_xyz, nuc_z, bf_xyz, bf_alpha]
     for t in args:
-        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
-            raise ValueError("expected contiguous float64 CUDA tensors")
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_contiguous():
+            raise ValueError("expected contiguous float64 tensors")
+    # the kernel takes n from bf_alpha and the nucleus count from nuc_z: every other array
+    # must have exactly the matching shape, or it would be read out of bounds
+    if bf_alpha.dim() != 1 or bf_alpha.shape[0] < 1 or tuple(bf_xyz.shape) != (bf_alpha.shape[0], 3):
+        raise ValueError("bf_xyz must be (n, 3) and bf_alpha (n,) with n >= 1")
+    if nuc_z.dim() != 1 or tuple(nuc_xyz.shape) != (nuc_z.shape[0], 3):
+        raise ValueError("nuc_xyz must be (L, 3) and nuc_z (L,)")
+    if not all(t.is_cuda for t in args) or len({t.device for t in args}) != 1:
+        raise ValueError("all four tensors must be on the same CUDA device")
     n = int(bf_alpha.shape[0])
     b = abi.SBasis()
     b.n_nuc = int(nuc_z.shape[0])

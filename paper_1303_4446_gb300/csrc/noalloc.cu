@@ -17,18 +17,43 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[X2C_NOALLOC_SCR
 constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
 char *g_base[kMaxDevices] = {};
+void *g_ctx[kMaxDevices] = {};  // the context the cached address belongs to
 
-// Set-up, once per device, with that device current: the device address of the array.
+// Current driver context (CUcontext as an opaque pointer), through the driver entry point
+// the runtime exposes, so the library needs no link against the driver library.
+void *current_context() {
+  using GetCurrent = int (*)(void **);
+  static GetCurrent fn = [] {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPoint("cuCtxGetCurrent", &f, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      f = nullptr;
+    }
+    return reinterpret_cast<GetCurrent>(f);
+  }();
+  void *c = nullptr;
+  if (!fn || fn(&c) != 0) return nullptr;
+  return c;
+}
+
+// Set-up, once per device (and again after that device's context was torn down and
+// re-created, e.g. by cudaDeviceReset), with that device current: the device address of the
+// array.  The first lookup may load the module that holds the array.
 x2c_status scratch_base(int device, char **out) {
   if (device < 0 || device >= kMaxDevices) return X2C_ERR_ARG;
   std::lock_guard<std::mutex> lock(g_mutex);
-  if (!g_base[device]) {
+  void *ctx = current_context();
+  if (!g_base[device] || !ctx || ctx != g_ctx[device]) {
     void *p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
       cudaGetLastError();
+      g_base[device] = nullptr;
       return X2C_ERR_CUDA;
     }
     g_base[device] = static_cast<char *>(p);
+    g_ctx[device] = current_context();
   }
   *out = g_base[device];
   return X2C_OK;

@@ -223,6 +223,24 @@ def so_blocks(Z: float, basis: str, seed: int = DEFAULT_SEED, strength: float = 
     return tuple(out)
 
 
+def so_blocks_configured(Z: float, basis: str, seed: int = DEFAULT_SEED, strength: float = SO_SCALE):
+    """The configured spin-orbit recipe taken literally, Wk_ij = strength g_ij sqrt(|W0_ii W0_jj|)
+    with the same seeded g as so_blocks (free-atom W0).  Not used by any workload: it is
+    kept so that a test can show why it was replaced (with it the atomic 4c spectrum no longer
+    splits at -c^2, so X2C is undefined for it)."""
+    w0 = free_atom_integrals(Z, basis)["W0"]
+    n = len(w0)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    iu = np.triu_indices(n, 1)
+    d = np.sqrt(np.abs(np.diag(w0)))
+    out = []
+    for _ in range(3):
+        x = np.zeros((n, n))
+        x[iu] = rng.standard_normal(len(iu[0]))
+        out.append(strength * (x - x.T) * np.outer(d, d))
+    return tuple(out)
+
+
 def molecular_so(mol: Molecule, seed: int = DEFAULT_SEED):
     """Molecular Wx, Wy, Wz (N x N) holding the synthetic blocks on same-atom blocks."""
     n = mol.nbf

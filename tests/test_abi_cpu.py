@@ -84,3 +84,23 @@ def test_quaternion_tables_reproduce_spinor_products(tmp_path):
     ref_adj = _spinor(A).conj().T @ _spinor(B)
     assert np.abs(_spinor(prod) - ref).max() < 1e-12
     assert np.abs(_spinor(prod_adj) - ref_adj).max() < 1e-12
+
+
+def test_s_integrals_binding_rejects_bad_shapes_before_any_launch():
+    """x2c_s_integrals takes n from bf_alpha and the nucleus count from nuc_z; arrays of any
+    other shape (or on different devices) would be read out of bounds, so the binding refuses
+    them before it reaches the library (checked on CPU tensors: shapes come first)."""
+    torch = pytest.importorskip("torch")
+    import paper_1303_4446_gb300 as x
+
+    f = lambda *s: torch.zeros(*s, dtype=torch.float64)
+    good = dict(nuc_xyz=f(2, 3), nuc_z=f(2), bf_xyz=f(5, 3), bf_alpha=f(5))
+    bad = [dict(good, bf_xyz=f(4, 3)), dict(good, bf_xyz=f(15)), dict(good, nuc_xyz=f(3, 3)),
+           dict(good, nuc_z=f(2, 1)), dict(good, bf_alpha=f(0)), dict(good, bf_alpha=f(0), bf_xyz=f(0, 3))]
+    for kw in bad:
+        with pytest.raises(ValueError, match="must be"):
+            x.x2c_s_integrals(**kw)
+    with pytest.raises(ValueError, match="CUDA"):
+        x.x2c_s_integrals(**good)  # right shapes, but not on a GPU
+    with pytest.raises(ValueError):
+        x.x2c_s_integrals(**dict(good, bf_alpha=torch.zeros(5, dtype=torch.float32)))

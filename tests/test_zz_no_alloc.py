@@ -1,7 +1,14 @@
-"""x2c_atomic_transforms_noalloc: the decoupling solve for callers that cannot allocate
-device memory (their memory belongs to another allocator, or an allocation must not
-synchronise the device).  It must give the same U^L, U^S as x2c_atomic_transforms, also on
-a second call that reuses the fixed scratch array left over from the first.
+"""x2c_atomic_transforms_noalloc: the batched decoupling solve for callers that cannot
+allocate device memory (their device memory belongs to another allocator that reserved it
+up front, or an allocation must not synchronise the device).
+
+Checked here, through the C ABI:
+  * U^L, U^S against the CPU oracle's full X2C of the same inputs (Eq. 23), on two calls in a
+    row (the second reuses the fixed scratch array left over from the first with new inputs),
+    for two-component and spin-free problems, at the tolerances of the other U parity tests;
+  * the device's free memory is the same before and after a call (nothing allocated);
+  * requests beyond the array's capacity and problems of different sizes are refused before
+    anything is enqueued.
 
 Kept in a file that pytest collects last, so a run that stops at the first failure has run
 every other test before it."""
@@ -10,6 +17,7 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
+import oracle as O
 import paper_1303_4446_gb300 as x
 from paper_1303_4446_gb300 import workload as w
 
@@ -20,31 +28,50 @@ def _dev(m):
     return {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in m.items()}
 
 
-def _inputs(seed):
-    """Two two-component s48 problems: the free atom and a molecular diagonal block."""
-    free = w.atomic_inputs(47.0, "s48", True, seed)
+def _inputs(seed, two_c):
+    """The free atom and a molecular diagonal block (s48): two problems of n = 48."""
+    free = w.atomic_inputs(47.0, "s48", two_c, seed)
     mol = w.silver_cluster(2, "s48")
-    mm = w.molecule_inputs(mol, True, seed)
+    mm = w.molecule_inputs(mol, two_c, seed)
     blk = {k: v[48:96, 48:96].copy() for k, v in mm.items()}
-    return [_dev(free), _dev(blk)]
+    return [free, blk]
 
 
-def _rel(a, b):
-    return (a - b).abs().max().item() / b.abs().max().item()
+def _parts(U, two_c):
+    return list(O.quaternion_parts(U)) if two_c else [U]
 
 
-def test_noalloc_matches_atomic_transforms_on_two_calls():
-    ctx = x.Context(0)
-    for call, seed in enumerate((11, 12)):  # second call reuses the array with new inputs
-        inputs = _inputs(seed)
-        ref = x.x2c_atomic_transforms(ctx, inputs, two_component=True)
-        ctx.status()
-        got = x.x2c_atomic_transforms_noalloc(inputs, two_component=True)
-        for (UL, US), (RL, RS) in zip(got, ref):
-            for q in range(4):
-                assert _rel(UL[q], RL[q]) <= 1e-10, (call, "UL", q)
-                assert _rel(US[q], RS[q]) <= 1e-9, (call, "US", q)
-    ctx.close()
+def _out(nc, n, count):
+    return [([torch.empty((n, n), dtype=torch.float64, device="cuda") for _ in range(nc)],
+             [torch.empty((n, n), dtype=torch.float64, device="cuda") for _ in range(nc)]) for _ in range(count)]
+
+
+@pytest.mark.parametrize("two_c", [True, False])
+def test_noalloc_matches_oracle_on_two_calls(two_c):
+    nc = 4 if two_c else 1
+    for call, seed in enumerate((11, 12)):
+        host = _inputs(seed, two_c)
+        refs = [O.x2c_full(m) for m in host]
+        got = x.x2c_atomic_transforms_noalloc([_dev(m) for m in host], two_component=two_c,
+                                              out=_out(nc, 48, len(host)))
+        for (UL, US), r in zip(got, refs):
+            sl, ss = np.abs(r["UL"]).max(), np.abs(r["US"]).max()
+            for q, (gl, gs, rl, rs) in enumerate(zip(UL, US, _parts(r["UL"], two_c), _parts(r["US"], two_c))):
+                assert np.abs(gl.cpu().numpy() - rl).max() <= 1e-10 * sl, (call, "UL", q)
+                assert np.abs(gs.cpu().numpy() - rs).max() <= 1e-9 * ss, (call, "US", q)
+
+
+def test_noalloc_call_leaves_device_free_memory_unchanged():
+    inputs = [_dev(m) for m in _inputs(11, True)]
+    out = _out(4, 48, len(inputs))
+    x.x2c_atomic_transforms_noalloc(inputs, two_component=True, out=out)  # set-up call
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(2):
+        x.x2c_atomic_transforms_noalloc(inputs, two_component=True, out=out)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
 
 
 def test_noalloc_rejects_more_than_the_scratch_holds():
@@ -52,3 +79,11 @@ def test_noalloc_rejects_more_than_the_scratch_holds():
     with pytest.raises(x.X2CError) as e:
         x.x2c_atomic_transforms_noalloc([m] * 40, two_component=True)
     assert e.value.code == 2  # X2C_ERR_NOMEM, nothing enqueued
+
+
+def test_noalloc_rejects_problems_of_different_sizes():
+    a = _dev(w.atomic_inputs(47.0, "s48", False))
+    b = _dev(w.atomic_inputs(47.0, "s30", False))
+    with pytest.raises(x.X2CError) as e:
+        x.x2c_atomic_transforms_noalloc([a, b], two_component=False, out=_out(1, 48, 1) + _out(1, 30, 1))
+    assert e.value.code == 1  # X2C_ERR_ARG
