@@ -82,7 +82,12 @@ typedef struct {
                                 only those blocks and skips the rest (two-component only) */
   int32_t n_slices;          /* split precision: BF16 slices per operand, 0 = default (5) */
   int32_t local_approx;      /* x2c_local_approx of the DLU calls (ignored by full X2C) */
-  int32_t reserved[2];       /* must be zero */
+  int32_t h_upper_only;      /* x2c_build_dlu_host only: 1 = write each h part back on its upper
+                                block triangle only (blocks A <= B; the other blocks of the host
+                                buffers are not written).  h0 is symmetric and h1..h3 are
+                                antisymmetric, so the lower blocks follow from the upper ones;
+                                this halves the device-to-host copy.  Other calls: must be 0 */
+  int32_t reserved[1];       /* must be zero */
 } x2c_options;
 
 typedef struct {

@@ -108,8 +108,9 @@ def _stream(stream):
 
 
 def options(two_component=False, c=None, precision=PREC_FP64, dlu_potential=DLU_FREE_ATOM,
-            so_same_atom_only=True, n_slices=0, local_approx=LOCAL_DLU) -> abi.Options:
+            so_same_atom_only=True, n_slices=0, local_approx=LOCAL_DLU, h_upper_only=False) -> abi.Options:
     o = abi.Options()
+    o.h_upper_only = int(bool(h_upper_only))
     o.local_approx = int(local_approx)
     o.c = float(c) if c else C_LIGHT
     o.two_component = int(bool(two_component))
@@ -297,9 +298,10 @@ def x2c_atomic_transforms_noalloc(inputs: list, two_component=False, c=None, out
 
 def x2c_build_dlu_host(ctx: Context, m: dict, offsets, atom_kind=None, kinds=None, two_component=False,
                        c=None, precision=PREC_FP64, dlu_potential=DLU_FREE_ATOM, so_same_atom_only=True,
-                       n_slices=0, local_approx=LOCAL_DLU, out=None, stream=None):
+                       n_slices=0, local_approx=LOCAL_DLU, out=None, stream=None, h_upper_only=False):
     """DLU build from HOST arrays (numpy float64 or CPU torch tensors, pinned or not);
-    h parts are written into `out` (host arrays) or new numpy arrays."""
+    h parts are written into `out` (host arrays) or new numpy arrays.  h_upper_only: only the
+    upper block triangle of each part is written (the rest of `out` is left as it was)."""
     nc = 4 if two_component else 1
     n = m["S"].shape[0]
 
@@ -328,7 +330,8 @@ def x2c_build_dlu_host(ctx: Context, m: dict, offsets, atom_kind=None, kinds=Non
     ho = abi.HOut()
     for q in range(nc):
         ho.h[q] = hp(out[q])
-    o = options(two_component, c, precision, dlu_potential, so_same_atom_only, n_slices, local_approx)
+    o = options(two_component, c, precision, dlu_potential, so_same_atom_only, n_slices, local_approx,
+                h_upper_only)
     abi.check(ctx.lib.x2c_build_dlu_host(ctx.handle, ctypes.byref(o), ctypes.byref(lay.s), ctypes.byref(ms),
                                          ctypes.byref(ho), _stream(stream)), "x2c_build_dlu_host", ctx.handle)
     return out

@@ -27,7 +27,8 @@ class Options(ctypes.Structure):
     _fields_ = [("c", ctypes.c_double), ("two_component", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("dlu_potential", ctypes.c_int32),
                 ("so_same_atom_only", ctypes.c_int32), ("n_slices", ctypes.c_int32),
-                ("local_approx", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("local_approx", ctypes.c_int32), ("h_upper_only", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 1)]
 
 
 class Mats(ctypes.Structure):

@@ -170,6 +170,7 @@ x2c_status check_options(const x2c_options *o) {
   if (o->dlu_potential != X2C_DLU_FREE_ATOM && o->dlu_potential != X2C_DLU_MOLECULAR_BLOCK) return X2C_ERR_ARG;
   if (o->n_slices < 0 || o->n_slices > 8) return X2C_ERR_ARG;
   if (o->local_approx != X2C_LOCAL_DLU && o->local_approx != X2C_LOCAL_DLH) return X2C_ERR_ARG;
+  if (o->h_upper_only != 0) return X2C_ERR_ARG;  // only x2c_build_dlu_host takes it (and clears it)
   for (int r : o->reserved)
     if (r != 0) return X2C_ERR_ARG;
   return X2C_OK;
@@ -383,7 +384,7 @@ using KindIndex = std::map<std::tuple<const double *, const double *, const doub
 
 x2c_status add_molecule(BuildPlan &plan, const x2c_options *opt, const x2c_layout *lay,
                         const x2c_mats *mol, const x2c_hout *h, int mol_index, KindIndex &kind_index,
-                        const KindTransforms *ku = nullptr) {
+                        const KindTransforms *ku = nullptr, int a_begin = 0, int a_end = -1) {
   const int nc = plan.nc;
   if (!lay || lay->n_atoms < 1 || !lay->atom_offset || !mats_ok(mol, nc) || !h) return X2C_ERR_ARG;
   for (int q = 0; q < nc; ++q)
@@ -439,7 +440,9 @@ x2c_status add_molecule(BuildPlan &plan, const x2c_options *opt, const x2c_layou
   // DLH: only the same-atom blocks are transformed; the rest is filled with T + V
   const bool dlh = opt->local_approx == X2C_LOCAL_DLH;
   if (dlh) plan.fills.push_back({mol_index, std::vector<int32_t>(lay->atom_offset, lay->atom_offset + L + 1)});
-  for (int A = 0; A < L; ++A) {
+  if (a_end < 0) a_end = L;
+  if (a_begin < 0 || a_begin >= a_end || a_end > L) return X2C_ERR_ARG;
+  for (int A = a_begin; A < a_end; ++A) {
     const int nA = lay->atom_offset[A + 1] - lay->atom_offset[A];
     plan.max_n = std::max(plan.max_n, nA);
     for (int B = A; B < (dlh ? A + 1 : L); ++B) {
@@ -771,15 +774,16 @@ x2c_status full_build(x2c_ctx *ctx, const x2c_options *opt, const x2c_mats *mol,
 
 x2c_status dlu_build(x2c_ctx *ctx, const x2c_options *opt, int n_mol, const x2c_layout *layouts,
                      const x2c_mats *mols, const x2c_hout *h, const KindTransforms *ku, cudaStream_t st,
-                     size_t *dry_bytes) {
+                     size_t *dry_bytes, int a_begin, int a_end) {
   X2C_TRY(begin_call(ctx));
   X2C_TRY(check_options(opt));
   if (n_mol < 1 || !layouts || !mols || !h) return X2C_ERR_ARG;
+  if ((a_begin != 0 || a_end >= 0) && n_mol != 1) return X2C_ERR_ARG;
   BuildPlan plan;
   plan.nc = opt->two_component ? 4 : 1;
   KindIndex kinds;
   for (int i = 0; i < n_mol; ++i)
-    X2C_TRY(add_molecule(plan, opt, &layouts[i], &mols[i], &h[i], i, kinds, ku ? &ku[i] : nullptr));
+    X2C_TRY(add_molecule(plan, opt, &layouts[i], &mols[i], &h[i], i, kinds, ku ? &ku[i] : nullptr, a_begin, a_end));
   auto enqueue = [&](cudaStream_t s, size_t *dry) { return run_plan(ctx, opt, plan, s, nullptr, nullptr, dry); };
   if (dry_bytes) return enqueue(st, dry_bytes);
   X2C_TRY(graph_run(ctx, st, [&] { return plan_key(ctx, 1, opt, plan, nullptr, 0); }, plan, enqueue));

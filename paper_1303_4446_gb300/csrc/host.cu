@@ -1,4 +1,10 @@
 // x2c_build_dlu_host: DLU build from host buffers (copy in, build, copy out).
+//
+// Free-atom DLU runs as a pipeline over chunks of row atoms: the pair blocks (A, B >= A) of
+// Eq. 42 are independent, so chunk k is assembled while the upper-block rows of chunk k+1
+// cross to the device and the h rows of chunk k-1 come back; the per-kind decoupling solve
+// runs while the first chunk is still copying.  Other modes copy everything in, build, and
+// copy everything out.
 #include <cstring>
 
 #include "common.cuh"
@@ -19,17 +25,54 @@ x2c_status copy_diag_blocks(x2c_ctx *ctx, double *dst, const double *src, int64_
   return X2C_OK;
 }
 
-// Copy the upper block triangle (rows of atom a, columns from the atom's first function to
-// N - 1) of an N x N host matrix into the same places of a device matrix.
-x2c_status copy_upper_blocks(x2c_ctx *ctx, double *dst, const double *src, int64_t N, const x2c_layout *lay,
-                             cudaStream_t st) {
-  for (int a = 0; a < lay->n_atoms; ++a) {
+// Copy the upper block triangle of rows of atoms [a0, a1) (rows of atom a, columns from the
+// atom's first function to N - 1) between an N x N host and device matrix.
+x2c_status copy_upper_rows(x2c_ctx *ctx, double *dst, const double *src, int64_t N, const x2c_layout *lay, int a0,
+                           int a1, cudaMemcpyKind kind, cudaStream_t st) {
+  for (int a = a0; a < a1; ++a) {
     const int64_t o = lay->atom_offset[a], n = lay->atom_offset[a + 1] - o;
     X2C_TRY_CUDA(ctx, cudaMemcpy2DAsync(dst + o * N + o, N * sizeof(double), src + o * N + o, N * sizeof(double),
-                                        (N - o) * sizeof(double), n, cudaMemcpyHostToDevice, st));
+                                        (N - o) * sizeof(double), n, kind, st));
   }
   return X2C_OK;
 }
+
+x2c_status copy_upper_blocks(x2c_ctx *ctx, double *dst, const double *src, int64_t N, const x2c_layout *lay,
+                             cudaStream_t st) {
+  return copy_upper_rows(ctx, dst, src, N, lay, 0, lay->n_atoms, cudaMemcpyHostToDevice, st);
+}
+
+// Row-atom chunks of about equal copy volume: atom a carries n_a (N - offset_a) elements of
+// the upper block triangle.
+std::vector<int> row_chunks(const x2c_layout *lay, int64_t N, int chunks) {
+  const int L = lay->n_atoms;
+  std::vector<double> cum(L + 1, 0.0);
+  for (int a = 0; a < L; ++a)
+    cum[a + 1] = cum[a] + double(lay->atom_offset[a + 1] - lay->atom_offset[a]) * double(N - lay->atom_offset[a]);
+  std::vector<int> cut{0};
+  for (int k = 1; k < chunks; ++k) {
+    const double target = cum[L] * k / chunks;
+    int a = cut.back() + 1;
+    while (a < L && cum[a] < target) ++a;
+    if (a < L && a > cut.back()) cut.push_back(a);
+  }
+  cut.push_back(L);
+  return cut;
+}
+
+struct Events {
+  std::vector<cudaEvent_t> ev;
+  ~Events() {
+    for (auto e : ev) cudaEventDestroy(e);
+  }
+  x2c_status make(x2c_ctx *ctx, size_t n) {
+    ev.assign(n, nullptr);
+    for (auto &e : ev) X2C_TRY_CUDA(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    return X2C_OK;
+  }
+};
+
+constexpr int kPipelineChunks = 8;
 
 }  // namespace
 
@@ -37,29 +80,49 @@ extern "C" x2c_status x2c_build_dlu_host(x2c_ctx *ctx, const x2c_options *opt, c
                                          const x2c_mats *mol, const x2c_hout *h, void *stream) {
   if (!ctx || !opt || !lay || !mol || !h || mol->n < 1 || lay->n_atoms < 1 || !lay->atom_offset)
     return X2C_ERR_ARG;
+  if (opt->h_upper_only != 0 && opt->h_upper_only != 1) return X2C_ERR_ARG;
   X2C_TRY_CUDA(ctx, cudaSetDevice(ctx->device));
+  x2c_options o = *opt;  // the build calls below take no host-copy options
+  o.h_upper_only = 0;
+  X2C_TRY(x2c::check_options(&o));
+  const bool upper_only = opt->h_upper_only == 1;
   const int nc = opt->two_component ? 4 : 1;
   const int64_t N = mol->n, N2 = N * N;
+  const int L = lay->n_atoms;
   const bool mb = opt->dlu_potential == X2C_DLU_MOLECULAR_BLOCK;
+  const bool dlh = opt->local_approx == X2C_LOCAL_DLH;
   const bool so_blocks = nc == 4 && opt->so_same_atom_only;
   if (!mol->S || !mol->T || !mol->V || !mol->W0) return X2C_ERR_ARG;
   if (nc == 4 && (!mol->Wx || !mol->Wy || !mol->Wz)) return X2C_ERR_ARG;
   for (int q = 0; q < nc; ++q)
     if (!h->h[q]) return X2C_ERR_ARG;
-  int64_t kind_doubles = 0;
+  if (lay->atom_offset[0] != 0 || lay->atom_offset[L] != N) return X2C_ERR_ARG;
+  for (int a = 0; a < L; ++a)
+    if (lay->atom_offset[a + 1] <= lay->atom_offset[a]) return X2C_ERR_ARG;
+  int64_t kind_doubles = 0, kind_u_doubles = 0;
   if (!mb) {
     if (!lay->kinds || lay->n_kinds < 1) return X2C_ERR_ARG;
-    for (int k = 0; k < lay->n_kinds; ++k) kind_doubles += (int64_t)(3 + nc + 1) * lay->kinds[k].n * lay->kinds[k].n;
+    for (int k = 0; k < lay->n_kinds; ++k) {
+      const int64_t n2 = (int64_t)lay->kinds[k].n * lay->kinds[k].n;
+      if (lay->kinds[k].n < 1) return X2C_ERR_ARG;
+      kind_doubles += (int64_t)(3 + nc + 1) * n2;
+      kind_u_doubles += 2 * nc * n2;
+    }
   }
-  // staging layout: S, T, V, W0, Wx, Wy, Wz (as needed), h parts, kinds
-  const int64_t mats = 4 + (nc == 4 ? 3 : 0);
-  const size_t bytes = sizeof(double) * ((mats + nc) * N2 + kind_doubles) + 1024;
+  const bool pipelined = !mb && !dlh && L >= 2;
+  // staging layout: S (molecular-block mode only), T, V, W0, Wx, Wy, Wz (as needed), h
+  // parts, kinds, kind transforms (pipelined path)
+  const int64_t mats = (mb ? 1 : 0) + 3 + (nc == 4 ? 3 : 0);
+  const size_t bytes = sizeof(double) * ((mats + nc) * N2 + kind_doubles + (pipelined ? kind_u_doubles : 0)) + 1024;
   X2C_TRY(ensure_stage(ctx, bytes));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  double *base = reinterpret_cast<double *>(ctx->stage);
-  double *dS = base, *dT = dS + N2, *dV = dT + N2, *dW0 = dV + N2;
+  double *next = reinterpret_cast<double *>(ctx->stage);
+  double *dS = nullptr;
+  if (mb) { dS = next; next += N2; }
+  double *dT = next, *dV = dT + N2, *dW0 = dV + N2;
+  next = dW0 + N2;
+  if (!mb) dS = dT;  // free-atom mode never reads the molecular S
   double *dW[3] = {nullptr, nullptr, nullptr};
-  double *next = dW0 + N2;
   if (nc == 4)
     for (int k = 0; k < 3; ++k) { dW[k] = next; next += N2; }
   double *dh[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -67,8 +130,7 @@ extern "C" x2c_status x2c_build_dlu_host(x2c_ctx *ctx, const x2c_options *opt, c
   const size_t full = N2 * sizeof(double);
   // The copies are spread over the call's stream and three side streams of the context, so
   // that several copy engines move the matrices at once; the side streams start after the
-  // work already on `st` and `st` waits for them before the build (and again for the copies
-  // of h back).
+  // work already on `st`, and `st` waits for them before it reads what they copied.
   X2C_TRY(x2c::ensure_aux_streams(ctx, 3));
   cudaStream_t cs[4] = {st, ctx->aux[0], ctx->aux[1], ctx->aux[2]};
   auto fork = [&]() -> x2c_status {
@@ -84,23 +146,7 @@ extern "C" x2c_status x2c_build_dlu_host(x2c_ctx *ctx, const x2c_options *opt, c
     return X2C_OK;
   };
   X2C_TRY(fork());
-  // the pair assembly reads the blocks A <= B; DLH reads T and V everywhere and W0 on the
-  // same-atom blocks only
-  if (opt->local_approx == X2C_LOCAL_DLH) {
-    X2C_TRY_CUDA(ctx, cudaMemcpyAsync(dT, mol->T, full, cudaMemcpyHostToDevice, cs[0]));
-    X2C_TRY_CUDA(ctx, cudaMemcpyAsync(dV, mol->V, full, cudaMemcpyHostToDevice, cs[1]));
-    X2C_TRY(copy_diag_blocks(ctx, dW0, mol->W0, N, lay, cs[2]));
-  } else {
-    X2C_TRY(copy_upper_blocks(ctx, dT, mol->T, N, lay, cs[0]));
-    X2C_TRY(copy_upper_blocks(ctx, dV, mol->V, N, lay, cs[1]));
-    X2C_TRY(copy_upper_blocks(ctx, dW0, mol->W0, N, lay, cs[2]));
-  }
-  if (mb) X2C_TRY(copy_diag_blocks(ctx, dS, mol->S, N, lay, cs[3]));
-  const double *hw[3] = {mol->Wx, mol->Wy, mol->Wz};
-  for (int k = 0; k < 3 && nc == 4; ++k) {
-    if (so_blocks) X2C_TRY(copy_diag_blocks(ctx, dW[k], hw[k], N, lay, cs[3]));
-    else X2C_TRY(copy_upper_blocks(ctx, dW[k], hw[k], N, lay, cs[(k + 1) % 4]));
-  }
+  // kinds (small) first, on the last side stream
   std::vector<x2c_mats> dk;
   if (!mb) {
     for (int k = 0; k < lay->n_kinds; ++k) {
@@ -121,6 +167,9 @@ extern "C" x2c_status x2c_build_dlu_host(x2c_ctx *ctx, const x2c_options *opt, c
       dk.push_back(d);
     }
   }
+  const double *hw[3] = {mol->Wx, mol->Wy, mol->Wz};
+  if (so_blocks)
+    for (int k = 0; k < 3; ++k) X2C_TRY(copy_diag_blocks(ctx, dW[k], hw[k], N, lay, cs[3]));
   x2c_mats dm{};
   dm.n = (int32_t)N;
   dm.S = dS; dm.T = dT; dm.V = dV; dm.W0 = dW0;
@@ -129,11 +178,87 @@ extern "C" x2c_status x2c_build_dlu_host(x2c_ctx *ctx, const x2c_options *opt, c
   if (!mb) dl.kinds = dk.data();
   x2c_hout dho{};
   for (int q = 0; q < nc; ++q) dho.h[q] = dh[q];
-  X2C_TRY(join());
-  X2C_TRY(x2c_build_dlu(ctx, opt, &dl, &dm, &dho, stream));
-  X2C_TRY(fork());
-  for (int q = 0; q < nc; ++q)
-    X2C_TRY_CUDA(ctx, cudaMemcpyAsync(h->h[q], dh[q], full, cudaMemcpyDeviceToHost, cs[q]));
+
+  if (!pipelined) {
+    if (dlh) {  // DLH reads T and V everywhere and W0 on the same-atom blocks only
+      X2C_TRY_CUDA(ctx, cudaMemcpyAsync(dT, mol->T, full, cudaMemcpyHostToDevice, cs[0]));
+      X2C_TRY_CUDA(ctx, cudaMemcpyAsync(dV, mol->V, full, cudaMemcpyHostToDevice, cs[1]));
+      X2C_TRY(copy_diag_blocks(ctx, dW0, mol->W0, N, lay, cs[2]));
+    } else {
+      X2C_TRY(copy_upper_blocks(ctx, dT, mol->T, N, lay, cs[0]));
+      X2C_TRY(copy_upper_blocks(ctx, dV, mol->V, N, lay, cs[1]));
+      X2C_TRY(copy_upper_blocks(ctx, dW0, mol->W0, N, lay, cs[2]));
+    }
+    if (mb) X2C_TRY(copy_diag_blocks(ctx, dS, mol->S, N, lay, cs[3]));
+    if (nc == 4 && !so_blocks)
+      for (int k = 0; k < 3; ++k) X2C_TRY(copy_upper_blocks(ctx, dW[k], hw[k], N, lay, cs[(k + 1) % 4]));
+    X2C_TRY(join());
+    X2C_TRY(x2c_build_dlu(ctx, &o, &dl, &dm, &dho, stream));
+    X2C_TRY(fork());
+    for (int q = 0; q < nc; ++q) {
+      if (upper_only)
+        X2C_TRY(copy_upper_rows(ctx, h->h[q], dh[q], N, lay, 0, L, cudaMemcpyDeviceToHost, cs[q]));
+      else
+        X2C_TRY_CUDA(ctx, cudaMemcpyAsync(h->h[q], dh[q], full, cudaMemcpyDeviceToHost, cs[q]));
+    }
+    X2C_TRY(join());
+    X2C_TRY_CUDA(ctx, cudaStreamSynchronize(st));
+    return X2C_OK;
+  }
+
+  // ---- pipelined free-atom DLU
+  // 1. per-kind transforms, as soon as the kinds are on the device (side stream 3 copied them)
+  const int nk = lay->n_kinds;
+  std::vector<x2c_uout> ku_out(nk);
+  std::vector<const double *> ul(nk), us(nk);
+  for (int k = 0; k < nk; ++k) {
+    const int64_t n2 = (int64_t)lay->kinds[k].n * lay->kinds[k].n;
+    x2c_uout u{};
+    for (int q = 0; q < nc; ++q) { u.UL[q] = next + q * n2; u.US[q] = next + (nc + q) * n2; }
+    ul[k] = next;
+    us[k] = next + nc * n2;
+    next += 2 * nc * n2;
+    ku_out[k] = u;
+  }
+  const std::vector<int> cut = row_chunks(lay, N, kPipelineChunks);
+  const int nch = (int)cut.size() - 1;
+  Events ev;
+  X2C_TRY(ev.make(ctx, 2 * (size_t)nch + 2));
+  cudaEvent_t ev_kinds = ev.ev[2 * nch], ev_out = ev.ev[2 * nch + 1];
+  X2C_TRY_CUDA(ctx, cudaEventRecord(ev_kinds, cs[3]));
+  X2C_TRY_CUDA(ctx, cudaStreamWaitEvent(st, ev_kinds, 0));
+  X2C_TRY(x2c_atomic_transforms(ctx, &o, nk, dk.data(), ku_out.data(), stream));
+  const x2c::KindTransforms kt{ul.data(), us.data()};
+  // 2. chunk k: rows in on side streams 0/1 (alternating), assembly on `st`, h rows out on
+  //    side stream 2
+  for (int c = 0; c < nch; ++c) {
+    const int a0 = cut[c], a1 = cut[c + 1];
+    cudaStream_t in = cs[1 + (c & 1)];
+    X2C_TRY(copy_upper_rows(ctx, dT, mol->T, N, lay, a0, a1, cudaMemcpyHostToDevice, in));
+    X2C_TRY(copy_upper_rows(ctx, dV, mol->V, N, lay, a0, a1, cudaMemcpyHostToDevice, in));
+    X2C_TRY(copy_upper_rows(ctx, dW0, mol->W0, N, lay, a0, a1, cudaMemcpyHostToDevice, in));
+    if (nc == 4 && !so_blocks)
+      for (int k = 0; k < 3; ++k)
+        X2C_TRY(copy_upper_rows(ctx, dW[k], hw[k], N, lay, a0, a1, cudaMemcpyHostToDevice, in));
+    X2C_TRY_CUDA(ctx, cudaEventRecord(ev.ev[2 * c], in));
+    X2C_TRY_CUDA(ctx, cudaStreamWaitEvent(st, ev.ev[2 * c], 0));
+    X2C_TRY(x2c::dlu_build(ctx, &o, 1, &dl, &dm, &dho, &kt, st, nullptr, a0, a1));
+    X2C_TRY_CUDA(ctx, cudaEventRecord(ev.ev[2 * c + 1], st));
+    // the rows of this chunk are complete now: their blocks left of the diagonal are the
+    // mirrors written by this and the earlier chunks, the rest by this chunk
+    cudaStream_t out = cs[3];
+    X2C_TRY_CUDA(ctx, cudaStreamWaitEvent(out, ev.ev[2 * c + 1], 0));
+    const int64_t r0 = lay->atom_offset[a0], r1 = lay->atom_offset[a1];
+    for (int q = 0; q < nc; ++q) {
+      if (upper_only)
+        X2C_TRY(copy_upper_rows(ctx, h->h[q], dh[q], N, lay, a0, a1, cudaMemcpyDeviceToHost, out));
+      else
+        X2C_TRY_CUDA(ctx, cudaMemcpyAsync(h->h[q] + r0 * N, dh[q] + r0 * N, (r1 - r0) * N * sizeof(double),
+                                          cudaMemcpyDeviceToHost, out));
+    }
+  }
+  X2C_TRY_CUDA(ctx, cudaEventRecord(ev_out, cs[3]));
+  X2C_TRY_CUDA(ctx, cudaStreamWaitEvent(st, ev_out, 0));
   X2C_TRY(join());
   X2C_TRY_CUDA(ctx, cudaStreamSynchronize(st));
   return X2C_OK;

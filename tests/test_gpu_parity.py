@@ -204,18 +204,22 @@ def test_batched_equals_single(ctx):
             assert (a - b).abs().max().item() <= 1e-13 * b.abs().max().item()
 
 
-@pytest.mark.parametrize("approx", [x.LOCAL_DLU, x.LOCAL_DLH])
+@pytest.mark.parametrize("L,approx,upper", [(3, x.LOCAL_DLU, False), (3, x.LOCAL_DLH, False),
+                                             (3, x.LOCAL_DLU, True), (13, x.LOCAL_DLU, False),
+                                             (13, x.LOCAL_DLU, True)])
 @pytest.mark.parametrize("prec", [x.PREC_FP64, x.PREC_SPLIT_BF16])
-def test_host_buffers_equal_device(ctx, approx, prec):
+def test_host_buffers_equal_device(ctx, L, approx, upper, prec):
     """The host-buffer call copies only the blocks the build reads: NaN in every other block
-    of the host inputs must not reach h."""
-    mol = w.silver_cluster(3, "s30")
+    of the host inputs must not reach h.  Free-atom DLU runs as a pipeline over row-atom
+    chunks (Ag13: eight chunks), and must give the device build's h bit for bit; with
+    h_upper_only it writes the upper block triangle and leaves the other blocks alone."""
+    mol = w.silver_cluster(L, "s30")
     m = w.molecule_inputs(mol, True)
     kind = w.atomic_inputs(47.0, "s30", True)
     kw = dict(two_component=True, precision=prec, local_approx=approx)
-    hd = x.x2c_build_dlu(ctx, dev(m), mol.offsets, [0] * 3, [dev(kind)], **kw)
+    hd = x.x2c_build_dlu(ctx, dev(m), mol.offsets, [0] * L, [dev(kind)], **kw)
     ctx.status()
-    atom = np.repeat(np.arange(3), np.diff(mol.offsets))
+    atom = np.repeat(np.arange(L), np.diff(mol.offsets))
     lower = atom[:, None] > atom[None, :]
     other = atom[:, None] != atom[None, :]
     hm = {k: v.copy() for k, v in m.items()}
@@ -227,9 +231,20 @@ def test_host_buffers_equal_device(ctx, approx, prec):
             hm[k][lower] = np.nan
     else:
         hm["W0"][other] = np.nan
-    hh = x.x2c_build_dlu_host(ctx, hm, mol.offsets, [0] * 3, [kind], **kw)
+    n = mol.nbf
+    out = [np.full((n, n), 7.0) for _ in range(4)]
+    hh = x.x2c_build_dlu_host(ctx, hm, mol.offsets, [0] * L, [kind], h_upper_only=upper, out=out, **kw)
     for a, b in zip(hd, hh):
-        assert np.array_equal(a.cpu().numpy(), b)
+        a = a.cpu().numpy()
+        if upper:
+            assert np.array_equal(a[~lower], b[~lower])
+            assert np.all(b[lower] == 7.0)
+        else:
+            assert np.array_equal(a, b)
+    if upper:  # the lower blocks follow from the symmetry of h0 and antisymmetry of h1..h3
+        full = [np.where(lower, (1.0 if q == 0 else -1.0) * b.T, b) for q, b in enumerate(hh)]
+        for a, b in zip(hd, full):
+            assert np.array_equal(a.cpu().numpy(), b)
 
 
 def test_quaternion_to_dense(ctx):
