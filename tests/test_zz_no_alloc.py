@@ -54,11 +54,16 @@ def test_noalloc_matches_oracle_on_two_calls(two_c):
         refs = [O.x2c_full(m) for m in host]
         got = x.x2c_atomic_transforms_noalloc([_dev(m) for m in host], two_component=two_c,
                                               out=_out(nc, 48, len(host)))
-        for (UL, US), r in zip(got, refs):
+        # the U parity tolerances of the other GPU tests: U^L 1e-10 for a free atom, 1e-9 with
+        # more than one nucleus in the potential (the molecular block); U^S 1e-9
+        for i, ((UL, US), r) in enumerate(zip(got, refs)):
             sl, ss = np.abs(r["UL"]).max(), np.abs(r["US"]).max()
+            tol_l = 1e-10 if i == 0 else 1e-9
             for q, (gl, gs, rl, rs) in enumerate(zip(UL, US, _parts(r["UL"], two_c), _parts(r["US"], two_c))):
-                assert np.abs(gl.cpu().numpy() - rl).max() <= 1e-10 * sl, (call, "UL", q)
-                assert np.abs(gs.cpu().numpy() - rs).max() <= 1e-9 * ss, (call, "US", q)
+                el = np.abs(gl.cpu().numpy() - rl).max() / sl
+                es = np.abs(gs.cpu().numpy() - rs).max() / ss
+                assert el <= tol_l, (call, i, "UL", q, el)
+                assert es <= 1e-9, (call, i, "US", q, es)
 
 
 def test_noalloc_call_leaves_device_free_memory_unchanged():
