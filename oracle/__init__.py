@@ -6,9 +6,11 @@ package.  It shares no code with the CUDA path (``paper_1303_4446_gb300``); both
 their inputs from the seeded workload generator ``paper_1303_4446_gb300.workload``,
 which holds none of the decoupling arithmetic.
 
-The oracle follows the paper's *non-orthogonal* formulation (the definition of the
-method), while the CUDA path uses an orthonormalised, GEMM-only formulation; the
-paper's appendix proves the two equal.
+The X2C oracle (x2c.py) follows the paper's *non-orthogonal* formulation (the definition
+of the method), while the CUDA path uses an orthonormalised, GEMM-only formulation; the
+paper's appendix proves the two equal.  BSS and DKHn (fw.py) are defined through the
+orthonormal kinetic basis and the free-particle transformation, and follow Sec. II.B-C
+step by step.
 """
 from .x2c import (  # noqa: F401
     C_LIGHT,
@@ -25,3 +27,4 @@ from .x2c import (  # noqa: F401
     dirac_ground_state,
     electronic_eigenvalues,
 )
+from . import fw  # noqa: F401  BSS and DKHn (Sec. II.B, II.C)
