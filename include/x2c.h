@@ -66,6 +66,22 @@ typedef enum {
                                  molecular matrices (Eq. 43 read literally); one solve per atom */
 } x2c_dlu_potential;
 
+/* The exact-decoupling or approximate transformation behind U^L, U^S (Sec. II):
+ *  X2C_DEC_X2C  (0)  X2C, Sec. II.A: the X-operator transform of the positive-energy solutions.
+ *  X2C_DEC_BSS  (1)  BSS, Sec. II.B: the same solutions reached through the free-particle
+ *                    transformation first; exact decoupling in another unitary frame (same
+ *                    eigenvalues as X2C, a different h).
+ *  n = 2..14         DKHn, Sec. II.C: exponential parametrisation cut at order n in the
+ *                    potential, with the operation count of Table I.  Full builds return the
+ *                    DKHn Hamiltonian E0 - c^2 + sum_{l<=n} E_l; the transforms (atomic ones for
+ *                    DLU, U of x2c_build_full) are the columns exp(-W_1) ... exp(-W_n) [1; 0]
+ *                    cut at order n and renormalised (Eq. 9 holds).
+ * BSS and DKHn diagonalise T in the metric S (Eq. 11) on the device, one CTA per matrix: they
+ * take problems of n <= 160 functions (atoms for DLU; whole systems up to that size for full
+ * builds); larger ones return X2C_ERR_ARG.  x2c_atomic_transforms_noalloc takes X2C only. */
+typedef enum { X2C_DEC_X2C = 0, X2C_DEC_BSS = 1, X2C_DEC_DKH2 = 2 } x2c_decoupling;
+#define X2C_DEC_MAX_DKH_ORDER 14
+
 typedef enum {
   X2C_LOCAL_DLU = 0,  /* every pair block h_AB from the atomic transforms (Eq. 42 in Eq. 8) */
   X2C_LOCAL_DLH = 1   /* diagonal local Hamiltonian (Sec. III.A): only the same-atom blocks
@@ -87,7 +103,7 @@ typedef struct {
                                 buffers are not written).  h0 is symmetric and h1..h3 are
                                 antisymmetric, so the lower blocks follow from the upper ones;
                                 this halves the device-to-host copy.  Other calls: must be 0 */
-  int32_t reserved[1];       /* must be zero */
+  int32_t decoupling;        /* x2c_decoupling: the decoupling transformation (default 0 = X2C) */
 } x2c_options;
 
 typedef struct {

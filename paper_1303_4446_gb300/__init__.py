@@ -14,6 +14,7 @@ from .abi import (DLU_FREE_ATOM, DLU_MOLECULAR_BLOCK, LOCAL_DLH, LOCAL_DLU, PREC
                   PREC_SPLIT_BF16, X2CError)
 
 C_LIGHT = 137.035999
+DEC_X2C, DEC_BSS = 0, 1  # x2c_decoupling; an integer n = 2..14 selects DKHn
 _MAT_KEYS = ("S", "T", "V", "W0", "Wx", "Wy", "Wz")
 
 
@@ -108,9 +109,12 @@ def _stream(stream):
 
 
 def options(two_component=False, c=None, precision=PREC_FP64, dlu_potential=DLU_FREE_ATOM,
-            so_same_atom_only=True, n_slices=0, local_approx=LOCAL_DLU, h_upper_only=False) -> abi.Options:
+            so_same_atom_only=True, n_slices=0, local_approx=LOCAL_DLU, h_upper_only=False,
+            decoupling=DEC_X2C) -> abi.Options:
+    """x2c_options.  decoupling: DEC_X2C (0), DEC_BSS (1) or the DKH order n (2..14)."""
     o = abi.Options()
     o.h_upper_only = int(bool(h_upper_only))
+    o.decoupling = int(decoupling)
     o.local_approx = int(local_approx)
     o.c = float(c) if c else C_LIGHT
     o.two_component = int(bool(two_component))
@@ -163,7 +167,7 @@ def _hout(parts):
 
 
 def x2c_build_full(ctx: Context, m: dict, two_component=False, c=None, want_U=False, stream=None,
-                   out=None, U_out=None):
+                   out=None, U_out=None, decoupling=DEC_X2C):
     """Full X2C: returns dict(h=[h0..], UL=[..], US=[..]) of CUDA tensors (quaternion parts).
     out / U_out = (UL parts, US parts): caller-owned outputs instead of new tensors."""
     nc = 4 if two_component else 1
@@ -179,7 +183,7 @@ def x2c_build_full(ctx: Context, m: dict, two_component=False, c=None, want_U=Fa
             U.UL[q] = UL[q].data_ptr()
             U.US[q] = US[q].data_ptr()
         out.update(UL=UL, US=US)
-    o = options(two_component, c)
+    o = options(two_component, c, decoupling=decoupling)
     ho = _hout(h)
     abi.check(ctx.lib.x2c_build_full(ctx.handle, ctypes.byref(o), ctypes.byref(ms), ctypes.byref(ho),
                                      ctypes.byref(U) if U is not None else None, _stream(stream)),
@@ -208,14 +212,15 @@ class LayoutHolder:
 
 def x2c_build_dlu(ctx: Context, m: dict, offsets, atom_kind=None, kinds=None, two_component=False,
                   c=None, precision=PREC_FP64, dlu_potential=DLU_FREE_ATOM, so_same_atom_only=True,
-                  n_slices=0, local_approx=LOCAL_DLU, out=None, stream=None):
+                  n_slices=0, local_approx=LOCAL_DLU, out=None, stream=None, decoupling=DEC_X2C):
     """DLU build.  m: molecular matrices (CUDA tensors); kinds: list of free-atom input dicts
     (FREE_ATOM mode) indexed by atom_kind.  Returns the list of h parts."""
     nc = 4 if two_component else 1
     ms = mats_struct(m, two_component)
     h = out if out is not None else _alloc_parts(ms.n, nc, m["S"].device)
     lay = LayoutHolder(offsets, atom_kind, kinds, two_component)
-    o = options(two_component, c, precision, dlu_potential, so_same_atom_only, n_slices, local_approx)
+    o = options(two_component, c, precision, dlu_potential, so_same_atom_only, n_slices, local_approx,
+                decoupling=decoupling)
     ho = _hout(h)
     abi.check(ctx.lib.x2c_build_dlu(ctx.handle, ctypes.byref(o), ctypes.byref(lay.s), ctypes.byref(ms),
                                     ctypes.byref(ho), _stream(stream)), "x2c_build_dlu", ctx.handle)
@@ -224,7 +229,7 @@ def x2c_build_dlu(ctx: Context, m: dict, offsets, atom_kind=None, kinds=None, tw
 
 def x2c_build_dlu_batched(ctx: Context, mols: list, layouts: list, two_component=False, c=None,
                           precision=PREC_FP64, dlu_potential=DLU_FREE_ATOM, so_same_atom_only=True,
-                          n_slices=0, local_approx=LOCAL_DLU, outs=None, stream=None):
+                          n_slices=0, local_approx=LOCAL_DLU, outs=None, stream=None, decoupling=DEC_X2C):
     """Batched DLU over several molecules.  mols: list of matrix dicts; layouts: list of
     (offsets, atom_kind, kinds) tuples.  Returns a list of h-part lists."""
     nc = 4 if two_component else 1
@@ -241,13 +246,15 @@ def x2c_build_dlu_batched(ctx: Context, mols: list, layouts: list, two_component
         h = outs[i] if outs is not None else _alloc_parts(ms[i].n, nc, m["S"].device)
         outs_.append(h)
         hs[i] = _hout(h)
-    o = options(two_component, c, precision, dlu_potential, so_same_atom_only, n_slices, local_approx)
+    o = options(two_component, c, precision, dlu_potential, so_same_atom_only, n_slices, local_approx,
+                decoupling=decoupling)
     abi.check(ctx.lib.x2c_build_dlu_batched(ctx.handle, ctypes.byref(o), n_mol, ls, ms, hs, _stream(stream)),
               "x2c_build_dlu_batched", ctx.handle)
     return outs_
 
 
-def x2c_atomic_transforms(ctx: Context, inputs: list, two_component=False, c=None, stream=None, out=None):
+def x2c_atomic_transforms(ctx: Context, inputs: list, two_component=False, c=None, stream=None, out=None,
+                          decoupling=DEC_X2C):
     """Decoupling transforms of independent input sets: list of (UL parts, US parts)
     (`out`: caller-owned list of the same form)."""
     nc = 4 if two_component else 1
@@ -265,7 +272,7 @@ def x2c_atomic_transforms(ctx: Context, inputs: list, two_component=False, c=Non
             us[i].UL[q] = UL[q].data_ptr()
             us[i].US[q] = US[q].data_ptr()
         res.append((UL, US))
-    o = options(two_component, c)
+    o = options(two_component, c, decoupling=decoupling)
     abi.check(ctx.lib.x2c_atomic_transforms(ctx.handle, ctypes.byref(o), k, ms, us, _stream(stream)),
               "x2c_atomic_transforms", ctx.handle)
     return res
@@ -298,7 +305,8 @@ def x2c_atomic_transforms_noalloc(inputs: list, two_component=False, c=None, out
 
 def x2c_build_dlu_host(ctx: Context, m: dict, offsets, atom_kind=None, kinds=None, two_component=False,
                        c=None, precision=PREC_FP64, dlu_potential=DLU_FREE_ATOM, so_same_atom_only=True,
-                       n_slices=0, local_approx=LOCAL_DLU, out=None, stream=None, h_upper_only=False):
+                       n_slices=0, local_approx=LOCAL_DLU, out=None, stream=None, h_upper_only=False,
+                       decoupling=DEC_X2C):
     """DLU build from HOST arrays (numpy float64 or CPU torch tensors, pinned or not);
     h parts are written into `out` (host arrays) or new numpy arrays.  h_upper_only: only the
     upper block triangle of each part is written (the rest of `out` is left as it was)."""
@@ -331,7 +339,7 @@ def x2c_build_dlu_host(ctx: Context, m: dict, offsets, atom_kind=None, kinds=Non
     for q in range(nc):
         ho.h[q] = hp(out[q])
     o = options(two_component, c, precision, dlu_potential, so_same_atom_only, n_slices, local_approx,
-                h_upper_only)
+                h_upper_only, decoupling)
     abi.check(ctx.lib.x2c_build_dlu_host(ctx.handle, ctypes.byref(o), ctypes.byref(lay.s), ctypes.byref(ms),
                                          ctypes.byref(ho), _stream(stream)), "x2c_build_dlu_host", ctx.handle)
     return out
@@ -553,14 +561,15 @@ class Server:
 
     def submit_dlu(self, m, offsets, atom_kind, kinds, kind_keys=None, two_component=False, c=None,
                    precision=PREC_FP64, n_slices=0, local_approx=LOCAL_DLU, so_same_atom_only=True,
-                   dlu_potential=DLU_FREE_ATOM, out=None, host=False, t_arrival=-1.0):
+                   dlu_potential=DLU_FREE_ATOM, out=None, host=False, t_arrival=-1.0, decoupling=DEC_X2C):
         """Queue a DLU build.  m: molecular matrices (CUDA tensors, or host arrays with
         host=True; row-major views such as big[:n, :n] are allowed); kinds: free-atom input
         dicts; kind_keys: one integer cache key per kind (0 = not cached); out: result
         buffers (device, or host with host=True), None = server-allocated device result."""
         nc = 4 if two_component else 1
         req = abi.Request()
-        req.opt = options(two_component, c, precision, dlu_potential, so_same_atom_only, n_slices, local_approx)
+        req.opt = options(two_component, c, precision, dlu_potential, so_same_atom_only, n_slices, local_approx,
+                          decoupling=decoupling)
         req.kind, req.memory = REQ_DLU, (MEM_HOST if host else MEM_DEVICE)
         req.mol, ld = self._mats(m, two_component, host)
         req.ld = ld
@@ -583,11 +592,12 @@ class Server:
         req.t_arrival = float(t_arrival)
         return self._submit(req, (m, kinds, lay, keys, outs), req.mol.n, nc)
 
-    def submit_full(self, m, two_component=False, c=None, out=None, host=False, t_arrival=-1.0):
+    def submit_full(self, m, two_component=False, c=None, out=None, host=False, t_arrival=-1.0,
+                    decoupling=DEC_X2C):
         """Queue a full X2C build of the whole system (see submit_dlu for the arguments)."""
         nc = 4 if two_component else 1
         req = abi.Request()
-        req.opt = options(two_component, c)
+        req.opt = options(two_component, c, decoupling=decoupling)
         req.kind, req.memory = REQ_FULL, (MEM_HOST if host else MEM_DEVICE)
         req.mol, ld = self._mats(m, two_component, host)
         req.ld = ld

@@ -28,7 +28,7 @@ class Options(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("dlu_potential", ctypes.c_int32),
                 ("so_same_atom_only", ctypes.c_int32), ("n_slices", ctypes.c_int32),
                 ("local_approx", ctypes.c_int32), ("h_upper_only", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 1)]
+                ("decoupling", ctypes.c_int32)]
 
 
 class Mats(ctypes.Structure):

@@ -15,7 +15,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(HERE, "libx2c_gb300.so")
 SOURCES = ["abi.cu", "solve.cu", "assemble.cu", "host.cu", "split.cu", "noalloc.cu", "serve.cu", "integrals.cu"]
-HEADERS = ["common.cuh", "gemm_f64.cuh", "umma.cuh", "split_int.cuh", "serve_policy.h", "integrals_math.cuh"]
+HEADERS = ["common.cuh", "gemm_f64.cuh", "umma.cuh", "split_int.cuh", "serve_policy.h", "integrals_math.cuh",
+           "solve_fw.cuh", "dkh_plan.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                      "-I", os.path.join(ROOT, "include"), "-diag-suppress", "177"]

@@ -5,6 +5,7 @@
 #include <tuple>
 
 #include "common.cuh"
+#include "dkh_plan.h"
 
 // A build captured into a CUDA graph (x2c_ctx_set_graphs), keyed by its launch plan.
 struct x2c_ctx::GraphEntry {
@@ -171,8 +172,7 @@ x2c_status check_options(const x2c_options *o) {
   if (o->n_slices < 0 || o->n_slices > 8) return X2C_ERR_ARG;
   if (o->local_approx != X2C_LOCAL_DLU && o->local_approx != X2C_LOCAL_DLH) return X2C_ERR_ARG;
   if (o->h_upper_only != 0) return X2C_ERR_ARG;  // only x2c_build_dlu_host takes it (and clears it)
-  for (int r : o->reserved)
-    if (r != 0) return X2C_ERR_ARG;
+  if (o->decoupling < 0 || o->decoupling > X2C_DEC_MAX_DKH_ORDER) return X2C_ERR_ARG;
   return X2C_OK;
 }
 
@@ -188,6 +188,16 @@ double credited_pair_flops(int nA, int nB, int nc, bool diag, bool so) {
 
 // Conventional counts of the paper's operation list (Tables II and III) for one
 // decoupling problem of size n: eigen 9 m^3, inversion 2 m^3, product 2 m^3, complex x4.
+// The DKHn Hamiltonian of one system: the kinetic basis (one diagonalisation of n, K^-1, the
+// potential transforms) and the P(n) products of Table I, conventional counts (eigen with
+// vectors 9 n^3, inverse 2 n^3, product 2 n^3; a quaternion product 16 real products) plus
+// the back transformation (2 products per part).
+double hamiltonian_flops(int n, int nc, int order) {
+  const double n3 = (double)n * n * n;
+  const double qp = (nc == 4 ? 16.0 : 1.0) * 2.0 * n3;
+  return 9 * n3 + 2 * n3 + 2 * (1 + nc) * 2 * n3 + dkh::hamiltonian_products(order) * qp + nc * 2 * 2 * n3;
+}
+
 double credited_solve_flops(int n, int nc) {
   const double N3 = (double)n * n * n;
   if (nc == 1) return (2 * 9 + 9 * 8 + 2 * 2 + 15 * 2) * N3;
@@ -218,6 +228,12 @@ struct BuildPlan {
   double credited = 0;
 };
 
+// Scratch of one size group's decoupling solve (X2C, or BSS / DKHn).
+size_t solve_bytes(const x2c_options *opt, int nb, int n, int nc) {
+  return opt->decoupling == X2C_DEC_X2C ? solve_workspace_bytes(nb, n, nc)
+                                        : solve_fw_workspace_bytes(nb, n, nc, opt->decoupling);
+}
+
 x2c_status run_plan(x2c_ctx *ctx, const x2c_options *opt, BuildPlan &plan, cudaStream_t st,
                     std::vector<double *> *UL_out = nullptr, std::vector<double *> *US_out = nullptr,
                     size_t *dry_bytes = nullptr) {
@@ -228,10 +244,13 @@ x2c_status run_plan(x2c_ctx *ctx, const x2c_options *opt, BuildPlan &plan, cudaS
   for (size_t i = 0; i < plan.problems.size(); ++i)
     if (!plan.problems[i].preUL) groups[plan.problems[i].n].push_back((int)i);
   size_t u_doubles = 0, solve_ws = 0, desc_bytes = 0;
+  if (opt->decoupling != X2C_DEC_X2C)
+    for (auto &g : groups)
+      if (!fw_supported(g.first, opt->decoupling)) return X2C_ERR_ARG;
   for (auto &g : groups) {
     const size_t n2 = (size_t)g.first * g.first;
     u_doubles += 2 * g.second.size() * nc * n2;
-    solve_ws += solve_workspace_bytes((int)g.second.size(), g.first, nc) + 256;  // groups run concurrently
+    solve_ws += solve_bytes(opt, (int)g.second.size(), g.first, nc) + 256;  // groups run concurrently
     desc_bytes += ((g.second.size() * sizeof(InputDesc) + 255) / 256) * 256;
   }
   const size_t np = plan.problems.size();
@@ -307,12 +326,15 @@ x2c_status run_plan(x2c_ctx *ctx, const x2c_options *opt, BuildPlan &plan, cudaS
       double *UL = Ustore + uo;
       double *US = UL + (size_t)nb * nc * n2;
       uo += 2 * (size_t)nb * nc * n2;
-      const size_t need = solve_workspace_bytes(nb, n, nc);
+      const size_t need = solve_bytes(opt, nb, n, nc);
       Arena mine;
       mine.base = static_cast<char *>(scratch.take_bytes(need));
       mine.cap = need;
       if (!mine.base) return X2C_ERR_NOMEM;
-      X2C_TRY(solve_transforms(ctx, gs[gi], c, nb, n, nc, ddescs[gi], UL, US, mine));
+      if (opt->decoupling == X2C_DEC_X2C)
+        X2C_TRY(solve_transforms(ctx, gs[gi], c, nb, n, nc, ddescs[gi], UL, US, mine));
+      else
+        X2C_TRY(solve_transforms_fw(ctx, gs[gi], c, nb, n, nc, opt->decoupling, ddescs[gi], UL, US, mine));
       ++gi;
     }
     for (int i = 1; i < ng && i <= kMaxAuxStreams; ++i) {
@@ -521,6 +543,7 @@ std::string plan_key(const x2c_ctx *ctx, int entry, const x2c_options *opt, cons
   k.put(opt->so_same_atom_only);
   k.put(opt->n_slices);
   k.put(opt->local_approx);
+  k.put(opt->decoupling);
   k.put(plan.nc);
   k.put(plan.max_n);
   k.put(ctx->split_variant);
@@ -755,9 +778,36 @@ x2c_status full_build(x2c_ctx *ctx, const x2c_options *opt, const x2c_mats *mol,
   plan.nc = nc;
   KindIndex kinds;
   X2C_TRY(add_molecule(plan, &o, &lay, mol, h, 0, kinds));
+  const bool dkh = o.decoupling >= 2;
+  if (dkh) {
+    // DKHn: h is the DKHn Hamiltonian itself (Sec. II.C), not Eq. 8 with the cut transforms;
+    // the plan then only solves for the transforms, when they are asked for
+    if (!fw_supported(mol->n, o.decoupling)) return X2C_ERR_ARG;
+    plan.pairs.clear();
+  }
   std::vector<double *> ULp, USp;
   auto enqueue = [&](cudaStream_t s, size_t *dry) -> x2c_status {
-    X2C_TRY(run_plan(ctx, &o, plan, s, &ULp, &USp, dry));
+    if (dkh) {
+      const size_t need = dkh_hamiltonian_workspace_bytes(mol->n, nc, o.decoupling) + 1024;
+      size_t u_need = 0;
+      if (U) X2C_TRY(run_plan(ctx, &o, plan, s, nullptr, nullptr, &u_need));
+      if (dry) {
+        *dry = std::max(need, u_need);
+        return X2C_OK;
+      }
+      Arena ar;
+      X2C_TRY(ensure_workspace(ctx, std::max(need, u_need), &ar, s));
+      auto *dd = reinterpret_cast<InputDesc *>(ar.take_bytes(sizeof(InputDesc)));
+      if (!dd) return X2C_ERR_NOMEM;
+      const InputDesc hd = input_desc(mol, nc, 0, mol->n);
+      X2C_TRY(upload(ctx, s, dd, &hd, sizeof(InputDesc)));
+      X2C_TRY(dkh_hamiltonian(ctx, s, speed_of_light(&o), mol->n, nc, o.decoupling, dd, h->h, ar));
+      plan.credited += hamiltonian_flops(mol->n, nc, o.decoupling);
+      if (!U) return X2C_OK;
+      X2C_TRY(run_plan(ctx, &o, plan, s, &ULp, &USp, nullptr));
+    } else {
+      X2C_TRY(run_plan(ctx, &o, plan, s, &ULp, &USp, dry));
+    }
     if (dry || !U) return X2C_OK;
     const size_t n2 = (size_t)mol->n * mol->n;
     for (int q = 0; q < nc; ++q) {

@@ -242,6 +242,17 @@ struct InputDesc {
 constexpr int kMaxSolveN = 168;  // largest n factorised in one CTA (bigger: blocked)
 x2c_status solve_transforms(x2c_ctx *ctx, cudaStream_t st, double c, int nb, int n, int nc,
                             const InputDesc *d_in, double *UL, double *US, Arena ar);
+// BSS (decoupling = 1) and DKHn (decoupling = n >= 2) transforms of nb problems of size n
+// (solve_fw.cuh); problems of n <= 160 (fw_supported).
+constexpr int kMaxDkhOrder = X2C_DEC_MAX_DKH_ORDER;
+bool fw_supported(int n, int decoupling);
+size_t solve_fw_workspace_bytes(int nb, int n, int nc, int decoupling);
+x2c_status solve_transforms_fw(x2c_ctx *ctx, cudaStream_t st, double c, int nb, int n, int nc, int decoupling,
+                               const InputDesc *d_in, double *UL, double *US, Arena ar);
+// The DKHn Hamiltonian of one whole system (h: nc device parts of n x n).
+size_t dkh_hamiltonian_workspace_bytes(int n, int nc, int order);
+x2c_status dkh_hamiltonian(x2c_ctx *ctx, cudaStream_t st, double c, int n, int nc, int order, const InputDesc *d_in,
+                           double *const *h, Arena ar);
 size_t solve_workspace_bytes(int nb, int n, int nc);
 
 // Pair-block assembly of h = U+ D U for block-diagonal U (Eq. 8 with Eq. 42).

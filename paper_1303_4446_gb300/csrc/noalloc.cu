@@ -68,6 +68,7 @@ extern "C" x2c_status x2c_atomic_transforms_noalloc(const x2c_options *opt, int3
                                                     void *stream) {
   if (!opt || n_problems < 1 || !inputs || !U) return X2C_ERR_ARG;
   if (opt->two_component != 0 && opt->two_component != 1) return X2C_ERR_ARG;
+  if (opt->decoupling != X2C_DEC_X2C || opt->h_upper_only != 0) return X2C_ERR_ARG;  // X2C transforms only
   const int nc = opt->two_component ? 4 : 1;
   const int n = inputs[0].n;
   if (n < 1 || n > x2c::kMaxSolveN) return X2C_ERR_ARG;

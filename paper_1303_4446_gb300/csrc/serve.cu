@@ -29,7 +29,7 @@ constexpr size_t kLargePairs = 2000;  // builds above this many pair blocks coun
 constexpr int kFreeSMs = 32;          // SMs a large build leaves to the other slots
 
 struct CacheEntry {
-  std::tuple<uint64_t, int, int, uint64_t> key;  // kind key, n, nc, bits of c
+  std::tuple<uint64_t, int, int, uint64_t> key;  // kind key, n, nc | decoupling << 8, bits of c
   double *U = nullptr;                           // U^L (nc n^2) then U^S (nc n^2)
   size_t bytes = 0;
   cudaEvent_t ready = nullptr;                   // recorded after the solve, on its slot
@@ -253,7 +253,7 @@ size_t x2c_server::extra_bytes(Slot &sl, const std::vector<ReqPtr> &batch, size_
       us[i].assign(r.kinds.size(), nullptr);
       for (size_t k = 0; k < r.kinds.size(); ++k) {
         if (!r.keys[k] || !r.used[k]) continue;
-        auto key = std::make_tuple(r.keys[k], r.kinds[k].n, nc, dbits(x2c::speed_of_light(&opt)));
+        auto key = std::make_tuple(r.keys[k], r.kinds[k].n, nc | (opt.decoupling << 8), dbits(x2c::speed_of_light(&opt)));
         auto it = cache.find(key);
         const double *p;
         if (it != cache.end()) {
@@ -488,7 +488,7 @@ void x2c_server::launch(int si, std::vector<ReqPtr> &batch) {
           continue;
         }
         const int n = r.kinds[k].n;
-        auto key = std::make_tuple(r.keys[k], n, nc, dbits(x2c::speed_of_light(&opt)));
+        auto key = std::make_tuple(r.keys[k], n, nc | (opt.decoupling << 8), dbits(x2c::speed_of_light(&opt)));
         auto it = cache.find(key);
         EntryPtr e;
         if (it != cache.end()) {

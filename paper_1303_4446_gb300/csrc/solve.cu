@@ -26,6 +26,7 @@
 #include <cmath>
 
 #include "common.cuh"
+#include "dkh_plan.h"
 #include "gemm_f64.cuh"
 
 namespace x2c {
@@ -542,6 +543,87 @@ x2c_status check(x2c_ctx *ctx, cudaStream_t st, int nb, int d, int nc, const dou
   return launched(ctx, "check_kernel", st);
 }
 
+// Z <- sign(Z0), Z0 = H^p + c^2 assembled from the orthonormal blocks (Vt, the L-S
+// coupling LSm, Wt; Eq. 14), scaled into [-1, 1] by its Gershgorin bound, by the per-problem
+// scaled Newton-Schulz schedule; then the convergence (||Z^2 - 1||) and half/half split
+// (|trace Z| < 1/2) checks.  Z, Zn, Y: nb nc (2n)^2 doubles each; Z and Zn are swapped so
+// that Z holds the result.
+x2c_status sign_of_hp(x2c_ctx *ctx, cudaStream_t st, int nb, int n, int nc, double c, const double *Vt,
+                      const double *LSm, const double *Wt, double *&Z, double *&Zn, double *Y,
+                      unsigned long long *slot, double *trace, double *sched, int *gate, double *part, int *status) {
+  const int d = 2 * n;
+  const int64_t d2 = (int64_t)d * d;
+  tbegin(ctx, st);
+  assemble_hp_kernel<<<aux_grid(nb * nc, d2), 256, 0, st>>>(n, nc, c, Vt, LSm, Wt, Z);
+  X2C_TRY(launched(ctx, "assemble_hp_kernel", st));
+  X2C_TRY_CUDA(ctx, cudaMemsetAsync(slot, 0, sizeof(unsigned long long) * nb, st));
+  tbegin(ctx, st);
+  gershgorin_kernel<<<aux_grid(nb, (int64_t)d * 32 * nc), 256, 0, st>>>(d, nc, Z, slot);
+  X2C_TRY(launched(ctx, "gershgorin_kernel", st));
+  tbegin(ctx, st);
+  scale_kernel<<<aux_grid(nb, nc * d2), 256, 0, st>>>(nc * d2, Z, slot, status);
+  X2C_TRY(launched(ctx, "scale_kernel", st));
+  // Sign function by the scaled Newton-Schulz schedule, per problem (sign_schedule_kernel);
+  // the host enqueues the longest possible schedule and the device skips the steps past the
+  // longest one it needs.
+  const int kmax = static_cast<int>(sign_schedule(kSignLowerBound).size());
+  if (kmax > kSignMaxSteps) return X2C_ERR_ARG;
+  tbegin(ctx, st);
+  sign_schedule_kernel<<<1, 256, 0, st>>>(nb, c * c, slot, sched, kmax, gate);
+  X2C_TRY(launched(ctx, "sign_schedule_kernel", st));
+  const bool herm_d = d >= kHermMin;
+  for (int k = 0; k < kmax; ++k) {
+    // Y = Z Z;  Zn = (3a/2) Z - (a^3/2) Z Y   (Z, Y commute and are Hermitian)
+    // (named apart from the other products: how many of them run is decided on the device, so
+    // they report no flops)
+    const char *sign_name = "solve_sign_gemm";
+    if (herm_d) {
+      X2C_TRY(quat_gemm_herm(ctx, st, nb, d, nc, Z, Z, StoreAxpbyHerm{Y, nullptr, d, (int64_t)nc * d2, 1.0, 0.0, d},
+                             gate, k, sign_name));
+      X2C_TRY(quat_gemm_herm(ctx, st, nb, d, nc, Z, Y,
+                             StoreSignStepHerm{Zn, Z, d, (int64_t)nc * d2, sched + k, kmax, d}, gate, k, sign_name));
+    } else {
+      X2C_TRY(quat_gemm(ctx, st, nb, d, nc, Z, Z, 1.0, store_plain(Y, d, nc), part, gate, k, sign_name));
+      StoreSignStep upd{Zn, Z, d, (int64_t)nc * d2, sched + k, kmax};
+      X2C_TRY(quat_gemm(ctx, st, nb, d, nc, Z, Y, 1.0, upd, part, gate, k, sign_name));
+    }
+    std::swap(Z, Zn);
+  }
+  X2C_TRY(check(ctx, st, nb, d, nc, Y, Z, kSignTol, slot, trace, status));
+  return X2C_OK;
+}
+
+// Yk <- G^1/2 and Zk <- G^-1/2 of Hermitian G with eigenvalues in (0, 1] (coupled
+// Newton-Schulz, kSqrtIters steps, then ||T - 1|| <= kSqrtTol checked on the device).  Every
+// buffer holds nb nc n^2 doubles; Yk/Yk2 and Zk/Zk2 are swapped so Yk, Zk hold the result.
+x2c_status coupled_sqrt(x2c_ctx *ctx, cudaStream_t st, int nb, int n, int nc, const double *G, double *&Yk,
+                        double *&Zk, double *Tm, double *&Yk2, double *&Zk2, double *part, unsigned long long *slot,
+                        int *status) {
+  const int64_t n2 = (int64_t)n * n;
+  const bool herm_n = n >= kHermMin;
+  X2C_TRY_CUDA(ctx, cudaMemcpyAsync(Yk, G, sizeof(double) * nb * nc * n2, cudaMemcpyDeviceToDevice, st));
+  tbegin(ctx, st);
+  identity_kernel<<<aux_grid(nb, nc * n2), 256, 0, st>>>(n, nc, Zk);
+  X2C_TRY(launched(ctx, "identity_kernel", st));
+  for (int it = 0; it < kSqrtIters; ++it) {
+    // Tm = 3/2 - Zk Yk / 2;  Yk <- Yk Tm;  Zk <- Tm Zk   (all functions of P_LL: Hermitian)
+    if (herm_n) {
+      X2C_TRY(quat_gemm_herm(ctx, st, nb, n, nc, Zk, Yk, StoreShiftIdentityHerm{Tm, n, (int64_t)nc * n2, n, -0.5, 1.5}));
+      X2C_TRY(quat_gemm_herm(ctx, st, nb, n, nc, Yk, Tm, StoreAxpbyHerm{Yk2, nullptr, n, (int64_t)nc * n2, 1.0, 0.0, n}));
+      X2C_TRY(quat_gemm_herm(ctx, st, nb, n, nc, Tm, Zk, StoreAxpbyHerm{Zk2, nullptr, n, (int64_t)nc * n2, 1.0, 0.0, n}));
+    } else {
+      StoreShiftIdentity tm{Tm, n, (int64_t)nc * n2, n, -0.5, 1.5};
+      X2C_TRY(quat_gemm(ctx, st, nb, n, nc, Zk, Yk, 1.0, tm, part));
+      X2C_TRY(quat_gemm(ctx, st, nb, n, nc, Yk, Tm, 1.0, store_plain(Yk2, n, nc), part));
+      X2C_TRY(quat_gemm(ctx, st, nb, n, nc, Tm, Zk, 1.0, store_plain(Zk2, n, nc), part));
+    }
+    std::swap(Yk, Yk2);
+    std::swap(Zk, Zk2);
+  }
+  X2C_TRY(check(ctx, st, nb, n, nc, Tm, nullptr, kSqrtTol, slot, nullptr, status));
+  return X2C_OK;
+}
+
 }  // namespace
 
 size_t solve_workspace_bytes(int nb, int n, int nc) {
@@ -617,68 +699,13 @@ x2c_status solve_transforms(x2c_ctx *ctx, cudaStream_t st, double c, int nb, int
     X2C_TRY((gemm_sq(ctx, st, nb * nc, n, Mat<false>{tmp, n, n2, 1.0},
                                  MatDiv<true>{inv + n2, n, 2 * n2, nc, 1.0}, StoreAxpby{Wt, nullptr, n, n2, 0.5, 0.0})));
   }
-  // 2. Z = H^p + c^2, scaled into [-1, 1].
-  tbegin(ctx, st);
-  assemble_hp_kernel<<<aux_grid(nb * nc, d2), 256, 0, st>>>(n, nc, c, Vt, LSm, Wt, Z);
-  X2C_TRY(launched(ctx, "assemble_hp_kernel", st));
-  X2C_TRY_CUDA(ctx, cudaMemsetAsync(slot, 0, sizeof(unsigned long long) * nb, st));
-  tbegin(ctx, st);
-  gershgorin_kernel<<<aux_grid(nb, (int64_t)d * 32 * nc), 256, 0, st>>>(d, nc, Z, slot);
-  X2C_TRY(launched(ctx, "gershgorin_kernel", st));
-  tbegin(ctx, st);
-  scale_kernel<<<aux_grid(nb, nc * d2), 256, 0, st>>>(nc * d2, Z, slot, status);
-  X2C_TRY(launched(ctx, "scale_kernel", st));
-  // 3. Sign function by the scaled Newton-Schulz schedule, per problem (sign_schedule_kernel);
-  // the host enqueues the longest possible schedule and the device skips the steps past the
-  // longest one it needs.
-  const int kmax = static_cast<int>(sign_schedule(kSignLowerBound).size());
-  if (kmax > kSignMaxSteps) return X2C_ERR_ARG;
-  tbegin(ctx, st);
-  sign_schedule_kernel<<<1, 256, 0, st>>>(nb, c * c, slot, sched, kmax, gate);
-  X2C_TRY(launched(ctx, "sign_schedule_kernel", st));
-  const bool herm_d = d >= kHermMin, herm_n = n >= kHermMin;
-  for (int k = 0; k < kmax; ++k) {
-    // Y = Z Z;  Zn = (3a/2) Z - (a^3/2) Z Y   (Z, Y commute and are Hermitian)
-    // (named apart from the other products: how many of them run is decided on the device, so
-    // they report no flops)
-    const char *sign_name = "solve_sign_gemm";
-    if (herm_d) {
-      X2C_TRY(quat_gemm_herm(ctx, st, nb, d, nc, Z, Z, StoreAxpbyHerm{Y, nullptr, d, (int64_t)nc * d2, 1.0, 0.0, d},
-                             gate, k, sign_name));
-      X2C_TRY(quat_gemm_herm(ctx, st, nb, d, nc, Z, Y,
-                             StoreSignStepHerm{Zn, Z, d, (int64_t)nc * d2, sched + k, kmax, d}, gate, k, sign_name));
-    } else {
-      X2C_TRY(quat_gemm(ctx, st, nb, d, nc, Z, Z, 1.0, store_plain(Y, d, nc), part, gate, k, sign_name));
-      StoreSignStep upd{Zn, Z, d, (int64_t)nc * d2, sched + k, kmax};
-      X2C_TRY(quat_gemm(ctx, st, nb, d, nc, Z, Y, 1.0, upd, part, gate, k, sign_name));
-    }
-    std::swap(Z, Zn);
-  }
-  X2C_TRY(check(ctx, st, nb, d, nc, Y, Z, kSignTol, slot, trace, status));
+  // 2-3. Z <- sign(H^p + c^2) (scaled Newton-Schulz), with its convergence and split checks.
+  X2C_TRY(sign_of_hp(ctx, st, nb, n, nc, c, Vt, LSm, Wt, Z, Zn, Y, slot, trace, sched, gate, part, status));
   tbegin(ctx, st);
   projector_kernel<<<aux_grid(nb * nc, n2), 256, 0, st>>>(n, nc, Z, PLL, PSL);
   X2C_TRY(launched(ctx, "projector_kernel", st));
   // 4. Coupled Newton-Schulz: Yk -> P_LL^1/2, Zk -> P_LL^-1/2.
-  X2C_TRY_CUDA(ctx, cudaMemcpyAsync(Yk, PLL, sizeof(double) * nb * nc * n2, cudaMemcpyDeviceToDevice, st));
-  tbegin(ctx, st);
-  identity_kernel<<<aux_grid(nb, nc * n2), 256, 0, st>>>(n, nc, Zk);
-  X2C_TRY(launched(ctx, "identity_kernel", st));
-  for (int it = 0; it < kSqrtIters; ++it) {
-    // Tm = 3/2 - Zk Yk / 2;  Yk <- Yk Tm;  Zk <- Tm Zk   (all functions of P_LL: Hermitian)
-    if (herm_n) {
-      X2C_TRY(quat_gemm_herm(ctx, st, nb, n, nc, Zk, Yk, StoreShiftIdentityHerm{Tm, n, (int64_t)nc * n2, n, -0.5, 1.5}));
-      X2C_TRY(quat_gemm_herm(ctx, st, nb, n, nc, Yk, Tm, StoreAxpbyHerm{Yk2, nullptr, n, (int64_t)nc * n2, 1.0, 0.0, n}));
-      X2C_TRY(quat_gemm_herm(ctx, st, nb, n, nc, Tm, Zk, StoreAxpbyHerm{Zk2, nullptr, n, (int64_t)nc * n2, 1.0, 0.0, n}));
-    } else {
-      StoreShiftIdentity tm{Tm, n, (int64_t)nc * n2, n, -0.5, 1.5};
-      X2C_TRY(quat_gemm(ctx, st, nb, n, nc, Zk, Yk, 1.0, tm, part));
-      X2C_TRY(quat_gemm(ctx, st, nb, n, nc, Yk, Tm, 1.0, store_plain(Yk2, n, nc), part));
-      X2C_TRY(quat_gemm(ctx, st, nb, n, nc, Tm, Zk, 1.0, store_plain(Zk2, n, nc), part));
-    }
-    std::swap(Yk, Yk2);
-    std::swap(Zk, Zk2);
-  }
-  X2C_TRY(check(ctx, st, nb, n, nc, Tm, nullptr, kSqrtTol, slot, nullptr, status));
+  X2C_TRY(coupled_sqrt(ctx, st, nb, n, nc, PLL, Yk, Zk, Tm, Yk2, Zk2, part, slot, status));
   // 5. X'R' = P_SL P_LL^-1/2
   X2C_TRY(quat_gemm(ctx, st, nb, n, nc, PSL, Zk, 1.0, store_plain(XR, n, nc), part));
   // 6. U^L_q = L^-T (R'_q L^T),  U^S_q = sqrt2 c M^-T (X'R'_q L^T)   (batch over problem x part)
@@ -694,5 +721,7 @@ x2c_status solve_transforms(x2c_ctx *ctx, cudaStream_t st, double c, int nb, int
   }
   return X2C_OK;
 }
+
+#include "solve_fw.cuh"
 
 }  // namespace x2c

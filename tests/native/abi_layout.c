@@ -8,7 +8,7 @@ int main(void) {
   printf("options %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(x2c_options), offsetof(x2c_options, two_component),
          offsetof(x2c_options, precision), offsetof(x2c_options, so_same_atom_only),
          offsetof(x2c_options, n_slices), offsetof(x2c_options, local_approx), offsetof(x2c_options, h_upper_only),
-         offsetof(x2c_options, reserved));
+         offsetof(x2c_options, decoupling));
   printf("property %zu %zu %zu\n", sizeof(x2c_property), offsetof(x2c_property, LL), offsetof(x2c_property, SS));
   printf("mats %zu %zu %zu\n", sizeof(x2c_mats), offsetof(x2c_mats, S), offsetof(x2c_mats, Wz));
   printf("hout %zu\n", sizeof(x2c_hout));

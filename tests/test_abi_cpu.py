@@ -44,7 +44,7 @@ def test_ctypes_structs_match_header(tmp_path):
     O = abi.Options
     assert out["options"] == [ctypes.sizeof(O), O.two_component.offset, O.precision.offset,
                               O.so_same_atom_only.offset, O.n_slices.offset, O.local_approx.offset,
-                              O.h_upper_only.offset, O.reserved.offset]
+                              O.h_upper_only.offset, O.decoupling.offset]
     assert out["property"] == [ctypes.sizeof(abi.Property), abi.Property.LL.offset, abi.Property.SS.offset]
     assert out["mats"] == [ctypes.sizeof(abi.Mats), abi.Mats.S.offset, abi.Mats.Wz.offset]
     assert out["hout"] == [ctypes.sizeof(abi.HOut)]
