@@ -2,7 +2,12 @@
 (oracle/fw.py), through the C ABI: full builds (h, U^L, U^S), atomic transforms, and DLU
 with BSS / DKHn atomic transforms (FP64 and split-precision assembly).
 
-Tolerances as for X2C: h within 1e-10 max|h| (split assembly: 1e-9), U within 1e-9 max|U|."""
+Tolerances: h within 1e-10 max|h| (split assembly: 1e-9), as for X2C.  U within
+max(1e-9, 10 x floor) max|U|, where the floor is how far the oracle's own U moves when the
+inputs are perturbed by one unit in the last place: both methods reach U^S through the
+kinetic basis, U^S = 2c K p^-1 Y_S K^-1, and the factor 2c/p of the most diffuse kinetic
+eigenfunctions magnifies rounding in their small components (s48, two-component: the floor
+is 6e-6 of max|U^S| while h moves by 1e-13 and U^L by 3e-10)."""
 import numpy as np
 import pytest
 
@@ -36,6 +41,23 @@ def err(got, ref_full, two_c):
     return max(np.abs(g.cpu().numpy() - r).max() for g, r in zip(got, parts(ref_full, two_c))) / scale
 
 
+def perturbed(m, seed=1):
+    """The inputs moved by about one unit in the last place (symmetry kept)."""
+    rng = np.random.default_rng(seed)
+    out = {}
+    for k, a in m.items():
+        e = rng.standard_normal(a.shape) * 2.0**-52 * np.abs(a)
+        out[k] = a + 0.5 * (e + (e.T if k in ("S", "T", "V", "W0") else -e.T))
+    return out
+
+
+def u_tol(f, m, r, key, two_c):
+    """max(1e-9, 10 x the oracle's own change of r[key] under perturbed inputs)."""
+    rp = f(perturbed(m))
+    floor = max(np.abs(a - b).max() for a, b in zip(parts(rp[key], two_c), parts(r[key], two_c)))
+    return max(1e-9, 10 * floor / np.abs(r[key]).max())
+
+
 CASES = [("atom", "s30", False), ("atom", "s48", True), ("ag4", "s30", False), ("ag4", "s30", True)]
 
 
@@ -52,8 +74,8 @@ def test_bss_full(ctx, kind, basis, two_c):
     out = x.x2c_build_full(ctx, dev(m), two_component=two_c, want_U=True, decoupling=x.DEC_BSS)
     ctx.status()
     assert err(out["h"], r["h"], two_c) <= 1e-10
-    assert err(out["UL"], r["UL"], two_c) <= 1e-9
-    assert err(out["US"], r["US"], two_c) <= 1e-9
+    assert err(out["UL"], r["UL"], two_c) <= u_tol(fw.bss_full, m, r, "UL", two_c)
+    assert err(out["US"], r["US"], two_c) <= u_tol(fw.bss_full, m, r, "US", two_c)
 
 
 @pytest.mark.parametrize("order", [2, 3, 4, 8])
@@ -73,8 +95,9 @@ def test_dkh_transforms(ctx, basis, two_c, order):
     r = fw.dkh_transforms(m, order)
     (UL, US), = x.x2c_atomic_transforms(ctx, [dev(m)], two_component=two_c, decoupling=order)
     ctx.status()
-    assert err(UL, r["UL"], two_c) <= 1e-9
-    assert err(US, r["US"], two_c) <= 1e-9
+    f = lambda mm: fw.dkh_transforms(mm, order)
+    assert err(UL, r["UL"], two_c) <= u_tol(f, m, r, "UL", two_c)
+    assert err(US, r["US"], two_c) <= u_tol(f, m, r, "US", two_c)
 
 
 @pytest.mark.parametrize("prec", [x.PREC_FP64, x.PREC_SPLIT_BF16])
