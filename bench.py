@@ -59,6 +59,9 @@ WORKLOADS = {
     "ag55_sf_full": dict(L=55, basis="s48", two_c=False, full=True),
     "ag55_2c_full": dict(L=55, basis="s48", two_c=True, full=True),
     "ag13_2c_full": dict(L=13, basis="s48", two_c=True, full=True),
+    # DLU with DKH2 (Sec. II.C) or BSS (Sec. II.B) atomic transforms instead of X2C ones
+    "ag309_2c_dkh2": dict(L=309, basis="s48", two_c=True, decoupling=2),
+    "ag309_2c_bss": dict(L=309, basis="s48", two_c=True, decoupling=1),
 }
 
 
@@ -176,14 +179,20 @@ def make_inputs(cfg, seed=w.DEFAULT_SEED):
     return mol, m, kind
 
 
-def cpu_oracle_rate(mol, m, kind, two_c, budget_s, seed=1, solves=1):
+def cpu_oracle_rate(mol, m, kind, two_c, budget_s, seed=1, solves=1, decoupling=0):
     """Oracle builds/s from the atomic solve (times `solves` per build) plus a timed seeded
     sample of pair blocks, extrapolated to all pair blocks.  Returns (builds/s,
     n_sampled_pairs, seconds)."""
     import oracle
+    from oracle import fw
 
     t0 = time.perf_counter()
-    r = oracle.x2c_full(kind)
+    if decoupling == 0:
+        r = oracle.x2c_full(kind)
+    elif decoupling == 1:
+        r = fw.bss_full(kind)
+    else:
+        r = fw.dkh_transforms(kind, decoupling)
     t_atom = (time.perf_counter() - t0) * solves
     UL, US = r["UL"], r["US"]
     pairs = pair_list(mol.natoms)
@@ -707,9 +716,11 @@ def main():
     kinds = [0] * mol.natoms
     dlu_pot = x.DLU_MOLECULAR_BLOCK if cfg.get("mb") else x.DLU_FREE_ATOM
 
+    dec = cfg.get("decoupling", 0)
+
     def build():
         x.x2c_build_dlu(ctx, g, mol.offsets, kinds, [gk], two_component=two_c, precision=prec, dlu_potential=dlu_pot,
-                        n_slices=args.slices, out=out, stream=stream)
+                        n_slices=args.slices, out=out, stream=stream, decoupling=dec)
 
     # with graphs the warm-up's second build captures the step the timed region replays
     for _ in range(args.warmup):
@@ -782,7 +793,8 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "bf16x-split",
             "data": "synthetic",
-            "config": {"workload": f"Ag{cfg['L']} {'two-component' if two_c else 'spin-free'} DLU "
+            "config": {"workload": f"Ag{cfg['L']} {'two-component' if two_c else 'spin-free'} "
+                                   f"{({0: '', 1: 'BSS-'}.get(dec, f'DKH{dec}-'))}DLU "
                                    f"({'molecular-block U per atom' if cfg.get('mb') else 'free-atom U per kind'}), "
                                    f"{cfg['basis']} primitives per atom, N={N}",
                        "pairs": len(pairs), "precision": args.precision, "inputs": "larger than L2 (no flush)",
@@ -803,7 +815,7 @@ def main():
 
         def build64():
             x.x2c_build_dlu(ctx, g, mol.offsets, kinds, [gk], two_component=two_c, precision=prec64, dlu_potential=dlu_pot,
-                            out=out, stream=stream)
+                            out=out, stream=stream, decoupling=dec)
 
         build64()
         torch.cuda.synchronize()
@@ -833,7 +845,7 @@ def main():
         # h comes back as the upper block triangle of each part (h0 symmetric, h1..h3
         # antisymmetric: the rest follows); free-atom builds run as a copy/compute pipeline
         e2e_args = dict(two_component=two_c, precision=prec, n_slices=args.slices, out=hout, stream=stream,
-                        dlu_potential=dlu_pot, h_upper_only=True)
+                        dlu_potential=dlu_pot, h_upper_only=True, decoupling=dec)
         x.x2c_build_dlu_host(ctx, pin, mol.offsets, kinds, [pink], **e2e_args)
         torch.cuda.synchronize()
         barrier()
@@ -856,7 +868,8 @@ def main():
         del pin, hout
 
     if rank == 0 and not args.no_cpu_baseline:
-        v, n, secs = cpu_oracle_rate(mol, m, kind, two_c, args.cpu_budget, solves=mol.natoms if cfg.get("mb") else 1)
+        v, n, secs = cpu_oracle_rate(mol, m, kind, two_c, args.cpu_budget, solves=mol.natoms if cfg.get("mb") else 1,
+                                     decoupling=dec)
         line["cpu_baseline"] = {"value": v, "unit": "builds/s", "cores": os.cpu_count(), "kind": "oracle",
                                 "sample": f"atomic solve + {n} seeded pair blocks ({secs:.1f} s), "
                                           f"extrapolated to {len(pairs)} pair blocks"}
