@@ -666,6 +666,9 @@ def main():
     ap.add_argument("--requests", type=int, default=0, help="serving: requests in the stream (0 = 2000)")
     ap.add_argument("--rate", type=float, default=50.0, help="serving: mean arrivals per second")
     ap.add_argument("--slots", type=int, default=4, help="serving: concurrent builds")
+    ap.add_argument("--shard", default="replicas", choices=["replicas", "pairs"],
+                    help="N > 1: every rank builds the whole molecule (replicas, weak scaling) or the ranks "
+                         "split one build's pair list (pairs, strong scaling)")
     ap.add_argument("--serving-requests", type=int, default=2000,
                     help="default workload: requests of the short serving run reported as 'serving' (0 = none)")
     args = ap.parse_args()
@@ -717,8 +720,18 @@ def main():
     dlu_pot = x.DLU_MOLECULAR_BLOCK if cfg.get("mb") else x.DLU_FREE_ATOM
 
     dec = cfg.get("decoupling", 0)
+    # --shard pairs (N > 1): the ranks split one build's pair list (x2c_dlu_partition) and each
+    # assembles its row atoms' blocks; otherwise every rank builds the whole molecule
+    shard = world > 1 and args.shard == "pairs"
+    rows = x.x2c_dlu_partition(mol.offsets, rank, world) if shard else (0, mol.natoms)
 
     def build():
+        if shard:
+            if rows[1] > rows[0]:
+                x.x2c_build_dlu_rows(ctx, g, mol.offsets, kinds, [gk], rows[0], rows[1], two_component=two_c,
+                                     precision=prec, dlu_potential=dlu_pot, n_slices=args.slices, out=out,
+                                     stream=stream, decoupling=dec)
+            return
         x.x2c_build_dlu(ctx, g, mol.offsets, kinds, [gk], two_component=two_c, precision=prec, dlu_potential=dlu_pot,
                         n_slices=args.slices, out=out, stream=stream, decoupling=dec)
 
@@ -789,17 +802,23 @@ def main():
     roof["launches"] = int(dom_launches)
     roof["avg_launch_ms"] = dom_ms / max(1, dom_launches)
 
-    line = {"metric": METRIC, "value": job_rate(world, ms_max * 1e-3), "unit": "builds/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "bf16x-split",
+    if shard:  # one build is the union of the ranks' shares: whole-job work of one build
+        tot = torch.tensor([credited], dtype=torch.float64, device=dev)
+        dist.all_reduce(tot)
+        credited = float(tot.item())
+    line = {"metric": METRIC, "value": job_rate(1 if shard else world, ms_max * 1e-3), "unit": "builds/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+            "higher_is_better": True, "scaling": "strong" if shard else "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "bf16x-split",
             "data": "synthetic",
             "config": {"workload": f"Ag{cfg['L']} {'two-component' if two_c else 'spin-free'} "
                                    f"{({0: '', 1: 'BSS-'}.get(dec, f'DKH{dec}-'))}DLU "
                                    f"({'molecular-block U per atom' if cfg.get('mb') else 'free-atom U per kind'}), "
                                    f"{cfg['basis']} primitives per atom, N={N}",
                        "pairs": len(pairs), "precision": args.precision, "inputs": "larger than L2 (no flush)",
-                       "parallelism": f"independent replicas x{world}"},
-            "fp64_equiv_tflops": world * credited / (ms_max * 1e-3) / 1e12,
+                       "parallelism": (f"pair-list partition x{world} (rows {rows[0]}..{rows[1]} on rank {rank})"
+                                       if shard else f"independent replicas x{world}")},
+            "fp64_equiv_tflops": (1 if shard else world) * credited / (ms_max * 1e-3) / 1e12,
             "credited_flops_per_build": credited,
             "gpu_launches": int(counters["kernel_launches"]) * args.steps,
             "roofline": roof, "clocks": clocks,

@@ -164,6 +164,24 @@ x2c_status x2c_build_full(x2c_ctx *ctx, const x2c_options *opt, const x2c_mats *
 x2c_status x2c_build_dlu(x2c_ctx *ctx, const x2c_options *opt, const x2c_layout *layout,
                          const x2c_mats *mol, const x2c_hout *h, void *stream);
 
+/* Pair-list partition of a DLU build over several GPUs (Sec. III.A: the pair blocks h_AB of
+ * Eqs. 42-43 are independent, and the per-kind transforms are small enough to solve on every
+ * GPU).  Rank `rank` of `world` is given the row atoms [*a_begin, *a_end): consecutive ranges
+ * over 0..n_atoms, disjoint, covering every atom, with about equal shares of the work of the
+ * upper block triangle (row atom A carries its blocks (A, B >= A), each weighted by
+ * n_A n_B (n_A + n_B)).  A range may be empty (*a_begin == *a_end) when world > n_atoms.
+ * Host-only: reads layout->atom_offset; no device work, no context. */
+x2c_status x2c_dlu_partition(const x2c_layout *layout, int32_t rank, int32_t world, int32_t *a_begin,
+                             int32_t *a_end);
+
+/* One rank's share of a partitioned DLU build: as x2c_build_dlu, but only the pair blocks
+ * (A, B >= A) with row atom A in [a_begin, a_end) are assembled (h_AB, and its mirror h_BA
+ * for B > A); every other block of h is left as it was.  The per-kind transforms are solved
+ * in full.  a_begin < a_end <= n_atoms, else X2C_ERR_ARG. */
+x2c_status x2c_build_dlu_rows(x2c_ctx *ctx, const x2c_options *opt, const x2c_layout *layout,
+                              const x2c_mats *mol, const x2c_hout *h, int32_t a_begin, int32_t a_end,
+                              void *stream);
+
 /* Batched DLU: n_mol independent molecules in one pass (one per-kind solve for the whole
  * batch and one grouped pair-assembly launch over all molecules' pair blocks).
  * layouts, mols, h: HOST arrays of n_mol entries. */

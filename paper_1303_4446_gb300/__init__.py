@@ -227,6 +227,75 @@ def x2c_build_dlu(ctx: Context, m: dict, offsets, atom_kind=None, kinds=None, tw
     return h
 
 
+def x2c_dlu_partition(offsets, rank: int, world: int):
+    """x2c_dlu_partition: the row atoms [a_begin, a_end) of rank `rank` of `world` in a
+    pair-list partitioned DLU build (host-only; no device, no context)."""
+    lay = LayoutHolder(offsets)
+    a0, a1 = ctypes.c_int32(), ctypes.c_int32()
+    abi.check(abi.load().x2c_dlu_partition(ctypes.byref(lay.s), int(rank), int(world), ctypes.byref(a0),
+                                           ctypes.byref(a1)), "x2c_dlu_partition")
+    return a0.value, a1.value
+
+
+def x2c_build_dlu_rows(ctx: Context, m: dict, offsets, atom_kind, kinds, a_begin: int, a_end: int, two_component=False,
+                       c=None, precision=PREC_FP64, dlu_potential=DLU_FREE_ATOM, so_same_atom_only=True, n_slices=0,
+                       out=None, stream=None, decoupling=DEC_X2C):
+    """x2c_build_dlu_rows: one rank's share of a partitioned DLU build (the pair blocks whose
+    row atom lies in [a_begin, a_end)); other blocks of `out` are left as they were."""
+    nc = 4 if two_component else 1
+    ms = mats_struct(m, two_component)
+    h = out if out is not None else _alloc_parts(ms.n, nc, m["S"].device)
+    lay = LayoutHolder(offsets, atom_kind, kinds, two_component)
+    o = options(two_component, c, precision, dlu_potential, so_same_atom_only, n_slices, decoupling=decoupling)
+    ho = _hout(h)
+    abi.check(ctx.lib.x2c_build_dlu_rows(ctx.handle, ctypes.byref(o), ctypes.byref(lay.s), ctypes.byref(ms),
+                                         ctypes.byref(ho), int(a_begin), int(a_end), _stream(stream)),
+              "x2c_build_dlu_rows", ctx.handle)
+    return h
+
+
+def gather_dlu_rows(h_parts: list, offsets, group=None, dst: int = 0):
+    """Collect a pair-list partitioned DLU h on rank `dst` (torch.distributed; gloo or NCCL).
+
+    Every rank passes its h parts (torch tensors, N x N, holding at least its own blocks: the
+    rows of its atom range on and right of the diagonal block, as x2c_build_dlu_rows writes
+    them).  Rank `dst` receives the other ranks' row bands, keeps the upper block triangle of
+    each and mirrors it (h0 symmetric, h1..h3 antisymmetric) into the lower one; it returns
+    the complete parts, the other ranks return None.  This is the optional gather of a
+    partitioned build: the build itself exchanges nothing."""
+    import torch
+    import torch.distributed as dist
+    rank, world = dist.get_rank(group), dist.get_world_size(group)
+    offs = np.asarray(offsets, dtype=np.int64)
+    N = int(offs[-1])
+    atom = np.repeat(np.arange(len(offs) - 1), np.diff(offs))
+    rows = [x2c_dlu_partition(offsets, r, world) for r in range(world)]
+    out = []
+    for q, hq in enumerate(h_parts):
+        bands = []
+        for r, (a0, a1) in enumerate(rows):
+            r0, r1 = int(offs[a0]), int(offs[a1])
+            if r1 == r0:
+                continue
+            if r == rank:
+                band = hq[r0:r1].contiguous()
+                if rank != dst:
+                    dist.send(band, dst=dst, group=group)
+            else:
+                if rank != dst:
+                    continue
+                band = torch.empty((r1 - r0, N), dtype=hq.dtype, device=hq.device)
+                dist.recv(band, src=r, group=group)
+            bands.append(band)
+        if rank != dst:
+            continue
+        full = torch.cat(bands, 0)
+        keep = torch.from_numpy(atom[:, None] <= atom[None, :]).to(full.device)
+        upper = torch.where(keep, full, torch.zeros_like(full))
+        out.append(torch.where(keep, full, upper.transpose(0, 1) * (1.0 if q == 0 else -1.0)))
+    return out if rank == dst else None
+
+
 def x2c_build_dlu_batched(ctx: Context, mols: list, layouts: list, two_component=False, c=None,
                           precision=PREC_FP64, dlu_potential=DLU_FREE_ATOM, so_same_atom_only=True,
                           n_slices=0, local_approx=LOCAL_DLU, outs=None, stream=None, decoupling=DEC_X2C):

@@ -1125,6 +1125,44 @@ x2c_status x2c_build_dlu(x2c_ctx *ctx, const x2c_options *opt, const x2c_layout 
   return dlu_build(ctx, opt, 1, layout, mol, h, nullptr, static_cast<cudaStream_t>(stream), nullptr);
 }
 
+x2c_status x2c_build_dlu_rows(x2c_ctx *ctx, const x2c_options *opt, const x2c_layout *layout, const x2c_mats *mol,
+                              const x2c_hout *h, int32_t a_begin, int32_t a_end, void *stream) {
+  if (!layout || a_begin < 0 || a_end <= a_begin || a_end > layout->n_atoms) return X2C_ERR_ARG;
+  return dlu_build(ctx, opt, 1, layout, mol, h, nullptr, static_cast<cudaStream_t>(stream), nullptr, a_begin, a_end);
+}
+
+x2c_status x2c_dlu_partition(const x2c_layout *layout, int32_t rank, int32_t world, int32_t *a_begin,
+                             int32_t *a_end) {
+  if (!layout || !layout->atom_offset || layout->n_atoms < 1 || world < 1 || rank < 0 || rank >= world || !a_begin ||
+      !a_end)
+    return X2C_ERR_ARG;
+  const int L = layout->n_atoms;
+  std::vector<double> n(L);
+  for (int a = 0; a < L; ++a) {
+    n[a] = layout->atom_offset[a + 1] - layout->atom_offset[a];
+    if (n[a] < 1) return X2C_ERR_ARG;
+  }
+  // work of row atom A: its pair blocks (A, B >= A), each about n_A n_B (n_A + n_B) products
+  std::vector<double> cum(L + 1, 0.0), tail_n(L + 1, 0.0), tail_n2(L + 1, 0.0);
+  for (int b = L - 1; b >= 0; --b) {
+    tail_n[b] = tail_n[b + 1] + n[b];
+    tail_n2[b] = tail_n2[b + 1] + n[b] * n[b];
+  }
+  for (int a = 0; a < L; ++a) cum[a + 1] = cum[a] + n[a] * (n[a] * tail_n[a] + tail_n2[a]);
+  // rank r takes the rows whose cumulative work starts in [r W / world, (r + 1) W / world)
+  auto cut = [&](int r) {
+    if (r <= 0) return 0;
+    if (r >= world) return L;
+    const double target = cum[L] * r / world;
+    int a = 0;
+    while (a < L && cum[a] < target) ++a;
+    return a;
+  };
+  *a_begin = cut(rank);
+  *a_end = cut(rank + 1);
+  return X2C_OK;
+}
+
 x2c_status x2c_build_dlu_batched(x2c_ctx *ctx, const x2c_options *opt, int32_t n_mol,
                                  const x2c_layout *layouts, const x2c_mats *mols,
                                  const x2c_hout *h, void *stream) {
