@@ -42,27 +42,31 @@ __device__ __forceinline__ void fw_factors(double t, double c, double &E0, doubl
 
 // Eigen-decomposition of symmetric matrices (one CTA per matrix, cyclic Jacobi with the
 // round-robin ordering: m/2 disjoint rotations per step, m - 1 steps per sweep, m = n rounded
-// up to even).  A rotation is skipped when |a_pq| <= 1e-17 sqrt(a_pp a_qq) (relative
-// criterion: small eigenvalues keep their relative accuracy); a sweep without rotations ends
-// the iteration (no convergence within kJacobiSweeps is flagged).  Output: eigenvalues
-// evals[b n + i] and eigenvectors as the ROWS of QT (QT[b][i][:] belongs to evals[b n + i]).
+// up to even; in step s, position k pairs with position m - 1 - k, position 0 holds index 0
+// and position i >= 1 holds 1 + (i - 1 + s) mod (m - 1)).  A rotation is skipped when
+// |a_pq| <= 1e-17 sqrt(a_pp a_qq) (relative criterion: small eigenvalues keep their relative
+// accuracy); a sweep without rotations ends the iteration (no convergence within
+// kJacobiSweeps is flagged).  The matrix lives in shared memory, and so do the eigenvectors
+// when both fit (n <= kJacobiSmemV), else they are updated in global memory.  Output:
+// eigenvalues evals[b n + i] and eigenvectors as the ROWS of QT (QT[b][i][:] belongs to
+// evals[b n + i]).
+constexpr int kJacobiSmemV = 110;  // 2 n^2 doubles <= 194 KB
 __global__ void __launch_bounds__(256) jacobi_kernel(const double *Ain, int n, int64_t stride, double *evals,
                                                      double *QT, int *status) {
   extern __shared__ double A[];
-  __shared__ int ring[kMaxJacobiN];
   __shared__ int pp[kMaxJacobiN / 2], qq[kMaxJacobiN / 2];
   __shared__ double cs[kMaxJacobiN / 2], sn[kMaxJacobiN / 2];
   __shared__ int rotated;
   const int b = blockIdx.x;
   const double *a0 = Ain + b * stride;
-  double *qt = QT + b * stride;
   const int nn = n * n;
+  const bool vsh = n <= kJacobiSmemV;
+  double *qt = vsh ? A + nn : QT + b * stride;
   for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
     A[idx] = a0[idx];
     qt[idx] = (idx / n == idx % n) ? 1.0 : 0.0;
   }
   const int m = n + (n & 1), half = m / 2;
-  for (int i = threadIdx.x; i < m; i += blockDim.x) ring[i] = i;
   __syncthreads();
   bool converged = n < 2;
   for (int sweep = 0; sweep < kJacobiSweeps && !converged; ++sweep) {
@@ -70,7 +74,9 @@ __global__ void __launch_bounds__(256) jacobi_kernel(const double *Ain, int n, i
     __syncthreads();
     for (int step = 0; step < m - 1; ++step) {
       for (int k = threadIdx.x; k < half; k += blockDim.x) {
-        int p = ring[k], q = ring[m - 1 - k];
+        const int i1 = k, i2 = m - 1 - k;
+        int p = i1 == 0 ? 0 : 1 + (i1 - 1 + step) % (m - 1);
+        int q = 1 + (i2 - 1 + step) % (m - 1);
         if (p > q) {
           const int t = p;
           p = q;
@@ -96,9 +102,9 @@ __global__ void __launch_bounds__(256) jacobi_kernel(const double *Ain, int n, i
       // rows p, q of A (J^T A) and of QT (V J: the eigenvectors are QT's rows)
       for (int idx = threadIdx.x; idx < half * n; idx += blockDim.x) {
         const int k = idx / n, j = idx - k * n;
-        const int p = pp[k], q = qq[k];
         const double s = sn[k];
-        if (q >= n || s == 0.0) continue;
+        if (s == 0.0) continue;
+        const int p = pp[k], q = qq[k];
         const double c = cs[k];
         const double ap = A[p * n + j], aq = A[q * n + j];
         A[p * n + j] = c * ap - s * aq;
@@ -111,19 +117,13 @@ __global__ void __launch_bounds__(256) jacobi_kernel(const double *Ain, int n, i
       // columns p, q of A (A J)
       for (int idx = threadIdx.x; idx < half * n; idx += blockDim.x) {
         const int k = idx / n, i = idx - k * n;
-        const int p = pp[k], q = qq[k];
         const double s = sn[k];
-        if (q >= n || s == 0.0) continue;
+        if (s == 0.0) continue;
+        const int p = pp[k], q = qq[k];
         const double c = cs[k];
         const double ap = A[i * n + p], aq = A[i * n + q];
         A[i * n + p] = c * ap - s * aq;
         A[i * n + q] = s * ap + c * aq;
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) {  // next round-robin pairing: ring[0] fixed, the rest rotates
-        const int last = ring[m - 1];
-        for (int i = m - 1; i > 1; --i) ring[i] = ring[i - 1];
-        ring[1] = last;
       }
       __syncthreads();
     }
@@ -132,6 +132,8 @@ __global__ void __launch_bounds__(256) jacobi_kernel(const double *Ain, int n, i
   }
   if (!converged && threadIdx.x == 0) flag_error(status, X2C_DEV_NOCONV);
   for (int i = threadIdx.x; i < n; i += blockDim.x) evals[(int64_t)b * n + i] = A[i * n + i];
+  if (vsh)
+    for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) QT[b * stride + idx] = qt[idx];
 }
 
 // The right operand of a quaternion product as a stack of parts (or of the parts of its
@@ -389,9 +391,10 @@ x2c_status kinetic_basis(x2c_ctx *ctx, cudaStream_t st, int nb, int n, int nc, c
                    StoreAxpby{kb.tmp, nullptr, n, n2, 1.0, 0.0})));
   X2C_TRY((gemm_sq(ctx, st, nb, n, Mat<false>{kb.tmp, n, n2, 1.0}, Mat<true>{kb.inv, n, 2 * n2, 1.0},
                    StoreAxpby{kb.Vt, nullptr, n, n2, 1.0, 0.0})));
-  X2C_TRY_CUDA(ctx, cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const size_t jsmem = (n <= kJacobiSmemV ? 2 : 1) * smem;
+  X2C_TRY_CUDA(ctx, cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jsmem));
   tbegin(ctx, st);
-  jacobi_kernel<<<nb, 256, smem, st>>>(kb.Vt, n, n2, kb.evals, kb.QT, status);
+  jacobi_kernel<<<nb, 256, jsmem, st>>>(kb.Vt, n, n2, kb.evals, kb.QT, status);
   X2C_TRY(launched(ctx, "jacobi_kernel", st));
   // K = L^-T Q,  K^-1 = Q^T L^T
   X2C_TRY((gemm_sq(ctx, st, nb, n, Mat<true>{kb.inv, n, 2 * n2, 1.0}, Mat<true>{kb.QT, n, n2, 1.0},
