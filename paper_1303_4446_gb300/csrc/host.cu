@@ -5,6 +5,7 @@
 // cross to the device and the h rows of chunk k-1 come back; the per-kind decoupling solve
 // runs while the first chunk is still copying.  Other modes copy everything in, build, and
 // copy everything out.
+#include <cstdlib>
 #include <cstring>
 
 #include "common.cuh"
@@ -72,7 +73,15 @@ struct Events {
   }
 };
 
-constexpr int kPipelineChunks = 8;
+// Row-atom chunks of the pipeline (X2C_HOST_CHUNKS overrides, 1..64).
+int pipeline_chunks() {
+  static const int n = [] {
+    const char *e = std::getenv("X2C_HOST_CHUNKS");
+    const int v = e ? std::atoi(e) : 0;
+    return (v >= 1 && v <= 64) ? v : 8;
+  }();
+  return n;
+}
 
 }  // namespace
 
@@ -220,7 +229,7 @@ extern "C" x2c_status x2c_build_dlu_host(x2c_ctx *ctx, const x2c_options *opt, c
     next += 2 * nc * n2;
     ku_out[k] = u;
   }
-  const std::vector<int> cut = row_chunks(lay, N, kPipelineChunks);
+  const std::vector<int> cut = row_chunks(lay, N, pipeline_chunks());
   const int nch = (int)cut.size() - 1;
   Events ev;
   X2C_TRY(ev.make(ctx, 2 * (size_t)nch + 2));
