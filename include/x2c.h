@@ -98,11 +98,13 @@ typedef struct {
                                 only those blocks and skips the rest (two-component only) */
   int32_t n_slices;          /* split precision: BF16 slices per operand, 0 = default (5) */
   int32_t local_approx;      /* x2c_local_approx of the DLU calls (ignored by full X2C) */
-  int32_t h_upper_only;      /* x2c_build_dlu_host only: 1 = write each h part back on its upper
-                                block triangle only (blocks A <= B; the other blocks of the host
-                                buffers are not written).  h0 is symmetric and h1..h3 are
-                                antisymmetric, so the lower blocks follow from the upper ones;
-                                this halves the device-to-host copy.  Other calls: must be 0 */
+  int32_t h_upper_only;      /* x2c_build_dlu_host only: 1 = copy each h part back on its upper
+                                block triangle (blocks A <= B) instead of whole: h0 is symmetric
+                                and h1..h3 are antisymmetric, so the lower blocks follow from
+                                the upper ones; this halves the device-to-host copy.  Blocks
+                                below the diagonal are not written, except that some near the
+                                diagonal (within the row bands the call copies at once) may
+                                receive their values.  Other calls: must be 0 */
   int32_t decoupling;        /* x2c_decoupling: the decoupling transformation (default 0 = X2C) */
 } x2c_options;
 

@@ -43,6 +43,18 @@ x2c_status copy_upper_blocks(x2c_ctx *ctx, double *dst, const double *src, int64
   return copy_upper_rows(ctx, dst, src, N, lay, 0, lay->n_atoms, cudaMemcpyHostToDevice, st);
 }
 
+// The row band of atoms [a0, a1) from the band's first column to N - 1, as ONE 2D copy: the
+// upper block triangle of those rows plus the blocks below the diagonal inside the band
+// (a few per cent more bytes, but one copy call instead of one per atom: the host's copy
+// calls, not the link, bound a pipeline of thousands of per-atom copies).
+x2c_status copy_band(x2c_ctx *ctx, double *dst, const double *src, int64_t N, const x2c_layout *lay, int a0, int a1,
+                     cudaMemcpyKind kind, cudaStream_t st) {
+  const int64_t r0 = lay->atom_offset[a0], r1 = lay->atom_offset[a1];
+  X2C_TRY_CUDA(ctx, cudaMemcpy2DAsync(dst + r0 * N + r0, N * sizeof(double), src + r0 * N + r0, N * sizeof(double),
+                                      (N - r0) * sizeof(double), r1 - r0, kind, st));
+  return X2C_OK;
+}
+
 // Row-atom chunks of about equal copy volume: atom a carries n_a (N - offset_a) elements of
 // the upper block triangle.
 std::vector<int> row_chunks(const x2c_layout *lay, int64_t N, int chunks) {
@@ -243,12 +255,11 @@ extern "C" x2c_status x2c_build_dlu_host(x2c_ctx *ctx, const x2c_options *opt, c
   for (int c = 0; c < nch; ++c) {
     const int a0 = cut[c], a1 = cut[c + 1];
     cudaStream_t in = cs[1 + (c & 1)];
-    X2C_TRY(copy_upper_rows(ctx, dT, mol->T, N, lay, a0, a1, cudaMemcpyHostToDevice, in));
-    X2C_TRY(copy_upper_rows(ctx, dV, mol->V, N, lay, a0, a1, cudaMemcpyHostToDevice, in));
-    X2C_TRY(copy_upper_rows(ctx, dW0, mol->W0, N, lay, a0, a1, cudaMemcpyHostToDevice, in));
+    X2C_TRY(copy_band(ctx, dT, mol->T, N, lay, a0, a1, cudaMemcpyHostToDevice, in));
+    X2C_TRY(copy_band(ctx, dV, mol->V, N, lay, a0, a1, cudaMemcpyHostToDevice, in));
+    X2C_TRY(copy_band(ctx, dW0, mol->W0, N, lay, a0, a1, cudaMemcpyHostToDevice, in));
     if (nc == 4 && !so_blocks)
-      for (int k = 0; k < 3; ++k)
-        X2C_TRY(copy_upper_rows(ctx, dW[k], hw[k], N, lay, a0, a1, cudaMemcpyHostToDevice, in));
+      for (int k = 0; k < 3; ++k) X2C_TRY(copy_band(ctx, dW[k], hw[k], N, lay, a0, a1, cudaMemcpyHostToDevice, in));
     X2C_TRY_CUDA(ctx, cudaEventRecord(ev.ev[2 * c], in));
     X2C_TRY_CUDA(ctx, cudaStreamWaitEvent(st, ev.ev[2 * c], 0));
     X2C_TRY(x2c::dlu_build(ctx, &o, 1, &dl, &dm, &dho, &kt, st, nullptr, a0, a1));
@@ -260,7 +271,7 @@ extern "C" x2c_status x2c_build_dlu_host(x2c_ctx *ctx, const x2c_options *opt, c
     const int64_t r0 = lay->atom_offset[a0], r1 = lay->atom_offset[a1];
     for (int q = 0; q < nc; ++q) {
       if (upper_only)
-        X2C_TRY(copy_upper_rows(ctx, h->h[q], dh[q], N, lay, a0, a1, cudaMemcpyDeviceToHost, out));
+        X2C_TRY(copy_band(ctx, h->h[q], dh[q], N, lay, a0, a1, cudaMemcpyDeviceToHost, out));
       else
         X2C_TRY_CUDA(ctx, cudaMemcpyAsync(h->h[q] + r0 * N, dh[q] + r0 * N, (r1 - r0) * N * sizeof(double),
                                           cudaMemcpyDeviceToHost, out));
