@@ -284,7 +284,11 @@ x2c_status x2c_atomic_transforms_noalloc(const x2c_options *opt, int32_t n_probl
  * pointer (mol, kinds, h) is a host pointer.  Only what the build reads crosses to the
  * device: the upper block triangle (blocks A <= B) of T, V and W0 (DLH: T and V whole, the
  * same-atom blocks of W0), the same-atom blocks of S (molecular-block mode) and of Wx, Wy,
- * Wz (so_same_atom_only = 1; else their upper block triangle); h comes back whole. */
+ * Wz (so_same_atom_only = 1; else their upper block triangle); h comes back whole, or on its
+ * upper block triangle (h_upper_only).  Free-atom DLU runs as a pipeline over row-atom chunks
+ * (chunk k+1 copies in and chunk k-1 copies out while chunk k is assembled); a chunk's rows
+ * cross as one band from its first column on, so a few blocks just below the diagonal are
+ * copied too (the build does not read them). */
 x2c_status x2c_build_dlu_host(x2c_ctx *ctx, const x2c_options *opt, const x2c_layout *layout,
                               const x2c_mats *mol, const x2c_hout *h, void *stream);
 
