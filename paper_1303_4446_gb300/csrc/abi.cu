@@ -67,6 +67,50 @@ size_t workspace_after_growth(const x2c_ctx *ctx, size_t bytes) {
   return bytes > ctx->ws_bytes ? bytes + bytes / 8 : ctx->ws_bytes;
 }
 
+// Copies and fills of the build path run as kernels, not on the copy engines: a host-buffer
+// build keeps the copy engines busy with its bulk transfers, and a small copy queued behind
+// them would hold up the build's kernels until those transfers finish.  Sources in pinned
+// host memory are read through their device mapping.
+__global__ void copy_bytes_kernel(unsigned char *dst, const unsigned char *src, size_t bytes) {
+  const size_t tid = blockIdx.x * (size_t)blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
+  if ((((uintptr_t)dst | (uintptr_t)src) & 15) == 0) {
+    const size_t words = bytes / 16;
+    for (size_t i = tid; i < words; i += stride)
+      reinterpret_cast<uint4 *>(dst)[i] = reinterpret_cast<const uint4 *>(src)[i];
+    for (size_t i = words * 16 + tid; i < bytes; i += stride) dst[i] = src[i];
+  } else {
+    for (size_t i = tid; i < bytes; i += stride) dst[i] = src[i];
+  }
+}
+__global__ void fill_bytes_kernel(unsigned char *dst, unsigned char v, size_t bytes) {
+  const size_t tid = blockIdx.x * (size_t)blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = tid; i < bytes; i += stride) dst[i] = v;
+}
+int copy_grid(size_t bytes) { return (int)std::min<size_t>(std::max<size_t>(1, (bytes / 16 + 255) / 256), 152 * 4); }
+
+x2c_status device_copy(x2c_ctx *ctx, cudaStream_t st, void *dst, const void *src, size_t bytes) {
+  if (bytes == 0) return X2C_OK;
+  tbegin(ctx, st);
+  copy_bytes_kernel<<<copy_grid(bytes), 256, 0, st>>>(static_cast<unsigned char *>(dst),
+                                                      static_cast<const unsigned char *>(src), bytes);
+  return launched(ctx, "copy_kernel", st);
+}
+
+x2c_status device_fill(x2c_ctx *ctx, cudaStream_t st, void *dst, int value, size_t bytes) {
+  if (bytes == 0) return X2C_OK;
+  tbegin(ctx, st);
+  fill_bytes_kernel<<<copy_grid(bytes), 256, 0, st>>>(static_cast<unsigned char *>(dst), (unsigned char)value, bytes);
+  return launched(ctx, "copy_kernel", st);
+}
+
+// Device address of a pinned host allocation (the same pointer under unified addressing).
+x2c_status mapped(x2c_ctx *ctx, const void *host, const void **dev) {
+  void *d = nullptr;
+  X2C_TRY_CUDA(ctx, cudaHostGetDevicePointer(&d, const_cast<void *>(host), 0));
+  *dev = d;
+  return X2C_OK;
+}
+
 x2c_status upload(x2c_ctx *ctx, cudaStream_t st, void *dst, const void *src, size_t bytes) {
   if (bytes == 0) return X2C_OK;
   const size_t need = (bytes + 255) & ~static_cast<size_t>(255);
@@ -89,8 +133,9 @@ x2c_status upload(x2c_ctx *ctx, cudaStream_t st, void *dst, const void *src, siz
     char *h = ctx->cap_pinned.back() + ctx->cap_off;
     ctx->cap_off += need;
     std::memcpy(h, src, bytes);
-    X2C_TRY_CUDA(ctx, cudaMemcpyAsync(dst, h, bytes, cudaMemcpyHostToDevice, st));
-    return X2C_OK;
+    const void *hd = nullptr;
+    X2C_TRY(mapped(ctx, h, &hd));
+    return device_copy(ctx, st, dst, hd, bytes);
   }
   auto retire = [&](const x2c_ctx::Staged &f) -> x2c_status {
     X2C_TRY_CUDA(ctx, cudaEventSynchronize(f.done));
@@ -131,7 +176,9 @@ x2c_status upload(x2c_ctx *ctx, cudaStream_t st, void *dst, const void *src, siz
     ctx->ring_inflight.erase(ctx->ring_inflight.begin());
   }
   std::memcpy(ctx->ring + start, src, bytes);
-  X2C_TRY_CUDA(ctx, cudaMemcpyAsync(dst, ctx->ring + start, bytes, cudaMemcpyHostToDevice, st));
+  const void *hd = nullptr;
+  X2C_TRY(mapped(ctx, ctx->ring + start, &hd));
+  X2C_TRY(device_copy(ctx, st, dst, hd, bytes));
   cudaEvent_t ev;
   if (!ctx->ring_events.empty()) {
     ev = ctx->ring_events.back();
@@ -811,8 +858,8 @@ x2c_status full_build(x2c_ctx *ctx, const x2c_options *opt, const x2c_mats *mol,
     if (dry || !U) return X2C_OK;
     const size_t n2 = (size_t)mol->n * mol->n;
     for (int q = 0; q < nc; ++q) {
-      if (U->UL[q]) X2C_TRY_CUDA(ctx, cudaMemcpyAsync(U->UL[q], ULp[0] + q * n2, n2 * sizeof(double), cudaMemcpyDeviceToDevice, s));
-      if (U->US[q]) X2C_TRY_CUDA(ctx, cudaMemcpyAsync(U->US[q], USp[0] + q * n2, n2 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      if (U->UL[q]) X2C_TRY(device_copy(ctx, s, U->UL[q], ULp[0] + q * n2, n2 * sizeof(double)));
+      if (U->US[q]) X2C_TRY(device_copy(ctx, s, U->US[q], USp[0] + q * n2, n2 * sizeof(double)));
     }
     return X2C_OK;
   };
@@ -861,8 +908,8 @@ x2c_status transforms_build(x2c_ctx *ctx, const x2c_options *opt, int n_problems
     for (int i = 0; i < n_problems; ++i) {
       const size_t n2 = (size_t)inputs[i].n * inputs[i].n;
       for (int q = 0; q < plan.nc; ++q) {
-        X2C_TRY_CUDA(ctx, cudaMemcpyAsync(U[i].UL[q], ULp[i] + q * n2, n2 * sizeof(double), cudaMemcpyDeviceToDevice, s));
-        X2C_TRY_CUDA(ctx, cudaMemcpyAsync(U[i].US[q], USp[i] + q * n2, n2 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        X2C_TRY(device_copy(ctx, s, U[i].UL[q], ULp[i] + q * n2, n2 * sizeof(double)));
+        X2C_TRY(device_copy(ctx, s, U[i].US[q], USp[i] + q * n2, n2 * sizeof(double)));
       }
     }
     return X2C_OK;
@@ -904,10 +951,8 @@ x2c_status with_transforms(x2c_ctx *ctx, const x2c_options *opt, const x2c_layou
     const size_t n2 = (size_t)layout->kinds[k].n * layout->kinds[k].n;
     double *dst = stage + off[k];
     for (int q = 0; q < nc; ++q) {
-      X2C_TRY_CUDA(ctx, cudaMemcpyAsync(dst + q * n2, kind_U[k].UL[q], n2 * sizeof(double),
-                                        cudaMemcpyDeviceToDevice, st));
-      X2C_TRY_CUDA(ctx, cudaMemcpyAsync(dst + (nc + q) * n2, kind_U[k].US[q], n2 * sizeof(double),
-                                        cudaMemcpyDeviceToDevice, st));
+      X2C_TRY(device_copy(ctx, st, dst + q * n2, kind_U[k].UL[q], n2 * sizeof(double)));
+      X2C_TRY(device_copy(ctx, st, dst + (nc + q) * n2, kind_U[k].US[q], n2 * sizeof(double)));
     }
     ul[k] = dst;
     us[k] = dst + nc * n2;
@@ -915,7 +960,7 @@ x2c_status with_transforms(x2c_ctx *ctx, const x2c_options *opt, const x2c_layou
   KindTransforms ku{ul.data(), us.data()};
   if (!P) return dlu_build(ctx, opt, 1, layout, mol, h, &ku, st, nullptr);
   double *zero = stage + off[nk];
-  X2C_TRY_CUDA(ctx, cudaMemsetAsync(zero, 0, zero_doubles * sizeof(double), st));
+  X2C_TRY(device_fill(ctx, st, zero, 0, zero_doubles * sizeof(double)));
   x2c_mats pm{};
   pm.n = P->n;
   pm.S = P->LL;  // not read: the transforms are given

@@ -196,6 +196,10 @@ x2c_status ensure_workspace(x2c_ctx *ctx, size_t bytes, Arena *out, cudaStream_t
 // ring, so that the call returns at once: cudaMemcpyAsync from pageable memory would first
 // wait for all work already queued on the stream.  The host data may be reused on return.
 x2c_status upload(x2c_ctx *ctx, cudaStream_t st, void *dst, const void *src, size_t bytes);
+// Device-side copy and byte fill (kernels, so that they never wait behind bulk transfers on
+// the copy engines); src may be pinned host memory's device mapping.
+x2c_status device_copy(x2c_ctx *ctx, cudaStream_t st, void *dst, const void *src, size_t bytes);
+x2c_status device_fill(x2c_ctx *ctx, cudaStream_t st, void *dst, int value, size_t bytes);
 
 // Destroy the context's captured graphs (waits for the device first).
 void drop_graphs(x2c_ctx *ctx);

@@ -529,7 +529,7 @@ x2c_status chol_inv_blocked(x2c_ctx *ctx, cudaStream_t st, double *A, int64_t ld
 // positive- and negative-energy states); failures are latched in the status word.
 x2c_status check(x2c_ctx *ctx, cudaStream_t st, int nb, int d, int nc, const double *Y, const double *Z,
                  double tol, unsigned long long *slot, double *trace, int *status) {
-  X2C_TRY_CUDA(ctx, cudaMemsetAsync(slot, 0, sizeof(unsigned long long) * nb, st));
+  X2C_TRY(device_fill(ctx, st, slot, 0, sizeof(unsigned long long) * nb));
   tbegin(ctx, st);
   deviation_kernel<<<aux_grid(nb, (int64_t)nc * d * d), 256, 0, st>>>(d, nc, Y, slot);
   X2C_TRY(launched(ctx, "check_kernel", st));
@@ -556,7 +556,7 @@ x2c_status sign_of_hp(x2c_ctx *ctx, cudaStream_t st, int nb, int n, int nc, doub
   tbegin(ctx, st);
   assemble_hp_kernel<<<aux_grid(nb * nc, d2), 256, 0, st>>>(n, nc, c, Vt, LSm, Wt, Z);
   X2C_TRY(launched(ctx, "assemble_hp_kernel", st));
-  X2C_TRY_CUDA(ctx, cudaMemsetAsync(slot, 0, sizeof(unsigned long long) * nb, st));
+  X2C_TRY(device_fill(ctx, st, slot, 0, sizeof(unsigned long long) * nb));
   tbegin(ctx, st);
   gershgorin_kernel<<<aux_grid(nb, (int64_t)d * 32 * nc), 256, 0, st>>>(d, nc, Z, slot);
   X2C_TRY(launched(ctx, "gershgorin_kernel", st));
@@ -601,7 +601,7 @@ x2c_status coupled_sqrt(x2c_ctx *ctx, cudaStream_t st, int nb, int n, int nc, co
                         int *status) {
   const int64_t n2 = (int64_t)n * n;
   const bool herm_n = n >= kHermMin;
-  X2C_TRY_CUDA(ctx, cudaMemcpyAsync(Yk, G, sizeof(double) * nb * nc * n2, cudaMemcpyDeviceToDevice, st));
+  X2C_TRY(device_copy(ctx, st, Yk, G, sizeof(double) * nb * nc * n2));
   tbegin(ctx, st);
   identity_kernel<<<aux_grid(nb, nc * n2), 256, 0, st>>>(n, nc, Zk);
   X2C_TRY(launched(ctx, "identity_kernel", st));
@@ -671,8 +671,8 @@ x2c_status solve_transforms(x2c_ctx *ctx, cudaStream_t st, double c, int nb, int
     // large matrices: blocked factorisation of a dense copy, one matrix at a time
     double *Acopy = ar.take(n2), *ctmp = ar.take(n2 / 4 + 32 * n);
     if (!ctmp) return X2C_ERR_NOMEM;
-    X2C_TRY_CUDA(ctx, cudaMemsetAsync(fac, 0, sizeof(double) * 2 * nb * n2, st));
-    X2C_TRY_CUDA(ctx, cudaMemsetAsync(inv, 0, sizeof(double) * 2 * nb * n2, st));
+    X2C_TRY(device_fill(ctx, st, fac, 0, sizeof(double) * 2 * nb * n2));
+    X2C_TRY(device_fill(ctx, st, inv, 0, sizeof(double) * 2 * nb * n2));
     for (int b = 0; b < nb; ++b)
       for (int which = 0; which < 2; ++which) {
         tbegin(ctx, st);

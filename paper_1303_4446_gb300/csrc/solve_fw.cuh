@@ -548,15 +548,15 @@ x2c_status solve_transforms_fw(x2c_ctx *ctx, cudaStream_t st, double c, int nb, 
                     slots + dkh::Plan::kSlotE1p * q, slots + dkh::Plan::kSlotO1 * q));
   X2C_TRY(run_dkh_ops(ctx, st, nb, n, nc, c, kb.evals, plan.ops(), slots, 0));
   X2C_TRY(fw_launch(ctx, st, "identity_kernel", identity_kernel, aux_grid(nb, nc * n2), n, nc, top));
-  X2C_TRY_CUDA(ctx, cudaMemsetAsync(bot, 0, sizeof(double) * q, st));
+  X2C_TRY(device_fill(ctx, st, bot, 0, sizeof(double) * q));
   const int64_t per = (int64_t)nc * n2;
   for (auto it = gens.rbegin(); it != gens.rend(); ++it) {
     const int k = it->first;
     const double *W = slots + (int64_t)it->second * q;
     // acc = Y; term = Y; for i = 1 .. order/k: term <- -(W term)/i, acc += term, where
     // W [a; b] = [W b; -W+ a]
-    X2C_TRY_CUDA(ctx, cudaMemcpyAsync(acc_a, top, sizeof(double) * q, cudaMemcpyDeviceToDevice, st));
-    X2C_TRY_CUDA(ctx, cudaMemcpyAsync(acc_b, bot, sizeof(double) * q, cudaMemcpyDeviceToDevice, st));
+    X2C_TRY(device_copy(ctx, st, acc_a, top, sizeof(double) * q));
+    X2C_TRY(device_copy(ctx, st, acc_b, bot, sizeof(double) * q));
     const double *pa = top, *pb = bot;
     for (int i = 1; i <= order / k; ++i) {
       X2C_TRY(quat_product_op(ctx, st, nb, n, nc, false, false, W, pb, na, -1.0 / i, 0.0, "dkh_gemm"));
@@ -614,7 +614,7 @@ x2c_status dkh_hamiltonian(x2c_ctx *ctx, cudaStream_t st, double c, int n, int n
                     slots + dkh::Plan::kSlotE1p * q, slots + dkh::Plan::kSlotO1 * q));
   X2C_TRY(run_dkh_ops(ctx, st, 1, n, nc, c, kb.evals, plan.ops(), slots, 0));
   // H = E0 - c^2 + sum_l E_l (upper blocks)
-  X2C_TRY_CUDA(ctx, cudaMemsetAsync(H, 0, sizeof(double) * q, st));
+  X2C_TRY(device_fill(ctx, st, H, 0, sizeof(double) * q));
   for (size_t t0 = 0; t0 < terms.size(); t0 += kLinTerms) {
     LinTerms L{};
     L.count = (int)std::min<size_t>(kLinTerms, terms.size() - t0);
@@ -632,6 +632,6 @@ x2c_status dkh_hamiltonian(x2c_ctx *ctx, cudaStream_t st, double c, int n, int n
   X2C_TRY((gemm_sq(ctx, st, nc, n, Mat<false>{kb.tmp, n, n2, 1.0}, MatDiv<false>{kb.Kinv, n, n2, nc, 1.0},
                    StoreAxpby{out, nullptr, n, n2, 1.0, 0.0})));
   for (int p = 0; p < nc; ++p)
-    X2C_TRY_CUDA(ctx, cudaMemcpyAsync(h[p], out + p * n2, sizeof(double) * n2, cudaMemcpyDeviceToDevice, st));
+    X2C_TRY(device_copy(ctx, st, h[p], out + p * n2, sizeof(double) * n2));
   return X2C_OK;
 }

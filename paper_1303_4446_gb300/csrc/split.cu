@@ -1077,7 +1077,7 @@ struct Runner {
         X2C_TRY(upload(ctx, st, dp, cls.data() + c0, np * sizeof(PairDesc)));
         if (rows2p > rows2) {  // the stage-2 tail rows are never written by the fused epilogue
           const size_t tail0 = (size_t)(rows2p - kTileM) * KP2 * S * 2;
-          X2C_TRY_CUDA(ctx, cudaMemsetAsync(reinterpret_cast<char *>(A2) + tail0, 0, (size_t)kTileM * KP2 * S * 2, st));
+          X2C_TRY(device_fill(ctx, st, reinterpret_cast<char *>(A2) + tail0, 0, (size_t)kTileM * KP2 * S * 2));
         }
         ClassInfo ci{dp, d_mols, nA, nB, nc, inv4c2};
         X2C_TRY(slice_mid(ctx, st, ci, np, TRA, KP1, k1p, A1, e1));
@@ -1137,7 +1137,7 @@ struct Runner {
           X2C_TRY(upload(ctx, st, ds, so.data() + s0, ns * sizeof(PairDesc)));
           if (srows2p > srows2) {
             const size_t tail0 = (size_t)(srows2p - kTileM) * KP2 * S * 2;
-            X2C_TRY_CUDA(ctx, cudaMemsetAsync(reinterpret_cast<char *>(A2) + tail0, 0, (size_t)kTileM * KP2 * S * 2, st));
+            X2C_TRY(device_fill(ctx, st, reinterpret_cast<char *>(A2) + tail0, 0, (size_t)kTileM * KP2 * S * 2));
           }
           ClassInfo cs{ds, d_mols, nA, nB, nc, inv4c2};
           for (int k = 1; k <= 3; ++k) {
