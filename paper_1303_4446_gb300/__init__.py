@@ -377,8 +377,9 @@ def x2c_build_dlu_host(ctx: Context, m: dict, offsets, atom_kind=None, kinds=Non
                        n_slices=0, local_approx=LOCAL_DLU, out=None, stream=None, h_upper_only=False,
                        decoupling=DEC_X2C):
     """DLU build from HOST arrays (numpy float64 or CPU torch tensors, pinned or not);
-    h parts are written into `out` (host arrays) or new numpy arrays.  h_upper_only: only the
-    upper block triangle of each part is written (the rest of `out` is left as it was)."""
+    h parts are written into `out` (host arrays) or new numpy arrays.  h_upper_only: the
+    upper block triangle of each part is written (blocks below the diagonal keep what `out`
+    held, except a few near the diagonal, which receive their values)."""
     nc = 4 if two_component else 1
     n = m["S"].shape[0]
 

@@ -26,6 +26,28 @@ x2c_status copy_diag_blocks(x2c_ctx *ctx, double *dst, const double *src, int64_
   return X2C_OK;
 }
 
+// The diagonal blocks of an N x N matrix in pinned host memory (src: its device mapping),
+// gathered by one kernel (CTA a copies atom a's block) instead of one copy per block.
+__global__ void gather_diag_kernel(const double *src, double *dst, int64_t N, const int32_t *off) {
+  const int a = blockIdx.x;
+  const int64_t o = off[a], n = off[a + 1] - o;
+  for (int64_t idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int64_t i = idx / n, j = idx - i * n;
+    dst[(o + i) * N + o + j] = src[(o + i) * N + o + j];
+  }
+}
+
+// Device mapping of a host pointer the GPU can read directly (pinned or registered), else NULL.
+const double *device_readable(const double *p) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type == cudaMemoryTypeHost && a.devicePointer) return static_cast<const double *>(a.devicePointer);
+  return nullptr;
+}
+
 // Copy the upper block triangle of rows of atoms [a0, a1) (rows of atom a, columns from the
 // atom's first function to N - 1) between an N x N host and device matrix.
 x2c_status copy_upper_rows(x2c_ctx *ctx, double *dst, const double *src, int64_t N, const x2c_layout *lay, int a0,
@@ -134,7 +156,8 @@ extern "C" x2c_status x2c_build_dlu_host(x2c_ctx *ctx, const x2c_options *opt, c
   // staging layout: S (molecular-block mode only), T, V, W0, Wx, Wy, Wz (as needed), h
   // parts, kinds, kind transforms (pipelined path)
   const int64_t mats = (mb ? 1 : 0) + 3 + (nc == 4 ? 3 : 0);
-  const size_t bytes = sizeof(double) * ((mats + nc) * N2 + kind_doubles + (pipelined ? kind_u_doubles : 0)) + 1024;
+  const size_t bytes =
+      sizeof(double) * ((mats + nc) * N2 + kind_doubles + (pipelined ? kind_u_doubles : 0) + (L + 1) / 2 + 64) + 1024;
   X2C_TRY(ensure_stage(ctx, bytes));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   double *next = reinterpret_cast<double *>(ctx->stage);
@@ -189,8 +212,24 @@ extern "C" x2c_status x2c_build_dlu_host(x2c_ctx *ctx, const x2c_options *opt, c
     }
   }
   const double *hw[3] = {mol->Wx, mol->Wy, mol->Wz};
-  if (so_blocks)
-    for (int k = 0; k < 3; ++k) X2C_TRY(copy_diag_blocks(ctx, dW[k], hw[k], N, lay, cs[3]));
+  if (so_blocks) {
+    // same-atom spin-orbit blocks: one gather kernel per matrix when the host buffers are
+    // device-readable (pinned), so that hundreds of small copies do not sit on the copy engine
+    // ahead of the row bands; else one copy per block
+    const double *mw[3] = {device_readable(hw[0]), device_readable(hw[1]), device_readable(hw[2])};
+    if (mw[0] && mw[1] && mw[2]) {
+      int32_t *doff = reinterpret_cast<int32_t *>(next);
+      next += (L + 1 + 1) / 2 + 32;
+      X2C_TRY(x2c::upload(ctx, cs[3], doff, lay->atom_offset, sizeof(int32_t) * (L + 1)));
+      for (int k = 0; k < 3; ++k) {
+        x2c::tbegin(ctx, cs[3]);
+        gather_diag_kernel<<<L, 256, 0, cs[3]>>>(mw[k], dW[k], N, doff);
+        X2C_TRY(x2c::launched(ctx, "gather_diag_kernel", cs[3]));
+      }
+    } else {
+      for (int k = 0; k < 3; ++k) X2C_TRY(copy_diag_blocks(ctx, dW[k], hw[k], N, lay, cs[3]));
+    }
+  }
   x2c_mats dm{};
   dm.n = (int32_t)N;
   dm.S = dS; dm.T = dT; dm.V = dV; dm.W0 = dW0;
