@@ -77,16 +77,26 @@ x2c_status copy_band(x2c_ctx *ctx, double *dst, const double *src, int64_t N, co
   return X2C_OK;
 }
 
-// Row-atom chunks of about equal copy volume: atom a carries n_a (N - offset_a) elements of
-// the upper block triangle.
+// Row-atom chunks by copy volume (atom a carries n_a (N - offset_a) elements of the upper
+// block triangle): the first two chunks take 1/4 and 1/2 of an even share, so that the copy
+// of results back, the bound of the pipeline, starts early; the rest share the remainder.
 std::vector<int> row_chunks(const x2c_layout *lay, int64_t N, int chunks) {
   const int L = lay->n_atoms;
   std::vector<double> cum(L + 1, 0.0);
   for (int a = 0; a < L; ++a)
     cum[a + 1] = cum[a] + double(lay->atom_offset[a + 1] - lay->atom_offset[a]) * double(N - lay->atom_offset[a]);
+  std::vector<double> frac{0.0};
+  if (chunks >= 4) {
+    const double even = 1.0 / chunks, head = 0.25 * even + 0.5 * even;
+    frac.push_back(0.25 * even);
+    frac.push_back(head);
+    for (int k = 1; k <= chunks - 2; ++k) frac.push_back(head + (1.0 - head) * k / (chunks - 2));
+  } else {
+    for (int k = 1; k <= chunks; ++k) frac.push_back(double(k) / chunks);
+  }
   std::vector<int> cut{0};
-  for (int k = 1; k < chunks; ++k) {
-    const double target = cum[L] * k / chunks;
+  for (size_t k = 1; k + 1 < frac.size(); ++k) {
+    const double target = cum[L] * frac[k];
     int a = cut.back() + 1;
     while (a < L && cum[a] < target) ++a;
     if (a < L && a > cut.back()) cut.push_back(a);
@@ -289,11 +299,11 @@ extern "C" x2c_status x2c_build_dlu_host(x2c_ctx *ctx, const x2c_options *opt, c
   X2C_TRY_CUDA(ctx, cudaStreamWaitEvent(st, ev_kinds, 0));
   X2C_TRY(x2c_atomic_transforms(ctx, &o, nk, dk.data(), ku_out.data(), stream));
   const x2c::KindTransforms kt{ul.data(), us.data()};
-  // 2. chunk k: rows in on side streams 0/1 (alternating), assembly on `st`, h rows out on
-  //    side stream 2
+  // 2. chunk k: rows in on side stream 1 (one stream, so that the copy engine delivers the
+  //    chunks in order), assembly on `st`, h rows out on side stream 3
   for (int c = 0; c < nch; ++c) {
     const int a0 = cut[c], a1 = cut[c + 1];
-    cudaStream_t in = cs[1 + (c & 1)];
+    cudaStream_t in = cs[1];
     X2C_TRY(copy_band(ctx, dT, mol->T, N, lay, a0, a1, cudaMemcpyHostToDevice, in));
     X2C_TRY(copy_band(ctx, dV, mol->V, N, lay, a0, a1, cudaMemcpyHostToDevice, in));
     X2C_TRY(copy_band(ctx, dW0, mol->W0, N, lay, a0, a1, cudaMemcpyHostToDevice, in));
