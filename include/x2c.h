@@ -352,7 +352,7 @@ x2c_status x2c_ctx_set_split_variant(x2c_ctx *ctx, int32_t variant);
  * caller's stream, and every later one launches that graph again.  The matrices are read
  * when the graph runs, so their contents may change between calls; a changed pointer makes
  * a new plan.  Per-kernel timing (x2c_ctx_set_timing) sees inside replays.  Graphs are kept
- * for the 16 most recently used plans and dropped when the workspace grows; enable = 0
+ * for the 32 most recently used plans and dropped when the workspace grows; enable = 0
  * drops them (and waits for the device).  Counters and x2c_ctx_counters() report a replayed
  * call like an eager one. */
 x2c_status x2c_ctx_set_graphs(x2c_ctx *ctx, int32_t enable);

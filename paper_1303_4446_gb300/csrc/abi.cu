@@ -566,7 +566,7 @@ void end_call(x2c_ctx *ctx, const BuildPlan &plan) {
 // captures the enqueued work on a private stream and every later one launches the
 // instantiated graph on the caller's stream.
 
-constexpr size_t kMaxGraphs = 16;
+constexpr size_t kMaxGraphs = 32;
 constexpr size_t kMaxSeenPlans = 4096;
 
 struct KeyBuf {
