@@ -166,6 +166,19 @@ x2c_status x2c_build_full(x2c_ctx *ctx, const x2c_options *opt, const x2c_mats *
 x2c_status x2c_build_dlu(x2c_ctx *ctx, const x2c_options *opt, const x2c_layout *layout,
                          const x2c_mats *mol, const x2c_hout *h, void *stream);
 
+/* Neighbouring-atomic-blocks approximation (named at the end of Sec. III.A as the way to
+ * linear scaling; the paper does not spell it out): the pair blocks of neighbouring atoms are
+ * assembled as in x2c_build_dlu (Eq. 42 in Eq. 8), every other atom-other-atom block is the
+ * non-relativistic T_AB + V_AB with zero spin parts, as in DLH.  neighbours: HOST array of
+ * n_atoms x n_atoms bytes, row-major; atoms A != B are neighbours when
+ * neighbours[A n_atoms + B] or neighbours[B n_atoms + A] is non-zero (the caller's criterion:
+ * a distance cutoff, an overlap threshold, ...); same-atom blocks are always transformed.  All
+ * non-zero gives DLU, all zero DLH.  opt->local_approx must be X2C_LOCAL_DLU.  Reads T and V
+ * on every block (W0 and the spin parts as DLU does on the neighbouring blocks). */
+x2c_status x2c_build_dlu_nab(x2c_ctx *ctx, const x2c_options *opt, const x2c_layout *layout,
+                             const x2c_mats *mol, const uint8_t *neighbours, const x2c_hout *h,
+                             void *stream);
+
 /* Pair-list partition of a DLU build over several GPUs (Sec. III.A: the pair blocks h_AB of
  * Eqs. 42-43 are independent, and the per-kind transforms are small enough to solve on every
  * GPU).  Rank `rank` of `world` is given the row atoms [*a_begin, *a_end): consecutive ranges

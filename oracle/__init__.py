@@ -19,6 +19,7 @@ from .x2c import (  # noqa: F401
     x2c_dlu,
     dlu_from_transforms,
     x2c_dlh,
+    x2c_nab,
     picture_change,
     dlu_atomic_transforms,
     dlu_pair_block,

@@ -198,6 +198,24 @@ def x2c_dlh(m_mol: dict, offsets, atomic_per_atom=None, c: float = C_LIGHT):
     return np.where(same, h, T + V)
 
 
+def x2c_nab(m_mol: dict, offsets, neighbours, atomic_per_atom=None, c: float = C_LIGHT):
+    """Neighbouring-atomic-blocks approximation (named at the end of Sec. III.A for linear
+    scaling; read here as): the DLU Hamiltonian on the pair blocks of neighbouring atoms
+    (neighbours[A][B] true; every same-atom block counts) and the non-relativistic T_AB + V_AB,
+    with no spin-dependent part, on every other block.  neighbours = all true gives DLU, the
+    identity gives DLH."""
+    two_c = "Wx" in m_mol
+    h = x2c_dlu(m_mol, offsets, atomic_per_atom, c)["h"]
+    S, T, V, W = spinor_inputs(m_mol)
+    L = len(offsets) - 1
+    atom = np.repeat(np.arange(L), np.diff(np.asarray(offsets)))
+    nb = np.asarray(neighbours, dtype=bool) | np.eye(L, dtype=bool)
+    keep = nb[atom[:, None], atom[None, :]]
+    if two_c:
+        keep = np.kron(np.ones((2, 2), dtype=bool), keep)
+    return np.where(keep, h, T + V)
+
+
 def picture_change(UL, US, PLL, PSS):
     """Picture-change transformation of a one-electron property operator without
     large-small coupling (Sec. II: the reason the decoupling transforms are kept):

@@ -227,6 +227,35 @@ def x2c_build_dlu(ctx: Context, m: dict, offsets, atom_kind=None, kinds=None, tw
     return h
 
 
+def neighbour_mask(coords, cutoff: float):
+    """Atoms within `cutoff` (bohr) of each other, as the n_atoms x n_atoms byte mask of
+    x2c_build_dlu_nab."""
+    xyz = np.asarray(coords, dtype=np.float64)
+    d = np.linalg.norm(xyz[:, None, :] - xyz[None, :, :], axis=-1)
+    return np.ascontiguousarray(d <= cutoff, dtype=np.uint8)
+
+
+def x2c_build_dlu_nab(ctx: Context, m: dict, offsets, atom_kind, kinds, neighbours, two_component=False, c=None,
+                      precision=PREC_FP64, so_same_atom_only=True, n_slices=0, out=None, stream=None,
+                      decoupling=DEC_X2C):
+    """x2c_build_dlu_nab: DLU blocks for neighbouring atoms (mask `neighbours`, n_atoms x
+    n_atoms), T + V on every other block."""
+    nc = 4 if two_component else 1
+    ms = mats_struct(m, two_component)
+    L = len(offsets) - 1
+    nbr = np.ascontiguousarray(neighbours, dtype=np.uint8)
+    if nbr.shape != (L, L):
+        raise ValueError("neighbours must be n_atoms x n_atoms")
+    h = out if out is not None else _alloc_parts(ms.n, nc, m["S"].device)
+    lay = LayoutHolder(offsets, atom_kind, kinds, two_component)
+    o = options(two_component, c, precision, DLU_FREE_ATOM, so_same_atom_only, n_slices, decoupling=decoupling)
+    ho = _hout(h)
+    abi.check(ctx.lib.x2c_build_dlu_nab(ctx.handle, ctypes.byref(o), ctypes.byref(lay.s), ctypes.byref(ms),
+                                        nbr.ctypes.data, ctypes.byref(ho), _stream(stream)),
+              "x2c_build_dlu_nab", ctx.handle)
+    return h
+
+
 def x2c_dlu_partition(offsets, rank: int, world: int):
     """x2c_dlu_partition: the row atoms [a_begin, a_end) of rank `rank` of `world` in a
     pair-list partitioned DLU build (host-only; no device, no context)."""

@@ -113,6 +113,8 @@ _SIGS = {
                                       ctypes.POINTER(HOut), ctypes.POINTER(UOut), ctypes.c_void_p]),
     "x2c_build_dlu": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Options), ctypes.POINTER(Layout),
                                      ctypes.POINTER(Mats), ctypes.POINTER(HOut), ctypes.c_void_p]),
+    "x2c_build_dlu_nab": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Options), ctypes.POINTER(Layout),
+                                         ctypes.POINTER(Mats), ctypes.c_void_p, ctypes.POINTER(HOut), ctypes.c_void_p]),
     "x2c_build_dlu_rows": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Options), ctypes.POINTER(Layout),
                                           ctypes.POINTER(Mats), ctypes.POINTER(HOut), ctypes.c_int32, ctypes.c_int32,
                                           ctypes.c_void_p]),

@@ -453,7 +453,8 @@ using KindIndex = std::map<std::tuple<const double *, const double *, const doub
 
 x2c_status add_molecule(BuildPlan &plan, const x2c_options *opt, const x2c_layout *lay,
                         const x2c_mats *mol, const x2c_hout *h, int mol_index, KindIndex &kind_index,
-                        const KindTransforms *ku = nullptr, int a_begin = 0, int a_end = -1) {
+                        const KindTransforms *ku = nullptr, int a_begin = 0, int a_end = -1,
+                        const uint8_t *nbr = nullptr) {
   const int nc = plan.nc;
   if (!lay || lay->n_atoms < 1 || !lay->atom_offset || !mats_ok(mol, nc) || !h) return X2C_ERR_ARG;
   for (int q = 0; q < nc; ++q)
@@ -506,15 +507,18 @@ x2c_status add_molecule(BuildPlan &plan, const x2c_options *opt, const x2c_layou
     }
   }
   plan.mols.push_back(mol_desc(mol, h, nc));
-  // DLH: only the same-atom blocks are transformed; the rest is filled with T + V
+  // DLH: only the same-atom blocks are transformed; the rest is filled with T + V.  With a
+  // neighbour mask (neighbouring-atomic-blocks approximation) the blocks of neighbouring atoms
+  // are transformed as in DLU after that fill.
   const bool dlh = opt->local_approx == X2C_LOCAL_DLH;
-  if (dlh) plan.fills.push_back({mol_index, std::vector<int32_t>(lay->atom_offset, lay->atom_offset + L + 1)});
+  if (dlh || nbr) plan.fills.push_back({mol_index, std::vector<int32_t>(lay->atom_offset, lay->atom_offset + L + 1)});
   if (a_end < 0) a_end = L;
   if (a_begin < 0 || a_begin >= a_end || a_end > L) return X2C_ERR_ARG;
   for (int A = a_begin; A < a_end; ++A) {
     const int nA = lay->atom_offset[A + 1] - lay->atom_offset[A];
     plan.max_n = std::max(plan.max_n, nA);
     for (int B = A; B < (dlh ? A + 1 : L); ++B) {
+      if (nbr && B != A && !nbr[(int64_t)A * L + B] && !nbr[(int64_t)B * L + A]) continue;
       PairDesc P{};
       P.offA = lay->atom_offset[A];
       P.offB = lay->atom_offset[B];
@@ -871,16 +875,18 @@ x2c_status full_build(x2c_ctx *ctx, const x2c_options *opt, const x2c_mats *mol,
 
 x2c_status dlu_build(x2c_ctx *ctx, const x2c_options *opt, int n_mol, const x2c_layout *layouts,
                      const x2c_mats *mols, const x2c_hout *h, const KindTransforms *ku, cudaStream_t st,
-                     size_t *dry_bytes, int a_begin, int a_end) {
+                     size_t *dry_bytes, int a_begin, int a_end, const uint8_t *nbr) {
   X2C_TRY(begin_call(ctx));
   X2C_TRY(check_options(opt));
   if (n_mol < 1 || !layouts || !mols || !h) return X2C_ERR_ARG;
-  if ((a_begin != 0 || a_end >= 0) && n_mol != 1) return X2C_ERR_ARG;
+  if ((a_begin != 0 || a_end >= 0 || nbr) && n_mol != 1) return X2C_ERR_ARG;
+  if (nbr && opt->local_approx != X2C_LOCAL_DLU) return X2C_ERR_ARG;
   BuildPlan plan;
   plan.nc = opt->two_component ? 4 : 1;
   KindIndex kinds;
   for (int i = 0; i < n_mol; ++i)
-    X2C_TRY(add_molecule(plan, opt, &layouts[i], &mols[i], &h[i], i, kinds, ku ? &ku[i] : nullptr, a_begin, a_end));
+    X2C_TRY(add_molecule(plan, opt, &layouts[i], &mols[i], &h[i], i, kinds, ku ? &ku[i] : nullptr, a_begin, a_end,
+                         nbr));
   auto enqueue = [&](cudaStream_t s, size_t *dry) { return run_plan(ctx, opt, plan, s, nullptr, nullptr, dry); };
   if (dry_bytes) return enqueue(st, dry_bytes);
   X2C_TRY(graph_run(ctx, st, [&] { return plan_key(ctx, 1, opt, plan, nullptr, 0); }, plan, enqueue));
@@ -1174,6 +1180,13 @@ x2c_status x2c_build_dlu_rows(x2c_ctx *ctx, const x2c_options *opt, const x2c_la
                               const x2c_hout *h, int32_t a_begin, int32_t a_end, void *stream) {
   if (!layout || a_begin < 0 || a_end <= a_begin || a_end > layout->n_atoms) return X2C_ERR_ARG;
   return dlu_build(ctx, opt, 1, layout, mol, h, nullptr, static_cast<cudaStream_t>(stream), nullptr, a_begin, a_end);
+}
+
+x2c_status x2c_build_dlu_nab(x2c_ctx *ctx, const x2c_options *opt, const x2c_layout *layout, const x2c_mats *mol,
+                             const uint8_t *neighbours, const x2c_hout *h, void *stream) {
+  if (!neighbours) return X2C_ERR_ARG;
+  return dlu_build(ctx, opt, 1, layout, mol, h, nullptr, static_cast<cudaStream_t>(stream), nullptr, 0, -1,
+                   neighbours);
 }
 
 x2c_status x2c_dlu_partition(const x2c_layout *layout, int32_t rank, int32_t world, int32_t *a_begin,

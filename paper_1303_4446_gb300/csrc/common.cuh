@@ -225,10 +225,11 @@ struct KindTransforms {
 x2c_status full_build(x2c_ctx *ctx, const x2c_options *opt, const x2c_mats *mol, const x2c_hout *h,
                       const x2c_uout *U, cudaStream_t st, size_t *dry_bytes);
 // a_begin, a_end (one molecule only): assemble only the pair blocks (A, B >= A) whose row
-// atom A lies in [a_begin, a_end); a_end < 0 means the last atom.
+// atom A lies in [a_begin, a_end); a_end < 0 means the last atom.  nbr (one molecule, host
+// n_atoms^2 mask): only neighbouring pairs are assembled, every other block is T + V.
 x2c_status dlu_build(x2c_ctx *ctx, const x2c_options *opt, int n_mol, const x2c_layout *layouts,
                      const x2c_mats *mols, const x2c_hout *h, const KindTransforms *ku, cudaStream_t st,
-                     size_t *dry_bytes, int a_begin = 0, int a_end = -1);
+                     size_t *dry_bytes, int a_begin = 0, int a_end = -1, const uint8_t *nbr = nullptr);
 x2c_status transforms_build(x2c_ctx *ctx, const x2c_options *opt, int n_problems, const x2c_mats *inputs,
                             const x2c_uout *U, cudaStream_t st, size_t *dry_bytes);
 

@@ -335,3 +335,32 @@ def test_identity_transforms_give_the_closed_form(two_c):
     b = np.r_[60:90, N + 60:N + 90] if two_c else np.r_[60:90]
     for blk in (np.ix_(a, a), np.ix_(a, b), np.ix_(b, b)):
         assert np.abs(mixed[blk] - dlu[blk]).max() <= 1e-12 * np.abs(dlu).max()
+
+
+@pytest.mark.parametrize("two_c", [False, True])
+def test_neighbouring_blocks_pins(two_c):
+    """Neighbouring-atomic-blocks approximation (reading of the end of Sec. III.A): all atoms
+    neighbours -> DLU; none -> DLH; a neighbour block is its DLU block, a non-neighbour block is
+    T + V exactly; with a growing distance cutoff the error against DLU falls monotonically to
+    zero (fcc Ag13: cutoffs at the first three shell distances)."""
+    mol = w.silver_cluster(13, "s30")
+    m = w.molecule_inputs(mol, two_c)
+    off = mol.offsets
+    kinds = [w.atomic_inputs(47.0, "s30", two_c)] * 13
+    dlu = O.x2c_dlu(m, off, kinds)["h"]
+    L = 13
+    assert np.array_equal(O.x2c_nab(m, off, np.ones((L, L), bool), kinds), dlu)
+    assert np.array_equal(O.x2c_nab(m, off, np.zeros((L, L), bool), kinds), O.x2c_dlh(m, off, kinds))
+    d = np.linalg.norm(mol.coords[:, None] - mol.coords[None], axis=-1)
+    S, T, V, W = O.spinor_inputs(m)
+    N = mol.nbf
+    sp = (lambda r: np.r_[r, N + r]) if two_c else (lambda r: r)
+    nb = d <= 5.5  # nearest neighbours (5.459 bohr)
+    h = O.x2c_nab(m, off, nb, kinds)
+    for A in range(L):
+        for B in range(L):
+            ra, rb = sp(np.arange(off[A], off[A + 1])), sp(np.arange(off[B], off[B + 1]))
+            ref = dlu if (nb[A, B] or A == B) else T + V
+            assert np.array_equal(h[np.ix_(ra, rb)], ref[np.ix_(ra, rb)])
+    errs = [_rel(O.x2c_nab(m, off, d <= r, kinds), dlu) for r in (0.1, 5.5, 7.8, 9.5, 12.0)]
+    assert all(a > b for a, b in zip(errs, errs[1:-1])) and errs[-1] == 0.0, errs
