@@ -44,7 +44,7 @@ __device__ __forceinline__ void fw_factors(double t, double c, double &E0, doubl
 // round-robin ordering: m/2 disjoint rotations per step, m - 1 steps per sweep, m = n rounded
 // up to even; in step s, position k pairs with position m - 1 - k, position 0 holds index 0
 // and position i >= 1 holds 1 + (i - 1 + s) mod (m - 1)).  A rotation is skipped when
-// |a_pq| <= 1e-17 sqrt(a_pp a_qq) (relative criterion: small eigenvalues keep their relative
+// |a_pq| <= 1e-15 sqrt(a_pp a_qq) (relative criterion: small eigenvalues keep their relative
 // accuracy); a sweep without rotations ends the iteration (no convergence within
 // kJacobiSweeps is flagged).  The matrix lives in shared memory, and so do the eigenvectors
 // when both fit (n <= kJacobiSmemV), else they are updated in global memory.  Output:
@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(256) jacobi_kernel(const double *Ain, int n, i
         double c = 1.0, s = 0.0;
         if (q < n) {
           const double apq = A[p * n + q], app = A[p * n + p], aqq = A[q * n + q];
-          if (fabs(apq) > 1e-17 * sqrt(fabs(app * aqq))) {
+          if (fabs(apq) > 1e-15 * sqrt(fabs(app * aqq))) {
             const double tau = (aqq - app) / (2.0 * apq);
             const double t = fabs(tau) > 1e150 ? 0.5 / tau : copysign(1.0, tau) / (fabs(tau) + sqrt(1.0 + tau * tau));
             c = 1.0 / sqrt(1.0 + t * t);
