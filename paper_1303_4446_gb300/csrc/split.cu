@@ -86,6 +86,21 @@ __device__ __forceinline__ __nv_bfloat16 bits_to_bf16(uint32_t f) {
 // Maximum over the warp (one redux.sync instruction).
 __device__ __forceinline__ int warp_max(int v) { return __reduce_max_sync(0xffffffffu, v); }
 
+// Eight consecutive TMEM columns of this warp's 32 lanes (one register each).
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+               : "r"(taddr)
+               : "memory");
+}
+
+// a b + c with a 64-bit c and result (one wide integer multiply-add).
+__device__ __forceinline__ long long mad_wide(int a, int b, long long c) {
+  long long d;
+  asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+  return d;
+}
+
 // ------------------------------------------------------------------ slicers
 // Class description: pairs share nA, nB and the transforms U_A, U_B.
 struct ClassInfo {
@@ -344,6 +359,7 @@ __host__ __device__ constexpr int gemm_threads(int wq) { return 64 + 128 * wq; }
 // with the sign of the quaternion product table (C_l = sign(l, l xor k) M_k F_(l xor k)).
 template <int S, int NCQ, bool SOP = false>
 struct Stage1Fused {
+  static constexpr bool kGroupDrain = false;
   const int *e1, *k2p, *eF;
   __nv_bfloat16 *A2;
   int *e2;
@@ -424,6 +440,7 @@ struct Stage1Fused {
 // per slice.
 template <int S, bool SOP = false>
 struct Stage1T {
+  static constexpr bool kGroupDrain = false;
   const int *e1, *k2p, *eF;
   __nv_bfloat16 *A2;
   int *e2;
@@ -521,6 +538,7 @@ struct SlotInfo {
 
 template <int NCQ>
 struct Stage2Store {
+  static constexpr bool kGroupDrain = true;
   const PairDesc *pairs;
   const MolDesc *mols;
   const int *e2, *eG;
@@ -565,45 +583,24 @@ struct Stage2Store {
       slot[tid] = si;
     }
     if (NCQ == 4) {
+      // Lane pq holds u_a = O[(j,pq),(i',a)], a term of output l = a xor pq (lane distance a)
+      // with sign sign+(l, pq).  A butterfly with fixed send indices routes every term to
+      // lane l: over xor 1 the terms a = 1, 3 move, over xor 2 the sum bound for lane pq xor 2.
+      // Padding rows and columns hold zero digits, so no term needs masking.
+      long long neg[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) neg[a] = quat_sign_adj(a ^ pq, pq) < 0 ? -1ll : 0ll;
 #pragma unroll
       for (int g = 0; g < NC / 4; ++g) {
         const int il = (c0 >> 2) + g;  // i' slot within the tile
         const int ip = nt * IT + il;
         const bool colv = ip < nA;
-        // t[l] = sign+(l, pq) I[4g + (l xor pq)]: the xor permutation as two conditional
-        // swaps, so that I stays in registers (no dynamically indexed local array)
-        long long t[4];
-        {
-          long long u0 = I[4 * g], u1 = I[4 * g + 1], u2 = I[4 * g + 2], u3 = I[4 * g + 3];
-          if (pq & 1) {
-            const long long a = u0, b = u2;
-            u0 = u1;
-            u1 = a;
-            u2 = u3;
-            u3 = b;
-          }
-          if (pq & 2) {
-            const long long a = u0, b = u1;
-            u0 = u2;
-            u1 = u3;
-            u2 = a;
-            u3 = b;
-          }
-          const bool ok = valid && colv;
-          t[0] = ok ? (quat_sign_adj(0, pq) < 0 ? -u0 : u0) : 0;
-          t[1] = ok ? (quat_sign_adj(1, pq) < 0 ? -u1 : u1) : 0;
-          t[2] = ok ? (quat_sign_adj(2, pq) < 0 ? -u2 : u2) : 0;
-          t[3] = ok ? (quat_sign_adj(3, pq) < 0 ? -u3 : u3) : 0;
-        }
-        // reduce-scatter over the quad: lane with pq = l ends up with sum_p t[l]
-        const int b0 = pq & 1, b1 = (pq >> 1) & 1;
-        long long keep0 = b0 ? t[1] : t[0], keep1 = b0 ? t[3] : t[2];
-        const long long send0 = b0 ? t[0] : t[1], send1 = b0 ? t[2] : t[3];
-        keep0 += __shfl_xor_sync(0xffffffffu, send0, 1);
-        keep1 += __shfl_xor_sync(0xffffffffu, send1, 1);
-        long long keep = b1 ? keep1 : keep0;
-        const long long send = b1 ? keep0 : keep1;
-        keep += __shfl_xor_sync(0xffffffffu, send, 2);
+        long long x[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) x[a] = (I[4 * g + a] ^ neg[a]) - neg[a];
+        const long long w0 = x[0] + __shfl_xor_sync(0xffffffffu, x[1], 1);
+        const long long w2 = x[2] + __shfl_xor_sync(0xffffffffu, x[3], 1);
+        const long long keep = w0 + __shfl_xor_sync(0xffffffffu, w2, 2);
         sv[(pq * IT + il) * JTP + jl] = (valid && colv) ? scaled_to_double(keep, E + eG[ip * 4]) : 0.0;
       }
     } else {
@@ -787,23 +784,43 @@ __global__ void __launch_bounds__(gemm_threads(Epi::template wq<NT>()), 1)
         break;
       }
       umma::fence_after_sync();
+      // I = sum_g acc_g 2^8(S-1-g), each accumulator an exact integer below 2^24, folded in by
+      // one 32 x 32 + 64 multiply-add (terms 2^8(S-1-g) >= 2^32 only touch the high word).
+      // Epilogues with a register budget to spare (Epi::kGroupDrain) load the S accumulators
+      // of 8 columns at a time (fewer waits); the others all columns of one accumulator at a
+      // time.
       long long I[CW];
+      auto fold = [](long long x, uint32_t acc, int g) {
+        const int d = __float2int_rn(__uint_as_float(acc));
+        const int sh = 8 * (S - 1 - g);
+        return sh < 32 ? mad_wide(d, 1 << sh, x) : x + (static_cast<long long>(d) << sh);
+      };
+      if constexpr (Epi::kGroupDrain) {
 #pragma unroll
-      for (int j = 0; j < CW; ++j) I[j] = 0;
+        for (int c = 0; c < CW; c += 8) {
+          uint32_t v[S][8];
 #pragma unroll
-      for (int g = 0; g < S; ++g) {
-        // all of this warp's columns of accumulator g in flight at once, then one wait
-        uint32_t v[CW];
+          for (int g = 0; g < S; ++g) tmem_ld8(lane_addr + static_cast<uint32_t>(g * NT + sub * CW + c), v[g]);
+          umma::tmem_ld_wait();
 #pragma unroll
-        for (int c = 0; c < CW; c += 8)
-          asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                       : "=r"(v[c]), "=r"(v[c + 1]), "=r"(v[c + 2]), "=r"(v[c + 3]), "=r"(v[c + 4]), "=r"(v[c + 5]),
-                         "=r"(v[c + 6]), "=r"(v[c + 7])
-                       : "r"(lane_addr + static_cast<uint32_t>(g * NT + sub * CW + c))
-                       : "memory");
-        umma::tmem_ld_wait();
+          for (int j = 0; j < 8; ++j) {
+            long long x = __float2int_rn(__uint_as_float(v[S - 1][j]));
 #pragma unroll
-        for (int j = 0; j < CW; ++j) I[j] = I[j] * 256 + __float2int_rn(__uint_as_float(v[j]));
+            for (int g = S - 2; g >= 0; --g) x = fold(x, v[g][j], g);
+            I[c + j] = x;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int g = 0; g < S; ++g) {
+          uint32_t v[CW];
+#pragma unroll
+          for (int c = 0; c < CW; c += 8)
+            tmem_ld8(lane_addr + static_cast<uint32_t>(g * NT + sub * CW + c), *reinterpret_cast<uint32_t(*)[8]>(v + c));
+          umma::tmem_ld_wait();
+#pragma unroll
+          for (int j = 0; j < CW; ++j) I[j] = g == 0 ? fold(0, v[j], 0) : fold(I[j], v[j], g);
+        }
       }
       umma::fence_before_sync();
       __syncwarp();
@@ -999,7 +1016,7 @@ struct Runner {
   // The stage-1 A operand of np pairs (one CTA each; requires nB <= 64, TRA >= 2 nA, KP >= 2 nB).
   static x2c_status slice_mid(x2c_ctx *ctx, cudaStream_t st, const ClassInfo &ci, int np, int TRA, int KP,
                               const int *kexp, __nv_bfloat16 *out, int *rexp) {
-    if (ci.nB > 64 || TRA < 2 * ci.nA || KP < 2 * ci.nB || (TRA & 7) || (KP & 7)) return X2C_ERR_ARG;
+    if (ci.nA > 64 || ci.nB > 64 || TRA < 2 * ci.nA || KP < 2 * ci.nB || (TRA & 7) || (KP & 7)) return X2C_ERR_ARG;
     const int smem = S * (TRA / 8) * (KP / 8) * kChunkPad * 2;
     auto kern = slice_mid_pair_kernel<S>;
     X2C_TRY_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
