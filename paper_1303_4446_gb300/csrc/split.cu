@@ -544,7 +544,8 @@ struct Stage2Store {
   const int *e2, *eG;
   int rows, nA, nB, S;
   int accumulate;  // add to h instead of writing it (the spin-orbit passes of diagonal pairs)
-  // staging: [part][i' (NT/NCQ)][j (128/NCQ), padded by one against bank conflicts] doubles,
+  // staging: [part][i' (NT/NCQ)][j (128/NCQ), padded by one against bank conflicts] values
+  // as IEEE-754 bits (no FP64 instruction runs here: the mirror's sign is an integer xor),
   // then the per-j-slot output addresses
   static constexpr int JT = kTileM / NCQ;
   static constexpr int JTP = NCQ == 4 ? JT + 1 : JT;  // two-component: padded row stride
@@ -556,7 +557,7 @@ struct Stage2Store {
                                              int lane, uint8_t *stage) const {
     constexpr int IT = WQ * NC / NCQ;  // i' slots per tile (NT = WQ NC columns: compile-time)
     (void)NT;
-    double *sv = reinterpret_cast<double *>(stage);
+    unsigned long long *sv = reinterpret_cast<unsigned long long *>(stage);
     SlotInfo<NCQ> *slot = reinterpret_cast<SlotInfo<NCQ> *>(stage + static_cast<size_t>(NT) * JTP * 8);
     const int r = mt * kTileM + rloc;
     const bool valid = r < rows;
@@ -601,14 +602,14 @@ struct Stage2Store {
         const long long w0 = x[0] + __shfl_xor_sync(0xffffffffu, x[1], 1);
         const long long w2 = x[2] + __shfl_xor_sync(0xffffffffu, x[3], 1);
         const long long keep = w0 + __shfl_xor_sync(0xffffffffu, w2, 2);
-        sv[(pq * IT + il) * JTP + jl] = (valid && colv) ? scaled_to_double(keep, E + eG[ip * 4]) : 0.0;
+        sv[(pq * IT + il) * JTP + jl] = (valid && colv) ? scaled_to_bits(keep, E + eG[ip * 4]) : 0ull;
       }
     } else {
 #pragma unroll
       for (int t = 0; t < NC; ++t) {
         const int il = c0 + t;
         const int ip = nt * IT + il;
-        sv[il * JTP + jl] = (valid && ip < nA) ? scaled_to_double(I[t], E + eG[ip]) : 0.0;
+        sv[il * JTP + jl] = (valid && ip < nA) ? scaled_to_bits(I[t], E + eG[ip]) : 0ull;
       }
     }
     (void)lane;
@@ -623,19 +624,20 @@ struct Stage2Store {
       const SlotInfo<NCQ> &si = slot[jl2];
       if (!si.valid || il2 >= iv) continue;
       double *dst = si.h[part] + static_cast<int64_t>(si.offA + ip0 + il2) * si.ld + si.offBj;
-      const double val = sv[(part * IT + il2) * JTP + jl2];
-      if (accumulate) *dst += val;
-      else *dst = val;
+      const unsigned long long val = sv[(part * IT + il2) * JTP + jl2];
+      if (accumulate) *dst += bits_to_double(val);
+      else *reinterpret_cast<unsigned long long *>(dst) = val;
     }
-    // mirror h_BA = h_AB+: rows offB + j, contiguous along i'
+    // mirror h_BA = h_AB+: rows offB + j, contiguous along i' (parts 1..3 change sign)
     if (!accumulate) {
       for (int idx = tid; idx < NCQ * IT * JT; idx += nthr) {
         const int il2 = idx % IT, rest = idx / IT;
         const int jl2 = rest % JT, part = rest / JT;
         const SlotInfo<NCQ> &si = slot[jl2];
         if (!si.valid || si.diag || il2 >= iv) continue;
-        const double v = sv[(part * IT + il2) * JTP + jl2];
-        si.h[part][static_cast<int64_t>(si.offBj) * si.ld + (si.offA + ip0 + il2)] = (part == 0) ? v : -v;
+        const unsigned long long v = sv[(part * IT + il2) * JTP + jl2] ^ (part == 0 ? 0ull : 0x8000000000000000ull);
+        *reinterpret_cast<unsigned long long *>(si.h[part] + static_cast<int64_t>(si.offBj) * si.ld +
+                                                 (si.offA + ip0 + il2)) = v;
       }
     }
     epi_sync();

@@ -93,9 +93,10 @@ __host__ __device__ __forceinline__ void digits(long long F, int (&d)[S]) {
   }
 }
 
-// I 2^E as a double with integer operations only (round half up on the magnitude).
-__host__ __device__ __forceinline__ double scaled_to_double(long long I, int E) {
-  if (I == 0) return 0.0;
+// The IEEE-754 bits of I 2^E as a double, by integer operations only (round half up on the
+// magnitude; underflow to a signed zero, overflow to a signed infinity).
+__host__ __device__ __forceinline__ unsigned long long scaled_to_bits(long long I, int E) {
+  if (I == 0) return 0ull;
   const unsigned long long neg = I < 0;
   const unsigned long long v = neg ? static_cast<unsigned long long>(-I) : static_cast<unsigned long long>(I);
   const int lz = clz64(v);
@@ -107,9 +108,14 @@ __host__ __device__ __forceinline__ double scaled_to_double(long long I, int E) 
     ex += 1;
   }
   const int be = ex + 1023;
-  if (be <= 0) return neg ? -0.0 : 0.0;
-  if (be >= 2047) return bits_to_double((neg << 63) | (0x7FFull << 52));
-  return bits_to_double((neg << 63) | (static_cast<unsigned long long>(be) << 52) | (mant & 0xFFFFFFFFFFFFFull));
+  if (be <= 0) return neg << 63;
+  if (be >= 2047) return (neg << 63) | (0x7FFull << 52);
+  return (neg << 63) | (static_cast<unsigned long long>(be) << 52) | (mant & 0xFFFFFFFFFFFFFull);
+}
+
+// I 2^E as a double (the value of scaled_to_bits).
+__host__ __device__ __forceinline__ double scaled_to_double(long long I, int E) {
+  return bits_to_double(scaled_to_bits(I, E));
 }
 
 }  // namespace x2c
