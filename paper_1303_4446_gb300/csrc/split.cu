@@ -86,12 +86,20 @@ __device__ __forceinline__ __nv_bfloat16 bits_to_bf16(uint32_t f) {
 // Maximum over the warp (one redux.sync instruction).
 __device__ __forceinline__ int warp_max(int v) { return __reduce_max_sync(0xffffffffu, v); }
 
-// Eight consecutive TMEM columns of this warp's 32 lanes (one register each).
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
-               : "r"(taddr)
-               : "memory");
+// N (4 or 8) consecutive TMEM columns of this warp's 32 lanes (one register each).
+template <int N>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t (&v)[N]) {
+  static_assert(N == 4 || N == 8, "columns");
+  if constexpr (N == 8)
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                 : "r"(taddr)
+                 : "memory");
+  else
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
+                 : "r"(taddr)
+                 : "memory");
 }
 
 // a b + c with a 64-bit c and result (one wide integer multiply-add).
@@ -99,6 +107,49 @@ __device__ __forceinline__ long long mad_wide(int a, int b, long long c) {
   long long d;
   asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
   return d;
+}
+__device__ __forceinline__ unsigned long long mad_wide_u(unsigned a, unsigned b, unsigned long long c) {
+  unsigned long long d;
+  asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+  return d;
+}
+
+// Recombination of the S FP32 accumulators of one output (a[g] = bits of acc_g, each an exact
+// integer) into I = sum_g acc_g 2^8(S-1-g), with one conversion-unit instruction at S = 5:
+// * g = 0, 1: |acc_0| <= 2^14 K and |acc_1| <= 2^15 K (leading digits within [-128, 128],
+//   K <= 128) are at most 2^22 in magnitude, so acc + 1.5 2^23 is exact and its bits are the
+//   integer plus 0x4B400000 (one FP32 add);
+// * g = 2 .. S-3: float-to-integer conversion;
+// * the last two diagonals are merged in FP32 as round((acc_{S-2} + acc_{S-1}/256) / 4) (the
+//   same add trick, |.| < 2^22): an error of at most 2^10 in I, against up to 2^15.8 of
+//   dropped diagonals g >= S.
+// The 0x4B400000 offsets of the float-carried terms are removed by one 64-bit constant.
+template <int S>
+__device__ __forceinline__ long long combine_acc(const uint32_t (&a)[S]) {
+  static_assert(S >= 3 && S <= 6, "slices");
+  constexpr float kC = 12582912.0f;    // 1.5 2^23
+  constexpr unsigned kCb = 0x4B400000u;  // its bits
+  constexpr int kLast = S - 2;           // diagonals kLast and kLast + 1 are merged
+  constexpr int kMagic = kLast < 2 ? kLast : 2;
+  unsigned long long off = static_cast<unsigned long long>(kCb) << 10;
+#pragma unroll
+  for (int g = 0; g < kMagic; ++g) off += static_cast<unsigned long long>(kCb) << (8 * (S - 1 - g));
+  const float t = __fmaf_rn(__uint_as_float(a[S - 1]), 0.0009765625f, __fmaf_rn(__uint_as_float(a[S - 2]), 0.25f, kC));
+  unsigned long long x = mad_wide_u(__float_as_uint(t), 1024u, 0ull - off);
+#pragma unroll
+  for (int g = kMagic; g < kLast; ++g) {
+    const int sh = 8 * (S - 1 - g);  // 16 or 24
+    x = static_cast<unsigned long long>(
+        mad_wide(__float2int_rn(__uint_as_float(a[g])), 1 << sh, static_cast<long long>(x)));
+  }
+#pragma unroll
+  for (int g = 0; g < kMagic; ++g) {
+    const unsigned b = __float_as_uint(__fadd_rn(__uint_as_float(a[g]), kC));
+    const int sh = 8 * (S - 1 - g);
+    if (sh < 32) x = mad_wide_u(b, 1u << sh, x);
+    else x += static_cast<unsigned long long>(b) << sh;
+  }
+  return static_cast<long long>(x);
 }
 
 // ------------------------------------------------------------------ slicers
@@ -184,6 +235,7 @@ __global__ void __launch_bounds__(256) slice8_fp64_kernel(Src src, int rows, int
   const int g0 = (rr / grp) * grp;
   for (int q = g0; q < g0 + grp; ++q) e = max(e, sexp[q]);
   if (e == kNoExp) e = 0;
+  e += 1;  // digit scale: |x| < 2^(e-1), so the leading digit stays within [-128, 128]
   if (lane == 0 && r < rows_pad) rexp[r] = e;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
@@ -266,6 +318,8 @@ __global__ void __launch_bounds__(512) slice_mid_pair_kernel(ClassInfo ci, int T
     eB = warp_max(eB);
     if (eT == kNoExp) eT = 0;
     if (eB == kNoExp) eB = 0;
+    eT += 1;  // digit scales with a leading digit within [-128, 128]
+    eB += 1;
     if (lane == 0) {
       rexp[static_cast<size_t>(p) * TRA + i] = eT;
       rexp[static_cast<size_t>(p) * TRA + nA + i] = eB;
@@ -359,7 +413,7 @@ __host__ __device__ constexpr int gemm_threads(int wq) { return 64 + 128 * wq; }
 // with the sign of the quaternion product table (C_l = sign(l, l xor k) M_k F_(l xor k)).
 template <int S, int NCQ, bool SOP = false>
 struct Stage1Fused {
-  static constexpr bool kGroupDrain = false;
+  static constexpr int kDrainGroup = 4;
   const int *e1, *k2p, *eF;
   __nv_bfloat16 *A2;
   int *e2;
@@ -403,6 +457,7 @@ struct Stage1Fused {
 #pragma unroll
       for (int q = 0; q < NCQ; ++q) m = max(m, bl[j + q]);
       if (m == kNoExp) m = 0;
+      m += 1;  // leading digit within [-128, 128]
 #pragma unroll
       for (int q = 0; q < NCQ; ++q) bl[j + q] = m;
     }
@@ -440,7 +495,7 @@ struct Stage1Fused {
 // per slice.
 template <int S, bool SOP = false>
 struct Stage1T {
-  static constexpr bool kGroupDrain = false;
+  static constexpr int kDrainGroup = 4;
   const int *e1, *k2p, *eF;
   __nv_bfloat16 *A2;
   int *e2;
@@ -483,6 +538,7 @@ struct Stage1T {
     m = max(m, __shfl_xor_sync(0xffffffffu, m, 1));  // the 4 quaternion rows of one j
     m = max(m, __shfl_xor_sync(0xffffffffu, m, 2));
     if (m == kNoExp) m = 0;
+    m += 1;  // leading digit within [-128, 128]
     int cd = c;
     bool neg = false;
     if (SOP) {
@@ -538,7 +594,7 @@ struct SlotInfo {
 
 template <int NCQ>
 struct Stage2Store {
-  static constexpr bool kGroupDrain = true;
+  static constexpr int kDrainGroup = 8;
   const PairDesc *pairs;
   const MolDesc *mols;
   const int *e2, *eG;
@@ -786,42 +842,23 @@ __global__ void __launch_bounds__(gemm_threads(Epi::template wq<NT>()), 1)
         break;
       }
       umma::fence_after_sync();
-      // I = sum_g acc_g 2^8(S-1-g), each accumulator an exact integer below 2^24, folded in by
-      // one 32 x 32 + 64 multiply-add (terms 2^8(S-1-g) >= 2^32 only touch the high word).
-      // Epilogues with a register budget to spare (Epi::kGroupDrain) load the S accumulators
-      // of 8 columns at a time (fewer waits); the others all columns of one accumulator at a
-      // time.
+      // I = sum_g acc_g 2^8(S-1-g) (combine_acc), the S accumulators of a group of DG columns
+      // in flight at once before one wait (DG: the epilogue's register budget)
+      constexpr int DG = Epi::kDrainGroup;
+      static_assert(CW % DG == 0, "drain groups");
       long long I[CW];
-      auto fold = [](long long x, uint32_t acc, int g) {
-        const int d = __float2int_rn(__uint_as_float(acc));
-        const int sh = 8 * (S - 1 - g);
-        return sh < 32 ? mad_wide(d, 1 << sh, x) : x + (static_cast<long long>(d) << sh);
-      };
-      if constexpr (Epi::kGroupDrain) {
 #pragma unroll
-        for (int c = 0; c < CW; c += 8) {
-          uint32_t v[S][8];
+      for (int c = 0; c < CW; c += DG) {
+        uint32_t v[S][DG];
 #pragma unroll
-          for (int g = 0; g < S; ++g) tmem_ld8(lane_addr + static_cast<uint32_t>(g * NT + sub * CW + c), v[g]);
-          umma::tmem_ld_wait();
+        for (int g = 0; g < S; ++g) tmem_ld<DG>(lane_addr + static_cast<uint32_t>(g * NT + sub * CW + c), v[g]);
+        umma::tmem_ld_wait();
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            long long x = __float2int_rn(__uint_as_float(v[S - 1][j]));
+        for (int j = 0; j < DG; ++j) {
+          uint32_t a[S];
 #pragma unroll
-            for (int g = S - 2; g >= 0; --g) x = fold(x, v[g][j], g);
-            I[c + j] = x;
-          }
-        }
-      } else {
-#pragma unroll
-        for (int g = 0; g < S; ++g) {
-          uint32_t v[CW];
-#pragma unroll
-          for (int c = 0; c < CW; c += 8)
-            tmem_ld8(lane_addr + static_cast<uint32_t>(g * NT + sub * CW + c), *reinterpret_cast<uint32_t(*)[8]>(v + c));
-          umma::tmem_ld_wait();
-#pragma unroll
-          for (int j = 0; j < CW; ++j) I[j] = g == 0 ? fold(0, v[j], 0) : fold(I[j], v[j], g);
+          for (int g = 0; g < S; ++g) a[g] = v[g][j];
+          I[c + j] = combine_acc<S>(a);
         }
       }
       umma::fence_before_sync();
