@@ -784,6 +784,7 @@ __global__ void __launch_bounds__(gemm_threads(Epi::template wq<NT>()), 1)
   } else if (warp == 1) {
     if (lane == 0) {  // ---------------- MMA issuer
       constexpr uint32_t idesc = umma::idesc_bf16_f32(kTileM, NT);
+      const uint64_t res_desc = umma::smem_desc(umma::smem_u32(sB), 128, G::KG * 128);
       bool ok = umma::mbar_wait(bar_b, 0, kWaitBudget);
       long long it = 0;
       for (int ti = 0; ti < n_my && ok && !abort_flag; ++ti) {
@@ -799,17 +800,16 @@ __global__ void __launch_bounds__(gemm_threads(Epi::template wq<NT>()), 1)
             break;
           }
           umma::fence_after_sync();
-          const uint32_t str0 = umma::smem_u32(sA + slot * STR_TILE);
+          // descriptors advance by address >> 4 in their low field (shared-memory addresses stay
+          // below 256 KB, so the 14-bit field never carries): one add per operand and MMA
+          const uint64_t str_d = umma::smem_desc(umma::smem_u32(sA + slot * STR_TILE), 128, G::KG * 128);
+          const uint32_t acc0 = s2 > 0 ? 1u : 0u;
           for (int t = 0; t + s2 < S; ++t) {
-            const uint32_t res0 = umma::smem_u32(sB + t * RES_TILE);
-            const uint32_t a0 = TRM ? res0 : str0, b0 = TRM ? str0 : res0;
+            const uint64_t res_d = res_desc + static_cast<uint64_t>(t) * (RES_TILE >> 4);
+            const uint64_t ad = TRM ? res_d : str_d, bd = TRM ? str_d : res_d;
             const uint32_t d = tmem + static_cast<uint32_t>((s2 + t) * NT);
 #pragma unroll
-            for (int kk = 0; kk < KP / 16; ++kk) {
-              const uint64_t ad = umma::smem_desc(a0 + kk * 256, 128, G::KG * 128);
-              const uint64_t bd = umma::smem_desc(b0 + kk * 256, 128, G::KG * 128);
-              umma::mma_bf16(d, ad, bd, idesc, (s2 > 0 || kk > 0) ? 1u : 0u);
-            }
+            for (int kk = 0; kk < KP / 16; ++kk) umma::mma_bf16(d, ad + kk * 16, bd + kk * 16, idesc, kk > 0 ? 1u : acc0);
           }
           umma::mma_commit(&empty[slot]);  // slot reusable once these MMAs are done
         }
