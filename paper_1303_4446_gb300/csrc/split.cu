@@ -1,12 +1,13 @@
 // Split-precision (Ozaki) DLU pair assembly on the tcgen05 BF16 tensor cores.
 //
-// Every FP64 operand row x_k (k < K) is scaled by a power of two 2^e (|x| < 2^e) and cut
-// into S signed 8-bit digits,  x 2^-e = sum_s a_s 2^-8(s+1),  |a_0| <= 256, a_s in
-// [-128, 127] (s >= 1), each exactly representable in BF16.  A product A B is the sum of the
-// digit products A_s B_t with s + t <= S - 1; all products of one diagonal g = s + t share
-// the scale 2^-8(g+2) and accumulate in their own FP32 TMEM accumulator.  With K <= 96 every
-// partial sum is an integer below 1.75 K 2^16 < 2^24, so the FP32 accumulation is exact and
-// the only error is the dropped diagonals g >= S (relative 2^-8S of the row x column scale).
+// Every FP64 operand row x_k (k < K) is scaled by a power of two 2^e (|x| < 2^(e-1)) and cut
+// into S signed 8-bit digits,  x 2^-e = sum_s a_s 2^-8(s+1),  |a_s| <= 128, each exactly
+// representable in BF16.  A product A B is the sum of the digit products A_s B_t with
+// s + t <= S - 1; all products of one diagonal g = s + t share the scale 2^-8(g+2) and
+// accumulate in their own FP32 TMEM accumulator.  With K <= 128 every partial sum is an
+// integer of magnitude at most (g + 1) 2^14 K < 2^24, so the FP32 accumulation is exact and
+// the error is the dropped diagonals g >= S (relative 2^-(8S-2) of the row x column scale)
+// plus the FP32 merge of the last two diagonals in combine_acc (below 2^-5 of that).
 //
 // GB300 has 2 FP64 FMA per clock per SM, so no FP64 arithmetic is used inside the pipeline:
 // digits are cut from the IEEE bits with integer operations, the epilogue recombines the S
@@ -588,18 +589,19 @@ struct Stage1T {
 template <int NCQ>
 struct SlotInfo {
   double *h[NCQ];  // output parts of the pair's molecule
-  long long ld;
+  int ld;
   int offA, offBj, valid, diag;  // h_AB rows start at offA, its column is offB + j
 };
 
-template <int NCQ>
+template <int NCQ, bool ACC = false>
 struct Stage2Store {
   static constexpr int kDrainGroup = 8;
   const PairDesc *pairs;
   const MolDesc *mols;
   const int *e2, *eG;
   int rows, nA, nB, S;
-  int accumulate;  // add to h instead of writing it (the spin-orbit passes of diagonal pairs)
+  // ACC: add to h instead of writing it (the spin-orbit passes of diagonal pairs); a compile-time
+  // choice, so the writing pass carries no FP64 instruction
   // staging: [part][i' (NT/NCQ)][j (128/NCQ), padded by one against bank conflicts] values
   // as IEEE-754 bits (no FP64 instruction runs here: the mirror's sign is an integer xor),
   // then the per-j-slot output addresses
@@ -632,7 +634,7 @@ struct Stage2Store {
         const MolDesc &m = mols[P.mol];
         si.valid = 1;
         si.diag = P.diag;
-        si.ld = m.ld;
+        si.ld = static_cast<int>(m.ld);
         si.offA = P.offA;
         si.offBj = P.offB + j;
         for (int q = 0; q < NCQ; ++q) si.h[q] = m.h[q];
@@ -679,13 +681,13 @@ struct Stage2Store {
       const int il2 = rest % IT, part = rest / IT;
       const SlotInfo<NCQ> &si = slot[jl2];
       if (!si.valid || il2 >= iv) continue;
-      double *dst = si.h[part] + static_cast<int64_t>(si.offA + ip0 + il2) * si.ld + si.offBj;
+      double *dst = si.h[part] + (static_cast<int64_t>(si.offA + ip0 + il2) * si.ld + si.offBj);
       const unsigned long long val = sv[(part * IT + il2) * JTP + jl2];
-      if (accumulate) *dst += bits_to_double(val);
+      if constexpr (ACC) *dst += bits_to_double(val);
       else *reinterpret_cast<unsigned long long *>(dst) = val;
     }
     // mirror h_BA = h_AB+: rows offB + j, contiguous along i' (parts 1..3 change sign)
-    if (!accumulate) {
+    if constexpr (!ACC) {
       for (int idx = tid; idx < NCQ * IT * JT; idx += nthr) {
         const int il2 = idx % IT, rest = idx / IT;
         const int jl2 = rest % JT, part = rest / JT;
@@ -1148,10 +1150,10 @@ struct Runner {
                            Stage1Fused<S, 1>{e1, k2p, eF, A2, e2, np, nA, cols1, KP2, TRA, 0}, 1, TRA, "split_stage1")));
         if (nc == 4)
           X2C_TRY((gemm_any<NT4, NT1>(ctx, st, nc, KP2, A2, Gs, rows2p / kTileM, cols2,
-                           Stage2Store<4>{dp, d_mols, e2, eG, rows2, nA, nB, S, 0}, 2, kTileM, "split_stage2")));
+                           Stage2Store<4>{dp, d_mols, e2, eG, rows2, nA, nB, S}, 2, kTileM, "split_stage2")));
         else
           X2C_TRY((gemm_any<NT4, NT1>(ctx, st, nc, KP2, A2, Gs, rows2p / kTileM, cols2,
-                           Stage2Store<1>{dp, d_mols, e2, eG, rows2, nA, nB, S, 0}, 2, kTileM, "split_stage2")));
+                           Stage2Store<1>{dp, d_mols, e2, eG, rows2, nA, nB, S}, 2, kTileM, "split_stage2")));
         // spin-orbit middle term, all pairs (general case): FP64 products.  (Same-atom blocks
         // only, the usual case: split passes after the chunk loop.)
         if (nc == 4 && so_all) {
@@ -1207,7 +1209,7 @@ struct Runner {
                                           Stage1Fused<S, 4, true>{e1, k2p, eF, A2, e2, ns, nA, cols1, KP2, TRA, k}, 1,
                                           TRA, "split_spin_orbit")));
             X2C_TRY((gemm_any<NT4, NT1>(ctx, st, nc, KP2, A2, Gs, srows2p / kTileM, cols2,
-                                        Stage2Store<4>{ds, d_mols, e2, eG, srows2, nA, nB, S, 1}, 2, kTileM,
+                                        Stage2Store<4, true>{ds, d_mols, e2, eG, srows2, nA, nB, S}, 2, kTileM,
                                         "split_spin_orbit")));
           }
         }
