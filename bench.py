@@ -40,7 +40,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # one ncu capture of the Ag55 two-component build (1540 pairs, the same per-pair shapes as
 # Ag309); a launch's traffic is this times its pairs.  Set an entry to None when its kernel
 # changes.
-PROFILED_DRAM_BYTES_PER_PAIR = {("split_stage1", "trm"): 238.6e3, ("split_stage2", "nt96"): 302.6e3}
+PROFILED_DRAM_BYTES_PER_PAIR = {("split_stage1", "trm"): 238.5e3, ("split_stage2", "nt96"): 302.0e3}
 WORKLOADS = {
     "ag309_2c": dict(L=309, basis="s48", two_c=True),
     # 64 uneven spin-free clusters, n ~ U[2, 43], basis s30/s48 50/50, one batched launch
