@@ -305,7 +305,7 @@ x2c_status run_plan(x2c_ctx *ctx, const x2c_options *opt, BuildPlan &plan, cudaS
   const size_t mol_bytes = ((plan.mols.size() * sizeof(MolDesc) + 255) / 256) * 256;
   size_t fill_bytes = 0;
   for (const auto &f : plan.fills) fill_bytes += ((f.off.size() * sizeof(int32_t) + 255) / 256) * 256;
-  const size_t asm_ws = assemble_workspace_bytes(plan.pairs, nc, plan.max_n, opt->precision);
+  const size_t asm_ws = assemble_workspace_bytes(plan.pairs, nc, plan.max_n, opt->precision, ctx->split_ws_cap);
   const size_t total = arena_doubles(u_doubles) + desc_bytes + table_bytes + mol_bytes + fill_bytes +
                        std::max(solve_ws, asm_ws) + 8192;
   if (dry_bytes) {

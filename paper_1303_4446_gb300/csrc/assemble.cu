@@ -186,15 +186,18 @@ constexpr int64_t kRChunkDoubles = (int64_t)1 << 27;  // 1 GiB of stage-1 interm
 
 }  // namespace
 
-size_t assemble_workspace_bytes(const std::vector<PairDesc> &pairs, int nc, int max_n, int precision) {
+size_t assemble_workspace_bytes(const std::vector<PairDesc> &pairs, int nc, int max_n, int precision,
+                                size_t split_cap) {
   if (precision == X2C_PREC_SPLIT_BF16) {
     // split path: per pair about 2nA*KP*S*2 + nc nB*2nA*8 + nc nB*KP*S*2 bytes (S <= 6,
-    // KP <= 128) plus per-kind operands; chunked inside, so cap the request at 3 GiB
+    // KP <= 128) plus per-kind operands; chunked inside.  The request is capped at split_cap
+    // (24 GiB by default: a build of Ag309's 47895 two-component pairs, about 17 GB, runs in
+    // one chunk, with fewer launches and kernel tails; larger ones in chunks of that size).
     const size_t kp = 128, S = 6;
     size_t need = 64u << 20;
     for (const auto &P : pairs)
       need += (size_t)2 * P.nA * kp * S * 2 + (size_t)nc * P.nB * 2 * P.nA * 8 + (size_t)nc * P.nB * kp * S * 2 + 4096;
-    return std::min<size_t>(need, (size_t)3 << 30);
+    return std::min<size_t>(need, split_cap);
   }
   int64_t total = 0, chunk_max = 0, cur = 0;
   for (const auto &P : pairs) {

@@ -47,6 +47,9 @@ struct x2c_ctx {
   // when set, the workspace grows stream-ordered from this pool on the call's stream
   // (no device-wide synchronisation; used by the server, whose slots run concurrently)
   cudaMemPool_t pool = nullptr;
+  // largest workspace a split-precision pair assembly asks for (it runs in chunks of what
+  // fits); the server keeps its slots at 3 GiB so that admission under its budget is unchanged
+  size_t split_ws_cap = (size_t)24 << 30;
   // streams on which independent size groups of a batched solve run concurrently
   std::vector<cudaStream_t> aux;
   std::vector<cudaEvent_t> aux_join;
@@ -287,7 +290,8 @@ x2c_status assemble_pairs_split(x2c_ctx *ctx, cudaStream_t st, double c, int nc,
                                 const std::vector<PairDesc> &pairs, const MolDesc *d_mols, UTable ut,
                                 const std::vector<const double *> &hUL, const std::vector<const double *> &hUS,
                                 int n_slices, Arena &ar);
-size_t assemble_workspace_bytes(const std::vector<PairDesc> &pairs, int nc, int max_n, int precision);
+size_t assemble_workspace_bytes(const std::vector<PairDesc> &pairs, int nc, int max_n, int precision,
+                                size_t split_cap);
 // DLH: h = T + V (spin parts 0) on every block of molecule `mol` outside the same-atom
 // blocks; d_off: device copy of the molecule's L + 1 atom offsets, N = d_off[L].
 x2c_status fill_nonrel_offdiag(x2c_ctx *ctx, cudaStream_t st, const MolDesc *d_mols, int mol, const int32_t *d_off,

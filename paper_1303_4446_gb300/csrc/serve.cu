@@ -25,6 +25,9 @@ using x2c::serve::Candidate;
 using Clock = std::chrono::steady_clock;
 
 constexpr uint64_t kDefaultBudget = 150ull * 1000 * 1000 * 1000;
+// Split-precision workspace cap of a slot: requests larger than it run their pair assembly in
+// chunks, and the admission budget counts no more than this per slot.
+constexpr size_t kSlotSplitCap = (size_t)3 << 30;
 constexpr size_t kLargePairs = 2000;  // builds above this many pair blocks count as large
 constexpr int kFreeSMs = 32;          // SMs a large build leaves to the other slots
 
@@ -758,6 +761,7 @@ x2c_status x2c_server_create(const x2c_server_options *opt, x2c_server **out) {
   ok = ok && cudaDeviceGetAttribute(&s->sms_, cudaDevAttrMultiProcessorCount, s->device) == cudaSuccess;
   ok = ok && cudaEventCreate(&s->ev_ref) == cudaSuccess;
   ok = ok && x2c_ctx_create(s->device, &s->planner) == X2C_OK;
+  if (s->planner) s->planner->split_ws_cap = kSlotSplitCap;
   for (int i = 0; ok && i < slots; ++i) {
     Slot sl;
     ok = cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking) == cudaSuccess &&
@@ -767,6 +771,7 @@ x2c_status x2c_server_create(const x2c_server_options *opt, x2c_server **out) {
          cudaHostAlloc(reinterpret_cast<void **>(&sl.h_status), sizeof(int), cudaHostAllocDefault) == cudaSuccess;
     if (sl.ctx) {
       sl.ctx->pool = s->pool;
+      sl.ctx->split_ws_cap = kSlotSplitCap;
       // no timing runs inside the request loop: they would synchronise a slot stream while
       // the scheduler holds its lock; the slots take the untuned default variant
       sl.ctx->autotune = false;
