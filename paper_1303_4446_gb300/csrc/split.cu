@@ -275,8 +275,12 @@ __global__ void __launch_bounds__(512) slice_mid_pair_kernel(ClassInfo ci, int T
   const int KG = KP >> 3;
   const int chunks = (TRA >> 3) * KG;  // core-matrix chunks per slice
   const int words = S * chunks * kChunkPad / 8;
-  for (int o = threadIdx.x; o < words; o += blockDim.x) reinterpret_cast<uint4 *>(stg)[o] = make_uint4(0, 0, 0, 0);
-  __syncthreads();
+  // the staged tile needs zeros only where it pads the pair's rows (TRA > 2 nA) or columns
+  // (KP > 2 nB): without padding every element read back below is written by put()
+  if (TRA != 2 * nA || KP != 2 * nB) {
+    for (int o = threadIdx.x; o < words; o += blockDim.x) reinterpret_cast<uint4 *>(stg)[o] = make_uint4(0, 0, 0, 0);
+    __syncthreads();
+  }
   const PairDesc &P = ci.pairs[p];
   const MolDesc &m = ci.mols[P.mol];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
