@@ -57,7 +57,11 @@ typedef enum {
   X2C_PREC_FP64 = 0,       /* every product in FP64 */
   X2C_PREC_SPLIT_BF16 = 1  /* DLU pair assembly as split-precision (Ozaki) BF16 products
                               with FP32 accumulation on the tensor cores; every eigen-type
-                              step (sign function, square roots, Cholesky) stays FP64 */
+                              step (sign function, square roots, Cholesky) stays FP64.  The
+                              assembly shares operands per class of pairs with the same
+                              (U_A, U_B): at most 64 classes per build (free-atom mode: kinds
+                              squared; molecular-block mode, one U per atom: up to ten atoms
+                              in DLU, 64 in DLH), else X2C_ERR_ARG */
 } x2c_precision;
 
 typedef enum {

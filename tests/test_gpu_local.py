@@ -43,8 +43,8 @@ def rel(got, ref_full, two_c):
 @pytest.mark.parametrize("mode", ["free_atom", "molecular_block"])
 @pytest.mark.parametrize("prec", [x.PREC_FP64, x.PREC_SPLIT_BF16])
 def test_dlh_matches_oracle(ctx, two_c, mode, prec):
-    if mode == "molecular_block" and prec == x.PREC_SPLIT_BF16:
-        pytest.skip("the split assembly shares operands per kind (free-atom mode)")
+    # molecular-block mode with split precision: every atom has its own transforms, so each
+    # (U_A, U_B) pair class is assembled by its own launches (up to 64 classes per build)
     mol = w.silver_cluster(4, "s30")
     m = w.molecule_inputs(mol, two_c)
     at = w.atomic_inputs(47.0, "s30", two_c)
@@ -62,6 +62,18 @@ def test_dlh_matches_oracle(ctx, two_c, mode, prec):
     assert torch.equal(h[0][a, b], g["T"][a, b] + g["V"][a, b])
     for q in range(1, len(h)):
         assert not h[q][a, b].any()
+
+
+@pytest.mark.parametrize("two_c", [False, True])
+def test_dlu_molecular_block_split(ctx, two_c):
+    # the paper-literal atomic blocks (Eq. 43 read literally): ten pair classes for Ag4
+    mol = w.silver_cluster(4, "s30")
+    m = w.molecule_inputs(mol, two_c)
+    at = w.atomic_inputs(47.0, "s30", two_c)
+    h = x.x2c_build_dlu(ctx, dev(m), mol.offsets, [0] * 4, [dev(at)], two_component=two_c,
+                        precision=x.PREC_SPLIT_BF16, dlu_potential=x.DLU_MOLECULAR_BLOCK)
+    ctx.status()
+    assert rel(h, O.x2c_dlu(m, mol.offsets, None)["h"], two_c) <= 1e-9
 
 
 def test_dlh_ag13_two_component_split(ctx):
