@@ -305,15 +305,24 @@ x2c_status run_plan(x2c_ctx *ctx, const x2c_options *opt, BuildPlan &plan, cudaS
   const size_t mol_bytes = ((plan.mols.size() * sizeof(MolDesc) + 255) / 256) * 256;
   size_t fill_bytes = 0;
   for (const auto &f : plan.fills) fill_bytes += ((f.off.size() * sizeof(int32_t) + 255) / 256) * 256;
-  const size_t asm_ws = assemble_workspace_bytes(plan.pairs, nc, plan.max_n, opt->precision, ctx->split_ws_cap);
-  const size_t total = arena_doubles(u_doubles) + desc_bytes + table_bytes + mol_bytes + fill_bytes +
-                       std::max(solve_ws, asm_ws) + 8192;
+  auto total_for = [&](size_t cap) {
+    const size_t asm_ws = assemble_workspace_bytes(plan.pairs, nc, plan.max_n, opt->precision, cap);
+    return arena_doubles(u_doubles) + desc_bytes + table_bytes + mol_bytes + fill_bytes +
+           std::max(solve_ws, asm_ws) + 8192;
+  };
+  const size_t total = total_for(ctx->split_ws_cap);
   if (dry_bytes) {
     *dry_bytes = total;
     return X2C_OK;
   }
   Arena ar;
-  X2C_TRY(ensure_workspace(ctx, total, &ar, st));
+  x2c_status ws = ensure_workspace(ctx, total, &ar, st);
+  if (ws == X2C_ERR_NOMEM && ctx->split_ws_cap > kSplitWsCapSmall) {
+    // the one-chunk workspace does not fit: this context assembles in smaller chunks from now on
+    ctx->split_ws_cap = kSplitWsCapSmall;
+    ws = ensure_workspace(ctx, total_for(ctx->split_ws_cap), &ar, st);
+  }
+  X2C_TRY(ws);
   double *Ustore = ar.take(std::max<size_t>(1, u_doubles));
   double **dUL = reinterpret_cast<double **>(ar.take_bytes(np * sizeof(double *)));
   double **dUS = reinterpret_cast<double **>(ar.take_bytes(np * sizeof(double *)));
@@ -708,7 +717,13 @@ x2c_status graph_run(x2c_ctx *ctx, cudaStream_t st, KeyFn &&make_key, BuildPlan 
   size_t need = 0;
   X2C_TRY(enqueue(st, &need));
   Arena unused;
-  X2C_TRY(ensure_workspace(ctx, need, &unused, st));
+  x2c_status ws = ensure_workspace(ctx, need, &unused, st);
+  if (ws == X2C_ERR_NOMEM && ctx->split_ws_cap > kSplitWsCapSmall) {
+    ctx->split_ws_cap = kSplitWsCapSmall;  // smaller chunks from now on (see dlu_build)
+    X2C_TRY(enqueue(st, &need));
+    ws = ensure_workspace(ctx, need, &unused, st);
+  }
+  X2C_TRY(ws);
   if (!ctx->cap_stream) X2C_TRY_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
   const size_t ev0 = ctx->ev_used, pend0 = ctx->pending.size();
   const int64_t launches0 = ctx->launches;

@@ -18,6 +18,10 @@
 #define X2C_DEV_DECOUPLING 6
 #define X2C_DEV_NONFINITE 7
 
+// Split-precision workspace cap of the server's slots, and the fallback of a context whose
+// larger workspace could not be allocated (the pair assembly then runs in chunks of this size).
+constexpr size_t kSplitWsCapSmall = (size_t)3 << 30;
+
 struct x2c_ctx {
   int device = 0;
   int *d_status = nullptr;      // first device-side error code (0 = none)
@@ -48,7 +52,8 @@ struct x2c_ctx {
   // (no device-wide synchronisation; used by the server, whose slots run concurrently)
   cudaMemPool_t pool = nullptr;
   // largest workspace a split-precision pair assembly asks for (it runs in chunks of what
-  // fits); the server keeps its slots at 3 GiB so that admission under its budget is unchanged
+  // fits); the server keeps its slots at kSplitWsCapSmall so that admission under its budget
+  // is unchanged, and a context whose large workspace cannot be allocated falls back to it
   size_t split_ws_cap = (size_t)24 << 30;
   // streams on which independent size groups of a batched solve run concurrently
   std::vector<cudaStream_t> aux;

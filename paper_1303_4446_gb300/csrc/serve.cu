@@ -27,7 +27,7 @@ using Clock = std::chrono::steady_clock;
 constexpr uint64_t kDefaultBudget = 150ull * 1000 * 1000 * 1000;
 // Split-precision workspace cap of a slot: requests larger than it run their pair assembly in
 // chunks, and the admission budget counts no more than this per slot.
-constexpr size_t kSlotSplitCap = (size_t)3 << 30;
+constexpr size_t kSlotSplitCap = ::kSplitWsCapSmall;
 constexpr size_t kLargePairs = 2000;  // builds above this many pair blocks count as large
 constexpr int kFreeSMs = 32;          // SMs a large build leaves to the other slots
 
