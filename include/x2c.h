@@ -25,7 +25,9 @@
  *    and returned by x2c_ctx_status(), which synchronises the stream.
  *  - A context is bound to one device and is not thread-safe; use one per host thread.
  *    It owns a device workspace that grows on demand (the first call of a larger size
- *    allocates) and is freed by x2c_ctx_destroy().
+ *    allocates) and is freed by x2c_ctx_destroy().  A split-precision DLU assembly asks for
+ *    up to 24 GiB (Ag309 two-component: about 17 GB, one chunk); if that cannot be
+ *    allocated, the context falls back to chunks of 3 GiB for the rest of its life.
  *  - No function aborts, traps or exits; errors are returned as x2c_status.
  */
 #ifndef X2C_H
