@@ -99,31 +99,52 @@ __global__ void __launch_bounds__(256) jacobi_kernel(const double *Ain, int n, i
         sn[k] = s;
       }
       __syncthreads();
-      // rows p, q of A (J^T A) and of QT (V J: the eigenvectors are QT's rows)
+      // A <- G A G^T for all the step's rotations at once, G_k = [[c, -s], [s, c]] on the
+      // rows and columns (p_k, q_k): the 2 x 2 block of pairs (k, k') becomes
+      // G_k B G_k'^T.  Only blocks k <= k' are computed (A is symmetric) and mirrored; each
+      // thread reads and writes only its block and the mirror, so the update is in place.
+      // The eigenvector rows p, q of QT take G_k in the same pass (disjoint data).
+      for (int idx = threadIdx.x; idx < half * half; idx += blockDim.x) {
+        const int k = idx / half, k2 = idx - k * half;
+        if (k > k2) continue;
+        const double c1 = cs[k], s1 = sn[k], c2 = cs[k2], s2 = sn[k2];
+        if (s1 == 0.0 && s2 == 0.0) continue;
+        const int r[2] = {pp[k], qq[k]}, q2[2] = {pp[k2], qq[k2]};
+        double blk[2][2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+#pragma unroll
+          for (int v = 0; v < 2; ++v) blk[u][v] = (r[u] < n && q2[v] < n) ? A[r[u] * n + q2[v]] : 0.0;
+        double t[2][2];
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+          t[0][v] = c1 * blk[0][v] - s1 * blk[1][v];
+          t[1][v] = s1 * blk[0][v] + c1 * blk[1][v];
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const double x0 = c2 * t[u][0] - s2 * t[u][1], x1 = s2 * t[u][0] + c2 * t[u][1];
+          blk[u][0] = x0;
+          blk[u][1] = x1;
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+#pragma unroll
+          for (int v = 0; v < 2; ++v)
+            if (r[u] < n && q2[v] < n) {
+              A[r[u] * n + q2[v]] = blk[u][v];
+              A[q2[v] * n + r[u]] = blk[u][v];
+            }
+      }
       for (int idx = threadIdx.x; idx < half * n; idx += blockDim.x) {
         const int k = idx / n, j = idx - k * n;
         const double s = sn[k];
         if (s == 0.0) continue;
         const int p = pp[k], q = qq[k];
         const double c = cs[k];
-        const double ap = A[p * n + j], aq = A[q * n + j];
-        A[p * n + j] = c * ap - s * aq;
-        A[q * n + j] = s * ap + c * aq;
         const double vp = qt[p * n + j], vq = qt[q * n + j];
         qt[p * n + j] = c * vp - s * vq;
         qt[q * n + j] = s * vp + c * vq;
-      }
-      __syncthreads();
-      // columns p, q of A (A J)
-      for (int idx = threadIdx.x; idx < half * n; idx += blockDim.x) {
-        const int k = idx / n, i = idx - k * n;
-        const double s = sn[k];
-        if (s == 0.0) continue;
-        const int p = pp[k], q = qq[k];
-        const double c = cs[k];
-        const double ap = A[i * n + p], aq = A[i * n + q];
-        A[i * n + p] = c * ap - s * aq;
-        A[i * n + q] = s * ap + c * aq;
       }
       __syncthreads();
     }
